@@ -1,0 +1,203 @@
+"""FP64 CPU oracle for HardSoftRas -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  The product (``paper_2204_01386_gb300``) never
+does, and this package imports nothing from it.  The arithmetic lives in
+``hardsoftras_oracle.c`` (plain C, FP64, brute force); this file only
+marshals numpy arrays into it.
+
+Inputs are taken as the float32 (or float16) values the CUDA path receives and
+widened exactly to float64, so the oracle evaluates the exact function of the
+very same inputs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hardsoftras_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _View(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("n_faces", C.c_int32),
+                ("pos", C.POINTER(C.c_double)), ("col", C.POINTER(C.c_double)),
+                ("uv", C.POINTER(C.c_double)), ("faces", C.POINTER(C.c_int32)),
+                ("tex_w", C.c_int32), ("tex_h", C.c_int32), ("tex", C.POINTER(C.c_double)),
+                ("mvp", C.c_double * 16), ("light", C.c_double * 3),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("K", C.c_int32), ("r", C.c_double), ("sigma", C.c_double), ("delta", C.c_double),
+                ("edge_mode", C.c_int32), ("shade_mode", C.c_int32), ("brute_force", C.c_int32)]
+
+
+class _Window(C.Structure):
+    _fields_ = [("x0", C.c_int32), ("y0", C.c_int32), ("w", C.c_int32), ("h", C.c_int32)]
+
+
+class _FwdOut(C.Structure):
+    _fields_ = [("rgba", C.POINTER(C.c_double)), ("ids", C.POINTER(C.c_int32)),
+                ("hard", C.POINTER(C.c_int32)), ("dist", C.POINTER(C.c_double)),
+                ("key", C.POINTER(C.c_double)), ("sh", C.POINTER(C.c_uint8)),
+                ("edge", C.POINTER(C.c_uint8)), ("margin_hard", C.POINTER(C.c_double)),
+                ("margin_cand", C.POINTER(C.c_double)), ("n_hard", C.POINTER(C.c_int32))]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            assert lib.orc_sizeof_view() == C.sizeof(_View)
+            assert lib.orc_sizeof_params() == C.sizeof(_Params)
+            assert lib.orc_sizeof_fwd_out() == C.sizeof(_FwdOut)
+            lib.orc_forward.argtypes = [C.POINTER(_View), C.POINTER(_Params), C.POINTER(_Window), C.POINTER(_FwdOut)]
+            lib.orc_backward.argtypes = [C.POINTER(_View), C.POINTER(_Params), C.POINTER(_Window),
+                                         C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _up(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_uint8))
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(np.asarray(a).astype(np.float64))
+
+
+class _Inputs:
+    """Keeps the float64 copies alive while the C call runs."""
+
+    def __init__(self, mesh, view, params, brute_force):
+        self.pos = _f64(mesh.pos)
+        self.col = _f64(getattr(mesh, "col", None))
+        self.uv = _f64(getattr(mesh, "uv", None))
+        self.faces = np.ascontiguousarray(np.asarray(mesh.faces, dtype=np.int32))
+        tex = getattr(mesh, "tex", None)
+        self.tex = _f64(tex)
+        v = _View()
+        v.n_verts, v.n_faces = self.pos.shape[0], self.faces.shape[0]
+        v.pos, v.col, v.uv = _dp(self.pos), _dp(self.col), _dp(self.uv)
+        v.faces = _ip(self.faces)
+        if self.tex is not None:
+            v.tex_h, v.tex_w = self.tex.shape[0], self.tex.shape[1]
+            v.tex = _dp(self.tex)
+        v.mvp[:] = [float(x) for x in np.asarray(view.mvp, np.float64).reshape(16)]
+        v.light[:] = [float(x) for x in np.asarray(view.light, np.float64).reshape(3)]
+        v.width, v.height = int(view.width), int(view.height)
+        self.view = v
+        p = _Params()
+        p.K, p.r, p.sigma, p.delta = int(params.K), float(params.r), float(params.sigma), float(params.delta)
+        p.edge_mode, p.shade_mode = int(params.edge_mode), int(params.shade_mode)
+        p.brute_force = int(bool(brute_force))
+        self.params = p
+
+
+def _window(view, window):
+    w = _Window()
+    if window is None:
+        window = (0, 0, int(view.width), int(view.height))
+    w.x0, w.y0, w.w, w.h = [int(x) for x in window]
+    return w
+
+
+def render(mesh, view, params, window=None, brute_force=False):
+    """Forward pass of one view over ``window`` = (x0, y0, w, h) pixels.
+
+    Returns a dict with ``rgba [h,w,4]``, ``ids``/``hard``/``dist`` ``[K,h,w]``,
+    ``key [K+1,h,w]``, ``sh``/``edge [h,w]``, ``margin_hard``/``margin_cand``
+    (pixel units) and ``n_hard`` plus the oracle's status word.
+    """
+    lib = _load()
+    inp = _Inputs(mesh, view, params, brute_force)
+    win = _window(view, window)
+    K, h, w = inp.params.K, win.h, win.w
+    res = dict(rgba=np.zeros((h, w, 4)), ids=np.zeros((K, h, w), np.int32),
+               hard=np.zeros((K, h, w), np.int32), dist=np.zeros((K, h, w)),
+               key=np.zeros((K + 1, h, w)), sh=np.zeros((h, w), np.uint8),
+               edge=np.zeros((h, w), np.uint8), margin_hard=np.zeros((h, w)),
+               margin_cand=np.zeros((h, w)), n_hard=np.zeros((h, w), np.int32))
+    o = _FwdOut(_dp(res["rgba"]), _ip(res["ids"]), _ip(res["hard"]), _dp(res["dist"]),
+                _dp(res["key"]), _up(res["sh"]), _up(res["edge"]), _dp(res["margin_hard"]),
+                _dp(res["margin_cand"]), _ip(res["n_hard"]))
+    st = lib.orc_forward(C.byref(inp.view), C.byref(inp.params), C.byref(win), C.byref(o))
+    if st & 1:
+        raise ValueError("oracle: invalid argument")
+    res["status"] = st
+    return res
+
+
+def backward(mesh, view, params, grad_rgba, window=None, brute_force=False):
+    """Adjoint of ``render`` for dL/d(rgba) = ``grad_rgba [h,w,4]`` over ``window``.
+
+    Returns ``(grad_pos [V,3], grad_col [V,3] or None, grad_tex [Ht,Wt,4] or None)``.
+    """
+    lib = _load()
+    inp = _Inputs(mesh, view, params, brute_force)
+    win = _window(view, window)
+    g = np.ascontiguousarray(np.asarray(grad_rgba, np.float64).reshape(win.h, win.w, 4))
+    gp = np.zeros_like(inp.pos)
+    gc = np.zeros_like(inp.pos) if inp.col is not None else None
+    gt = np.zeros_like(inp.tex) if inp.tex is not None else None
+    st = lib.orc_backward(C.byref(inp.view), C.byref(inp.params), C.byref(win), _dp(g), _dp(gp), _dp(gc), _dp(gt))
+    if st & 1:
+        raise ValueError("oracle: invalid argument")
+    return gp, gc, gt
+
+
+def render_scene(scene, windows=None, brute_force=False):
+    """Per-view forward results for a whole scene (list of dicts)."""
+    out = []
+    for i, v in enumerate(scene.views):
+        win = None if windows is None else windows[i]
+        out.append(render(scene.meshes[v.mesh], v, scene.params, win, brute_force))
+    return out
+
+
+def backward_scene(scene, grads, windows=None):
+    """Gradients summed over the views of a scene, per mesh."""
+    res = []
+    for m in scene.meshes:
+        res.append([np.zeros(m.pos.shape), None if m.col is None else np.zeros(m.col.shape),
+                    None if m.tex is None else np.zeros(m.tex.shape)])
+    for i, v in enumerate(scene.views):
+        win = None if windows is None else windows[i]
+        gp, gc, gt = backward(scene.meshes[v.mesh], v, scene.params, grads[i], win)
+        r = res[v.mesh]
+        r[0] += gp
+        if gc is not None:
+            r[1] += gc
+        if gt is not None:
+            r[2] += gt
+    return res
