@@ -118,7 +118,9 @@ class _Inputs:
         v.width, v.height = int(view.width), int(view.height)
         self.view = v
         p = _Params()
-        p.K, p.r, p.sigma, p.delta = int(params.K), float(params.r), float(params.sigma), float(params.delta)
+        # the soft-raster parameters reach the CUDA path as float32: use the same values
+        f32 = lambda x: float(np.float32(x))  # noqa: E731
+        p.K, p.r, p.sigma, p.delta = int(params.K), f32(params.r), f32(params.sigma), f32(params.delta)
         p.edge_mode, p.shade_mode = int(params.edge_mode), int(params.shade_mode)
         p.brute_force = int(bool(brute_force))
         self.params = p

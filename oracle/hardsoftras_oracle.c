@@ -25,7 +25,9 @@
  *   5. hard test      inside the closed triangle with the top-left fill rule
  *   6. Shift          key = depth/2 if hard else |dist|/2 + 1/2  (Eq. Shift)
  *   7. peel           the K smallest (key, face id) pairs (Alg. 2 outer loop)
- *   8. barycentrics   perspective correct, unclamped outside the hard face
+ *   8. barycentrics   perspective correct; a soft fragment takes the barycentrics
+ *                     of its closest point of the hard face (reading: soft faces
+ *                     extend the hard face, Sec. 3.3.2)
  *   9. normals        area-weighted vertex normals (listing BuildNormalCompute)
  *  10. texture        bilinear, texel centres at i + 1/2, REPEAT wrap
  *  11. shading        vertex colour / unlit texture / texture * max(0, n.l)
@@ -164,8 +166,10 @@ typedef struct {
     int id, hard;
     double dist_px;   /* signed pixel distance */
     double key;
-    double lam[3];    /* screen-space barycentrics */
+    double lam[3];    /* screen-space barycentrics (of the closest point for soft fragments) */
     int feat;         /* closest boundary feature: 0..2 edge i interior, 3..5 corner i-3 */
+    int segP, segQ;   /* edge feature: canonical endpoints; closest point = P + t (Q - P) */
+    double segt;
 } frag_t;
 
 static int lex_less(double ax, double ay, double bx, double by)
@@ -176,8 +180,8 @@ static int lex_less(double ax, double ay, double bx, double by)
 /* evaluates face t at p; fills fr and returns the signed pixel distance */
 static double eval_face(const face_t *t, int id, double px, double py, double S, frag_t *fr)
 {
-    double Fnum[3], L[3], seg[3];
-    int segfeat[3];
+    double Fnum[3], L[3], seg[3], segt[3];
+    int segfeat[3], segP[3], segQ[3];
     int inside = 1;
     for (int i = 0; i < 3; ++i) {
         int a = i, b = (i + 1) % 3;
@@ -192,12 +196,13 @@ static double eval_face(const face_t *t, int id, double px, double py, double S,
         if (!(Fnum[i] > 0.0 || (Fnum[i] == 0.0 && t->owns[i]))) inside = 0;
         double tP = dPx * ex + dPy * ey;
         double tQ = dQx * ex + dQy * ey;
+        segP[i] = P; segQ[i] = Q; segt[i] = 0.0;
         if (tP <= 0.0) { seg[i] = sqrt(dPx * dPx + dPy * dPy); segfeat[i] = 3 + P; }
         else if (tQ >= 0.0) { seg[i] = sqrt(dQx * dQx + dQy * dQy); segfeat[i] = 3 + Q; }
-        else { seg[i] = fabs(c) / L[i]; segfeat[i] = i; }
+        else { seg[i] = fabs(c) / L[i]; segfeat[i] = i; segt[i] = tP / (ex * ex + ey * ey); }
     }
     double dist;
-    int feat;
+    int feat, mseg = 0;
     if (inside) {
         int m = 0;
         double best = Fnum[0] / L[0];
@@ -206,17 +211,29 @@ static double eval_face(const face_t *t, int id, double px, double py, double S,
     } else {
         int m = 0;
         for (int i = 1; i < 3; ++i) if (seg[i] < seg[m]) m = i;
-        dist = -seg[m]; feat = segfeat[m];
+        dist = -seg[m]; feat = segfeat[m]; mseg = m;
     }
     double absA = fabs(t->A2);
     fr->id = id;
     fr->hard = inside;
     fr->dist_px = dist;
     fr->feat = feat;
-    /* vertex opposite edge i is (i + 2) % 3 */
-    fr->lam[2] = Fnum[0] / absA;
-    fr->lam[0] = Fnum[1] / absA;
-    fr->lam[1] = Fnum[2] / absA;
+    fr->segP = segP[mseg]; fr->segQ = segQ[mseg]; fr->segt = segt[mseg];
+    if (inside) {
+        /* area ratios; the vertex opposite edge i is (i + 2) % 3 */
+        fr->lam[2] = Fnum[0] / absA;
+        fr->lam[0] = Fnum[1] / absA;
+        fr->lam[1] = Fnum[2] / absA;
+    } else {
+        /* the closest point of the hard face: a corner, or a point of an edge */
+        fr->lam[0] = fr->lam[1] = fr->lam[2] = 0.0;
+        if (feat >= 3) {
+            fr->lam[feat - 3] = 1.0;
+        } else {
+            fr->lam[fr->segP] = 1.0 - fr->segt;
+            fr->lam[fr->segQ] = fr->segt;
+        }
+    }
     if (inside) {
         double z = fr->lam[0] * t->Z[0] + fr->lam[1] * t->Z[1] + fr->lam[2] * t->Z[2];
         fr->key = 0.5 * z;
@@ -591,10 +608,26 @@ static void dist_grad(const face_t *t, const frag_t *fr, double px, double py, d
     }
 }
 
-/* d lam_i / d corners; lam_i = cross(V_{i+2} - V_{i+1}, p - V_{i+1}) / A2 */
+/* d lam_i / d corners.  Hard fragment: lam_i = cross(V_{i+2} - V_{i+1}, p - V_{i+1}) / A2.
+   Soft fragment on an edge: lam_P = 1 - s, lam_Q = s, s = (p - P).(Q - P) / |Q - P|^2.
+   Soft fragment at a corner: constant. */
 static void lam_grad(const face_t *t, const frag_t *fr, double px, double py, const double glam[3],
                      corner_grad_t *cg)
 {
+    if (!fr->hard) {
+        if (fr->feat >= 3) return;
+        int P = fr->segP, Q = fr->segQ;
+        double ex = t->X[Q] - t->X[P], ey = t->Y[Q] - t->Y[P];
+        double dx = px - t->X[P], dy = py - t->Y[P];
+        double ee = ex * ex + ey * ey, s = fr->segt;
+        double gs = glam[Q] - glam[P];
+        /* ds/dd = e/ee, ds/de = (d - 2 s e)/ee; d = p - P, e = Q - P */
+        double gex = (dx - 2 * s * ex) / ee, gey = (dy - 2 * s * ey) / ee;
+        double gdx = ex / ee, gdy = ey / ee;
+        cg->X[Q] += gs * gex; cg->Y[Q] += gs * gey;
+        cg->X[P] += gs * (-gex - gdx); cg->Y[P] += gs * (-gey - gdy);
+        return;
+    }
     double gA2 = 0;
     for (int i = 0; i < 3; ++i) {
         int A = (i + 1) % 3, B = (i + 2) % 3;

@@ -113,6 +113,37 @@ def test_single_triangle_alpha_is_sigmoid_of_distance():
     np.testing.assert_allclose(out["dist"][0][cand.reshape(H, W)] * W, sd[cand], atol=2.5e-5)
 
 
+def test_soft_fragment_takes_attributes_of_nearest_boundary_point():
+    """K = 1, E = 1, w = 1 (so perspective weights are screen-linear): a soft fragment
+    has the colour of the closest point of the hard face, found here by dense sampling
+    of the boundary."""
+    W = H = 20
+    tri = [(4.0, 3.0), (15.0, 6.0), (6.0, 16.0)]
+    col = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    s = pixel_scene(pixel_mesh(tri, [(0, 1, 2)], W, H, col=col), W, H, K=1, r=3.0 / W, sigma=1.0 / W,
+                    delta=3.0 / W, edge_mode=1)
+    out = _render(s)
+    n = 100001
+    t = np.linspace(0, 1, n)
+    samples, cols = [], []
+    for i in range(3):
+        a, b = np.asarray(tri[i]), np.asarray(tri[(i + 1) % 3])
+        samples.append(a[None] + t[:, None] * (b - a)[None])
+        cols.append((1 - t)[:, None] * col[i][None] + t[:, None] * col[(i + 1) % 3][None])
+    samples, cols = np.concatenate(samples), np.concatenate(cols)
+    checked = 0
+    for y in range(H):
+        for x in range(W):
+            if out["ids"][0, y, x] < 0 or out["hard"][0, y, x]:
+                continue
+            p = np.array([x + 0.5, y + 0.5])
+            j = np.argmin(((samples - p) ** 2).sum(1))
+            # sample spacing <= 1.5e-4 px along an edge; colours change by <= 1 per edge length
+            np.testing.assert_allclose(out["rgba"][y, x, :3], cols[j], atol=2e-5)
+            checked += 1
+    assert checked > 40
+
+
 def test_sigma_to_zero_recovers_hard_stencil():
     """As sigma -> 0 the silhouette equals S^H, because Shift puts every hard face in layer 1."""
     s = synth.config1()
