@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Throughput of the HardSoftRas forward + adjoint hot path on GB300.
+
+One step = forward (store layer ids) + L2 pixel gradient + adjoint over a
+batch of views, all in libdressi kernels, inputs resident in HBM.  Default
+workload: the batched multi-view configuration (64 views of 512^2 of a
+20,480-triangle displaced UV sphere with a 1024^2 FP32 texture, Lambert
+shading, K = 3, r = 2 px, sigma = r/7, delta = r).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "fwd+bwd Mpixel*views/s"
+UNIT = "Mpixel*views/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def workload_scene(rank=0, world=1, n_views=64, res=512):
+    """Batched multi-view workload; with several ranks every rank renders its own
+    64 views (Fibonacci directions strided over ranks): weak scaling."""
+    s = synth.config3(n_views=n_views * world, res=res)
+    s.views = s.views[rank::world]
+    return s
+
+
+def workload_desc(s):
+    m = s.meshes[0]
+    return {"workload": "batched multi-view: %d views x %dx%d, %d-tri displaced UV sphere, %dx%d FP32 texture, "
+                        "Lambert, K=%d, r=2px" % (len(s.views), s.views[0].width, s.views[0].height,
+                                                   m.faces.shape[0], m.tex.shape[1], m.tex.shape[0], s.params.K),
+            "views": len(s.views), "resolution": s.views[0].width, "triangles": int(m.faces.shape[0]),
+            "texture": int(m.tex.shape[0]), "K": s.params.K, "store_layers": True,
+            "l2": "512 MiB buffer written between timed steps"}
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ----------------------------------------------------------------------------
+def time_oracle(scene, n_views, seed=0):
+    import oracle
+    rng = np.random.default_rng(seed)
+    px = 0
+    t0 = time.perf_counter()
+    for v in scene.views[:n_views]:
+        m = scene.meshes[v.mesh]
+        oracle.render(m, v, scene.params)
+        g = rng.normal(size=(v.height, v.width, 4))
+        oracle.backward(m, v, scene.params, g)
+        px += v.width * v.height
+    dt = time.perf_counter() - t0
+    return px, dt
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    s = workload_scene(0, 1)
+    views_per_step = 1
+    for _ in range(args.warmup):
+        time_oracle(s, views_per_step)
+    times, pxs = [], 0
+    for k in range(args.steps):
+        sub = synth.Scene(s.name, s.meshes, s.views[k % len(s.views):][:views_per_step], s.params)
+        px, dt = time_oracle(sub, views_per_step, seed=k)
+        times.append(dt)
+        pxs += px
+    total = sum(times)
+    value = pxs / total / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_desc(s),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{views_per_step} view(s) of {s.views[0].width}^2 per step, FP64 C oracle "
+                                       "(bbox pre-test), single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def algorithmic_bytes(scene, K, backward):
+    """Bytes one launch of the per-tile kernel must move at minimum (store-layer mode):
+    forward: RGBA out 16 B + K layer ids 4 B per pixel; per view the vertex records
+    (32 B) and faces (12 B); the texture once (16 B/texel).
+    adjoint: dL/dI 16 B + K ids 4 B per pixel; per view vertex records, faces and the
+    screen-gradient accumulators (16 B read + 16 B written per vertex); texture read
+    once and the texel gradient read + written once (2 x 16 B/texel)."""
+    m = scene.meshes[0]
+    V, F = m.pos.shape[0], m.faces.shape[0]
+    texels = m.tex.shape[0] * m.tex.shape[1]
+    px = scene.pixels
+    per_view = len(scene.views) * (32 * V + 12 * F)
+    if not backward:
+        return px * (16 + 4 * K) + per_view + 16 * texels
+    return px * (16 + 4 * K) + per_view + len(scene.views) * 32 * V + 3 * 16 * texels
+
+
+def ours(args, rank, world, local_rank):
+    import ctypes as C
+
+    import torch
+
+    from paper_2204_01386_gb300 import PackedScene, Renderer
+    from paper_2204_01386_gb300 import binding as B
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    s = workload_scene(rank, world)
+    tgt_scene = synth.perturbed(s, 4321 + rank)
+    ps = PackedScene(s.meshes, dev)
+    r = Renderer(ps, s.views, s.params)
+    # target images (inputs of the loss), rendered once outside the timed region
+    pt = PackedScene(tgt_scene.meshes, dev)
+    rt = Renderer(pt, tgt_scene.views, tgt_scene.params)
+    target, _ = rt.forward(store_layers=False)
+    torch.cuda.synchronize()
+    del rt, pt
+    lib = B.load()
+    n_pix = r.n_pix
+    out = torch.empty(n_pix, 4, device=dev)
+    ids = torch.empty(s.params.K, n_pix, dtype=torch.int32, device=dev)
+    grad = torch.empty_like(out)
+    loss = torch.zeros(1, device=dev)
+    gp = torch.empty(3, ps.n_verts_total, device=dev)
+    gt = torch.empty(ps.n_texels, 4, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+
+    def step():
+        r.forward(store_layers=True, out=out, ids=ids)
+        loss.zero_()
+        r.l2_grad(out, target, grad, loss)
+        r.backward(grad, ids=ids, grad_pos=gp, grad_tex=gt)
+        if world > 1:
+            dist.all_reduce(gp)
+            dist.all_reduce(gt)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert (r.device_status() & ~1) == 0, r.device_status()
+
+    stream = torch.cuda.current_stream(dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    for e in ev:
+        for x in e:
+            x.record(stream)
+    torch.cuda.synchronize()
+    launches0 = lib.dressi_launch_count()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e = ev[k]
+        lib.dressi_set_profile_events(C.c_void_p(e[2].cuda_event), C.c_void_p(e[3].cuda_event),
+                                      C.c_void_p(e[4].cuda_event), C.c_void_p(e[5].cuda_event))
+        e[0].record(stream)
+        step()
+        e[1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clock_info = clocks.stop()
+    lib.dressi_set_profile_events(None, None, None, None)
+    launches = lib.dressi_launch_count() - launches0
+    step_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    fwd_ms = [e[2].elapsed_time(e[3]) for e in ev]
+    bwd_ms = [e[4].elapsed_time(e[5]) for e in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    px_all = s.pixels * world * args.steps
+    value = px_all / (total_ms * 1e-3) / 1e6
+
+    # dominant kernel roofline (live CUDA-event durations of the per-tile kernels)
+    import json as _json
+    peaks = {}
+    try:
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    fwd_avg, bwd_avg = statistics.mean(fwd_ms), statistics.mean(bwd_ms)
+    bwd_dom = bwd_avg >= fwd_avg
+    kb = algorithmic_bytes(s, s.params.K, bwd_dom)
+    dur = (bwd_avg if bwd_dom else fwd_avg) * 1e-3
+    achieved = kb / dur / 1e9
+    roofline = {"kernel": "k_tile<3,%s>" % ("bwd" if bwd_dom else "fwd"), "bound": "hbm", "achieved": achieved,
+                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback",
+                "fwd_tile_ms": fwd_avg, "bwd_tile_ms": bwd_avg, "algorithmic_bytes": kb}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_pos = ps.pos.cpu().pin_memory()
+        h_tex = ps.tex.cpu().pin_memory()
+        h_tgt = target.cpu().pin_memory()
+        h_loss = torch.empty(1).pin_memory()
+        h_gp = torch.empty_like(gp, device="cpu").pin_memory()
+        h_gt = torch.empty_like(gt, device="cpu").pin_memory()
+        h2d = h_pos.numel() * 4 + h_tex.numel() * h_tex.element_size() + h_tgt.numel() * 4
+        d2h = 4 + h_gp.numel() * 4 + h_gt.numel() * 4
+
+        def e2e_step():
+            ps.pos.copy_(h_pos, non_blocking=True)
+            ps.tex.copy_(h_tex, non_blocking=True)
+            target.copy_(h_tgt, non_blocking=True)
+            step()
+            h_loss.copy_(loss, non_blocking=True)
+            h_gp.copy_(gp, non_blocking=True)
+            h_gt.copy_(gt, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        n_e2e = max(3, args.steps // 2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_e2e):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        e2e = {"value": s.pixels * world * n_e2e / (ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": n_e2e}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nv = args.cpu_views
+        px, dt = time_oracle(s, nv)
+        cpu = {"value": px / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nv} of {len(s.views)} views ({s.views[0].width}^2), forward + adjoint, FP64 C oracle, "
+                         f"single thread, {dt:.1f} s"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_desc(s), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clock_info}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-views", type=int, default=12)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * dressi.h -- C ABI of the GB300 HardSoftRas forward / adjoint library (libdressi.so).
+ *
+ * HardSoftRas is the soft rasterizer of "Dressi: A Hardware-Agnostic
+ * Differentiable Renderer with Reactive Shader Packing and Soft Rasterization"
+ * (arXiv 2204.01386), Sec. 3.3.  One call renders (or back-propagates through)
+ * a ragged batch of views, each view showing one mesh of a packed scene:
+ *
+ *   transform and triangle setup      (Sec. 3.3.2; the render-graph listing's
+ *                                      vertex transform and face lookup)
+ *   per-tile binning of faces grown by r   (Enlarge(), Sec. 3.3.2)
+ *   SignedDist, hard test, Shift, K-layer peel  (Alg. 2, Eq. Shift)
+ *   perspective-correct interpolation, bilinear texture, shading  (Sec. 3.2.2, 3.3.3)
+ *   D_k = sigmoid(dist_k / sigma), edge mask E, colour and silhouette blend
+ *                                      (the three blend equations of Sec. 3.3.3)
+ *   adjoint of all of the above back to vertex positions, vertex colours and
+ *   texels (Sec. 3.3: the gradient dL/dTheta by the chain rule).
+ *
+ * Conventions shared by every entry point
+ *   - Screen space: pixel (x, y) has its centre at (x + 1/2, y + 1/2); the
+ *     vertex with clip coordinates c lands at X = (c.x/c.w + 1)/2 * W,
+ *     Y = (c.y/c.w + 1)/2 * H (y down), depth c.z/c.w must lie in [0, 1].
+ *     Distances handed to sigmoid and Shift are pixel distances / max(W, H)
+ *     (the paper's [0, 1] screen units); r, sigma, delta are in those units.
+ *   - Ownership: every buffer is owned by the caller.  The library never
+ *     allocates device memory; all scratch space lives in the caller's
+ *     workspace `ws` (size from dressi_workspace_size).
+ *   - Execution: all work is enqueued on `stream` (a cudaStream_t; NULL =
+ *     legacy default stream).  No call synchronises the host, so calls can be
+ *     captured into a CUDA graph.
+ *   - Return codes are synchronous argument checks (DRESSI_*).  Faults found
+ *     on the device are OR-ed into `*dev_status` (DRESSI_DEV_* bits); nothing
+ *     on the device traps or asserts.
+ */
+#ifndef DRESSI_H
+#define DRESSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* exported from libdressi.so (built with hidden visibility by default) */
+#if defined(__GNUC__)
+#define DRESSI_API __attribute__((visibility("default")))
+#else
+#define DRESSI_API
+#endif
+
+#define DRESSI_ABI_VERSION 1
+#define DRESSI_MAX_K 5          /* the paper keeps K at most five (Sec. 3.3.2) */
+#define DRESSI_MAX_VIEWS 65535
+#define DRESSI_MAX_MESHES 4096
+
+/* synchronous return codes */
+#define DRESSI_OK 0
+#define DRESSI_ERR_ARG 1        /* invalid argument (null pointer, bad size, bad mode) */
+#define DRESSI_ERR_WORKSPACE 2  /* ws NULL or ws_bytes below dressi_workspace_size() */
+#define DRESSI_ERR_LAUNCH 3     /* a CUDA launch failed (cudaGetLastError) */
+
+/* device status bits, OR-ed into *dev_status */
+#define DRESSI_DEV_TILE_OVERFLOW 1  /* a tile list exceeded list_cap; that tile fell back to
+                                       scanning every face of its view (results stay exact) */
+#define DRESSI_DEV_FACE_RANGE 2     /* a face referenced a vertex outside its mesh; face skipped */
+#define DRESSI_DEV_NONFINITE 4      /* a vertex transformed to a non-finite position; its faces skipped */
+
+#define DRESSI_TEX_F32 0
+#define DRESSI_TEX_F16 1
+
+/* One mesh of the packed scene (host struct). */
+typedef struct {
+    int32_t n_verts;      /* vertices of this mesh */
+    int32_t n_faces;      /* faces of this mesh */
+    int64_t vert_off;     /* first vertex in the packed vertex planes */
+    int64_t face_off;     /* first face in the packed face array */
+    int64_t tex_off;      /* first texel in the packed texture buffer (ignored without texture) */
+    int32_t tex_w, tex_h; /* texture size in texels (0 without texture) */
+} dressi_mesh;
+
+/* Packed ragged scene.  The struct and `meshes` live in HOST memory; the data
+   pointers are DEVICE pointers (caller-owned, read only). */
+typedef struct {
+    int32_t n_meshes;
+    const dressi_mesh *meshes;   /* host array [n_meshes] */
+    int64_t n_verts_total;       /* length of one vertex plane */
+    const float *pos;            /* [3][n_verts_total] planar x, y, z (object space) */
+    const float *col;            /* [3][n_verts_total] planar r, g, b; NULL unless shade_mode 0 */
+    const float *uv;             /* [2][n_verts_total] planar u, v; NULL for shade_mode 0 */
+    const int32_t *faces;        /* [sum n_faces][3] vertex indices local to the face's mesh */
+    const void *tex;             /* [sum texels][4] RGBx texels (row-major per mesh, v = 0 at row 0) */
+    int32_t tex_dtype;           /* DRESSI_TEX_F32 or DRESSI_TEX_F16 */
+} dressi_scene;
+
+/* One view (host struct, passed as a host array). */
+typedef struct {
+    float mvp[16];      /* row-major 4x4, clip = mvp * (x, y, z, 1) */
+    float light[3];     /* unit vector towards a directional light (shade_mode 2) */
+    int32_t mesh;       /* index into scene->meshes */
+    int32_t width, height;
+    int64_t pix_off;    /* first pixel of this view in the packed image buffers; the view
+                           occupies pixels [pix_off, pix_off + width*height), row-major */
+} dressi_view;
+
+/* Soft-raster parameters (Sec. 3.3.2-3.3.3) and execution choices. */
+typedef struct {
+    int32_t K;          /* peel layers, 1..DRESSI_MAX_K (Alg. 2) */
+    float r;            /* blur radius: faces grow to reach r (Enlarge) */
+    float sigma;        /* sigmoid scale of D_k; the paper's default is r / 7 */
+    float delta;        /* edge-mask width; window radius rho = max(1, round(delta * max(W, H))) px */
+    float gamma;        /* accepted for interface compatibility; unused (the paper drops depth
+                           from the colour blend) */
+    int32_t edge_mode;  /* 0 edge mask from S^H, 1 E = 1 everywhere (SoftRas-like), 2 E = 0 (hard) */
+    int32_t shade_mode; /* 0 vertex colour, 1 unlit texture, 2 texture * max(0, n.l) */
+    int32_t texgrad_mode; /* 0 warp-aggregated atomics, 1 texel-space gather (deterministic) */
+    int32_t tile;       /* tile edge in pixels: 8, 16 or 32; 0 = 16 */
+    int64_t list_cap;   /* tile-list capacity in entries; 0 = library default (see header of
+                           dressi_workspace_size) */
+} dressi_params;
+
+/* Size in bytes of the workspace that dressi_forward / dressi_backward need for
+   this scene, view set and parameters (host-only computation; views is a host
+   array).  Returns 0 on invalid arguments. */
+DRESSI_API size_t dressi_workspace_size(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
+                             const dressi_params *params);
+
+/* Forward pass (Alg. 2 and the blend equations of Sec. 3.3.3).
+     out_rgba   DEVICE [n_pix][4] float: colour I_c in rgb, silhouette I_s in alpha,
+                at the views' pixel offsets.  Pixels of no view are left untouched.
+     layer_ids  DEVICE [K][n_pix] int32 or NULL: face index (local to the view's mesh) of
+                each peel layer, -1 where a layer is empty.  Pass it to dressi_backward
+                to skip re-rasterization; NULL keeps nothing between the passes.
+     n_pix      total pixels of the packed image buffers (>= every pix_off + W*H).
+     ws         DEVICE workspace of ws_bytes >= dressi_workspace_size(...).
+     dev_status DEVICE int32, OR-ed with DRESSI_DEV_* bits (never cleared by the library).
+     stream     cudaStream_t. */
+DRESSI_API int dressi_forward(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
+                   const dressi_params *params, float *out_rgba, int32_t *layer_ids, int64_t n_pix,
+                   void *ws, size_t ws_bytes, int32_t *dev_status, void *stream);
+
+/* Adjoint of dressi_forward for the pixel gradient grad_rgba = dL/d(out_rgba).
+     grad_rgba  DEVICE [n_pix][4] float.
+     layer_ids  DEVICE [K][n_pix] from dressi_forward with the same inputs, or NULL to
+                recompute layers and barycentrics (checkpointing).
+     grad_pos   DEVICE [3][n_verts_total] float, OVERWRITTEN with dL/dpos summed over views.
+     grad_col   DEVICE [3][n_verts_total] float or NULL, OVERWRITTEN (shade_mode 0).
+     grad_tex   DEVICE [sum texels][4] float or NULL, OVERWRITTEN (shade_mode 1, 2); channel 3
+                stays zero.  Always FP32, also for an FP16 texture.
+   Discrete quantities (layer choice, hard flags, S^H, E, depth keys) carry no gradient. */
+DRESSI_API int dressi_backward(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
+                    const dressi_params *params, const float *grad_rgba, const int32_t *layer_ids,
+                    int64_t n_pix, float *grad_pos, float *grad_col, float *grad_tex,
+                    void *ws, size_t ws_bytes, int32_t *dev_status, void *stream);
+
+/* L2 loss helper for training loops: grad[i] = 2 (out[i] - target[i]) over n floats and
+   *loss_accum += sum (out - target)^2 (DEVICE float, accumulated atomically). */
+DRESSI_API int dressi_l2_loss_grad(const float *out, const float *target, int64_t n, float *grad,
+                        float *loss_accum, void *stream);
+
+/* Static description of a synchronous return code (DRESSI_OK .. DRESSI_ERR_LAUNCH). */
+DRESSI_API const char *dressi_status_string(int code);
+
+/* Static description of one DRESSI_DEV_* bit of *dev_status. */
+DRESSI_API const char *dressi_dev_status_string(int bit);
+
+/* Profiling hook (no counterpart in the paper): when set, each pass records
+   `begin` / `end` (cudaEvent_t handles, caller-owned) on its stream right
+   before and after its per-tile kernel, so a caller can time that kernel with
+   cudaEventElapsedTime.  fwd_* are used by dressi_forward, bwd_* by
+   dressi_backward; NULL disables.  Process-wide setting, not thread safe. */
+DRESSI_API int dressi_set_profile_events(void *fwd_begin, void *fwd_end, void *bwd_begin, void *bwd_end);
+
+/* Number of kernels this library has launched since it was loaded (process-wide). */
+DRESSI_API unsigned long long dressi_launch_count(void);
+
+/* DRESSI_ABI_VERSION of the loaded library. */
+DRESSI_API int dressi_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DRESSI_H */

@@ -1,0 +1,359 @@
+// dressi_api.cu -- the extern "C" entry points declared in include/dressi.h:
+// argument checks, workspace layout, upload of the view / mesh tables into the
+// workspace, and the order of the kernel launches of one pass.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "dressi_core.cuh"
+#include "dressi_launch.h"
+
+namespace dressi {
+
+constexpr int TILE_DEFAULT = 16;
+constexpr int RHO_LIMIT = 8;
+constexpr size_t ALIGN = 256;
+
+static size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+// optional events recorded around the per-tile kernel (profiling hook)
+static cudaEvent_t g_prof[4] = {nullptr, nullptr, nullptr, nullptr};
+
+static void launch_tile_profiled(const Globals &g, bool bwd, cudaStream_t s)
+{
+    cudaEvent_t b = g_prof[bwd ? 2 : 0], e = g_prof[bwd ? 3 : 1];
+    if (b) cudaEventRecord(b, s);
+    launch_tile(g, bwd, s);
+    if (e) cudaEventRecord(e, s);
+}
+
+struct Layout {
+    size_t views, meshes, vrec, tile_count, tile_off, tile_cursor, lists, nrm, nrm_sum, sgrad, ngrad, total;
+    long long n_vrec;
+    int total_tiles;
+    long long list_cap;
+};
+
+struct Plan {
+    std::vector<ViewK> views;
+    std::vector<MeshK> meshes;
+    Layout lay;
+    int max_nv = 0, max_nf = 0, max_nv_view = 0, max_nf_view = 0;
+    long long n_texels = 0;
+};
+
+static bool check_params(const dressi_params *p)
+{
+    if (!p) return false;
+    if (p->K < 1 || p->K > DRESSI_MAX_K) return false;
+    if (!(p->r >= 0.f) || !(p->sigma > 0.f) || !(p->delta >= 0.f) || !std::isfinite(p->r) ||
+        !std::isfinite(p->sigma) || !std::isfinite(p->delta))
+        return false;
+    if (p->edge_mode < 0 || p->edge_mode > 2) return false;
+    if (p->shade_mode < 0 || p->shade_mode > 2) return false;
+    if (p->texgrad_mode < 0 || p->texgrad_mode > 1) return false;
+    if (p->tile != 0 && p->tile != TILE_DEFAULT) return false;
+    if (p->list_cap < 0) return false;
+    return true;
+}
+
+// Builds the host-side tables and the workspace layout; false on invalid arguments.
+static bool make_plan(const dressi_scene *sc, const dressi_view *views, int n_views, const dressi_params *p,
+                      long long n_pix, Plan &P)
+{
+    if (!sc || !views || !check_params(p)) return false;
+    if (n_views < 1 || n_views > DRESSI_MAX_VIEWS) return false;
+    if (sc->n_meshes < 1 || sc->n_meshes > DRESSI_MAX_MESHES || !sc->meshes) return false;
+    if (sc->n_verts_total < 0 || sc->tex_dtype < 0 || sc->tex_dtype > 1) return false;
+    const bool textured = p->shade_mode != 0;
+    P.meshes.resize(sc->n_meshes);
+    for (int m = 0; m < sc->n_meshes; ++m) {
+        const dressi_mesh &dm = sc->meshes[m];
+        if (dm.n_verts < 0 || dm.n_faces < 0 || dm.vert_off < 0 || dm.face_off < 0) return false;
+        if (dm.vert_off + dm.n_verts > sc->n_verts_total) return false;
+        MeshK &k = P.meshes[m];
+        k.vert_off = dm.vert_off;
+        k.face_off = dm.face_off;
+        k.tex_off = dm.tex_off;
+        k.nV = dm.n_verts;
+        k.nF = dm.n_faces;
+        k.tex_w = dm.tex_w;
+        k.tex_h = dm.tex_h;
+        if (textured) {
+            if (dm.tex_w <= 0 || dm.tex_h <= 0 || dm.tex_off < 0) return false;
+            P.n_texels = std::max(P.n_texels, (long long)dm.tex_off + (long long)dm.tex_w * dm.tex_h);
+        }
+        P.max_nv = std::max(P.max_nv, dm.n_verts);
+        P.max_nf = std::max(P.max_nf, dm.n_faces);
+    }
+    if (!sc->pos || !sc->faces) return false;
+    if (p->shade_mode == 0 && !sc->col) return false;
+    if (textured && (!sc->uv || !sc->tex)) return false;
+
+    P.views.resize(n_views);
+    long long vrec = 0, view_faces = 0;
+    int tiles = 0;
+    const int T = TILE_DEFAULT;
+    for (int v = 0; v < n_views; ++v) {
+        const dressi_view &dv = views[v];
+        if (dv.mesh < 0 || dv.mesh >= sc->n_meshes) return false;
+        if (dv.width < 1 || dv.height < 1 || dv.width > 32768 || dv.height > 32768) return false;
+        if (dv.pix_off < 0 || dv.pix_off + (long long)dv.width * dv.height > n_pix) return false;
+        for (int i = 0; i < 16; ++i)
+            if (!std::isfinite(dv.mvp[i])) return false;
+        ViewK &k = P.views[v];
+        std::memcpy(k.mvp, dv.mvp, sizeof(k.mvp));
+        std::memcpy(k.light, dv.light, sizeof(k.light));
+        k.mesh = dv.mesh;
+        k.W = dv.width;
+        k.H = dv.height;
+        k.tiles_x = (dv.width + T - 1) / T;
+        k.tiles_y = (dv.height + T - 1) / T;
+        k.tile_base = tiles;
+        const double S = (double)std::max(dv.width, dv.height);
+        int rho = (int)std::lround((double)p->delta * S);
+        if (rho < 1) rho = 1;
+        if (p->edge_mode == 0 && rho > RHO_LIMIT) return false;
+        k.rho = rho;
+        k.r_px = (float)((double)p->r * S);
+        k.inv_sigma_px = (float)(1.0 / ((double)p->sigma * S));
+        k.half_inv_S = (float)(0.5 / S);
+        k.bin_R = std::max(k.r_px, p->edge_mode == 0 ? (float)rho : 0.f) + 1.0f;
+        k.pad = 0;
+        k.pix_off = dv.pix_off;
+        k.vrec_off = vrec;
+        const MeshK &mk = P.meshes[dv.mesh];
+        vrec += mk.nV;
+        view_faces += mk.nF;
+        P.max_nv_view = std::max(P.max_nv_view, mk.nV);
+        P.max_nf_view = std::max(P.max_nf_view, mk.nF);
+        long long nt = (long long)tiles + (long long)k.tiles_x * k.tiles_y;
+        if (nt > 0x7fffffff) return false;
+        tiles = (int)nt;
+    }
+    Layout &L = P.lay;
+    L.n_vrec = vrec;
+    L.total_tiles = tiles;
+    L.list_cap = p->list_cap > 0 ? p->list_cap : std::max<long long>(4 * view_faces, 64LL * tiles);
+    if (L.list_cap > 0x7fffffffLL) L.list_cap = 0x7fffffffLL;
+    size_t o = 0;
+    L.views = o; o = align_up(o + sizeof(ViewK) * n_views);
+    L.meshes = o; o = align_up(o + sizeof(MeshK) * sc->n_meshes);
+    L.vrec = o; o = align_up(o + sizeof(VRec) * (size_t)std::max<long long>(vrec, 1));
+    L.tile_count = o; o = align_up(o + sizeof(int) * (size_t)tiles);
+    L.tile_off = o; o = align_up(o + sizeof(int) * (size_t)(tiles + 1));
+    L.tile_cursor = o; o = align_up(o + sizeof(int) * (size_t)tiles);
+    L.lists = o; o = align_up(o + sizeof(int) * (size_t)L.list_cap);
+    const size_t nv = (size_t)std::max<long long>(sc->n_verts_total, 1);
+    L.nrm = o; o = align_up(o + sizeof(float4) * nv);
+    L.nrm_sum = o; o = align_up(o + sizeof(float4) * nv);
+    L.sgrad = o; o = align_up(o + sizeof(float4) * (size_t)std::max<long long>(vrec, 1));
+    L.ngrad = o; o = align_up(o + sizeof(float4) * nv);
+    L.total = o;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// table upload: the tables travel as kernel parameters (no host-to-device copy,
+// so a whole pass can be captured into a CUDA graph)
+// ---------------------------------------------------------------------------
+constexpr int BLOB_WORDS = 4000;
+struct Blob {
+    unsigned int n;
+    unsigned int w[BLOB_WORDS];
+};
+
+__global__ void k_upload(const __grid_constant__ Blob b, unsigned int *dst)
+{
+    for (unsigned int i = threadIdx.x; i < b.n; i += blockDim.x) dst[i] = b.w[i];
+}
+
+static void upload(const void *src, size_t bytes, void *dst, cudaStream_t s)
+{
+    const unsigned int *w = static_cast<const unsigned int *>(src);
+    size_t words = bytes / 4;
+    unsigned int *d = static_cast<unsigned int *>(dst);
+    Blob b;
+    while (words > 0) {
+        const size_t n = std::min<size_t>(words, BLOB_WORDS);
+        b.n = (unsigned int)n;
+        std::memcpy(b.w, w, n * 4);
+        k_upload<<<1, 256, 0, s>>>(b, d);
+        count_launch(1);
+        w += n;
+        d += n;
+        words -= n;
+    }
+}
+
+static Globals make_globals(const dressi_scene *sc, const dressi_params *p, const Plan &P, char *ws,
+                            long long n_pix, int *status)
+{
+    Globals g;
+    std::memset(&g, 0, sizeof(g));
+    const Layout &L = P.lay;
+    g.views = reinterpret_cast<const ViewK *>(ws + L.views);
+    g.meshes = reinterpret_cast<const MeshK *>(ws + L.meshes);
+    g.n_views = (int)P.views.size();
+    g.K = p->K;
+    g.edge_mode = p->edge_mode;
+    g.shade_mode = p->shade_mode;
+    g.tile = TILE_DEFAULT;
+    g.tile_shift = 4;
+    g.tex_f16 = sc->tex_dtype == DRESSI_TEX_F16;
+    g.texgrad_mode = p->texgrad_mode;
+    g.n_verts_total = sc->n_verts_total;
+    g.n_pix = n_pix;
+    g.list_cap = L.list_cap;
+    g.total_tiles = L.total_tiles;
+    g.pos = sc->pos;
+    g.col = sc->col;
+    g.uv = sc->uv;
+    g.faces = sc->faces;
+    g.tex = sc->tex;
+    g.vrec = reinterpret_cast<VRec *>(ws + L.vrec);
+    g.tile_count = reinterpret_cast<int *>(ws + L.tile_count);
+    g.tile_off = reinterpret_cast<int *>(ws + L.tile_off);
+    g.tile_cursor = reinterpret_cast<int *>(ws + L.tile_cursor);
+    g.lists = reinterpret_cast<int *>(ws + L.lists);
+    g.nrm = reinterpret_cast<float4 *>(ws + L.nrm);
+    g.nrm_sum = reinterpret_cast<float4 *>(ws + L.nrm_sum);
+    g.sgrad = reinterpret_cast<float4 *>(ws + L.sgrad);
+    g.ngrad = reinterpret_cast<float4 *>(ws + L.ngrad);
+    g.status = status;
+    return g;
+}
+
+// setup shared by both passes: tables, vertex transform, normals, binning
+static void run_setup(const Globals &g, const Plan &P, char *ws, bool need_bins, cudaStream_t s)
+{
+    const Layout &L = P.lay;
+    upload(P.views.data(), sizeof(ViewK) * P.views.size(), ws + L.views, s);
+    upload(P.meshes.data(), sizeof(MeshK) * P.meshes.size(), ws + L.meshes, s);
+    launch_vertex(g, (int)P.views.size(), P.max_nv_view, s);
+    if (g.shade_mode == 2) {
+        cudaMemsetAsync(ws + L.nrm_sum, 0, sizeof(float4) * (size_t)std::max<long long>(g.n_verts_total, 1), s);
+        launch_normals(g, (int)P.meshes.size(), P.max_nf, s);
+    }
+    if (need_bins) {
+        cudaMemsetAsync(ws + L.tile_count, 0, sizeof(int) * (size_t)L.total_tiles, s);
+        cudaMemsetAsync(ws + L.tile_cursor, 0, sizeof(int) * (size_t)L.total_tiles, s);
+        launch_bin(g, (int)P.views.size(), P.max_nf_view, s);
+    }
+}
+
+}  // namespace dressi
+
+using namespace dressi;
+
+extern "C" {
+
+int dressi_abi_version(void) { return DRESSI_ABI_VERSION; }
+
+int dressi_set_profile_events(void *fwd_begin, void *fwd_end, void *bwd_begin, void *bwd_end)
+{
+    g_prof[0] = static_cast<cudaEvent_t>(fwd_begin);
+    g_prof[1] = static_cast<cudaEvent_t>(fwd_end);
+    g_prof[2] = static_cast<cudaEvent_t>(bwd_begin);
+    g_prof[3] = static_cast<cudaEvent_t>(bwd_end);
+    return DRESSI_OK;
+}
+
+unsigned long long dressi_launch_count(void) { return g_launches.load(); }
+
+const char *dressi_status_string(int code)
+{
+    switch (code) {
+    case DRESSI_OK: return "ok";
+    case DRESSI_ERR_ARG: return "invalid argument";
+    case DRESSI_ERR_WORKSPACE: return "workspace missing or too small";
+    case DRESSI_ERR_LAUNCH: return "CUDA launch failed";
+    default: return "unknown return code";
+    }
+}
+
+const char *dressi_dev_status_string(int bit)
+{
+    switch (bit) {
+    case 0: return "ok";
+    case DRESSI_DEV_TILE_OVERFLOW: return "tile list over capacity (exact fallback used)";
+    case DRESSI_DEV_FACE_RANGE: return "face index out of range (face skipped)";
+    case DRESSI_DEV_NONFINITE: return "non-finite vertex input (faces skipped)";
+    default: return "unknown device status bit";
+    }
+}
+
+size_t dressi_workspace_size(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
+                             const dressi_params *params)
+{
+    Plan P;
+    if (!make_plan(scene, views, n_views, params, (long long)1 << 62, P)) return 0;
+    return P.lay.total;
+}
+
+int dressi_forward(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
+                   const dressi_params *params, float *out_rgba, int32_t *layer_ids, int64_t n_pix, void *ws,
+                   size_t ws_bytes, int32_t *dev_status, void *stream)
+{
+    Plan P;
+    if (!out_rgba || !dev_status || n_pix < 1) return DRESSI_ERR_ARG;
+    if (!make_plan(scene, views, n_views, params, n_pix, P)) return DRESSI_ERR_ARG;
+    if (!ws || ws_bytes < P.lay.total) return DRESSI_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaGetLastError();
+    char *w = static_cast<char *>(ws);
+    Globals g = make_globals(scene, params, P, w, n_pix, dev_status);
+    g.out = out_rgba;
+    g.ids = layer_ids;
+    run_setup(g, P, w, true, s);
+    launch_tile_profiled(g, false, s);
+    return cudaGetLastError() == cudaSuccess ? DRESSI_OK : DRESSI_ERR_LAUNCH;
+}
+
+int dressi_backward(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
+                    const dressi_params *params, const float *grad_rgba, const int32_t *layer_ids, int64_t n_pix,
+                    float *grad_pos, float *grad_col, float *grad_tex, void *ws, size_t ws_bytes,
+                    int32_t *dev_status, void *stream)
+{
+    Plan P;
+    if (!grad_rgba || !grad_pos || !dev_status || n_pix < 1) return DRESSI_ERR_ARG;
+    if (!make_plan(scene, views, n_views, params, n_pix, P)) return DRESSI_ERR_ARG;
+    if (!ws || ws_bytes < P.lay.total) return DRESSI_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaGetLastError();
+    char *w = static_cast<char *>(ws);
+    Globals g = make_globals(scene, params, P, w, n_pix, dev_status);
+    g.gin = grad_rgba;
+    g.ids_in = layer_ids;
+    g.gpos = grad_pos;
+    g.gcol = params->shade_mode == 0 ? grad_col : nullptr;
+    g.gtex = params->shade_mode != 0 ? grad_tex : nullptr;
+    const long long nvt = scene->n_verts_total;
+    cudaMemsetAsync(grad_pos, 0, sizeof(float) * 3 * (size_t)nvt, s);
+    if (grad_col) cudaMemsetAsync(grad_col, 0, sizeof(float) * 3 * (size_t)nvt, s);
+    if (grad_tex && P.n_texels > 0) cudaMemsetAsync(grad_tex, 0, sizeof(float) * 4 * (size_t)P.n_texels, s);
+    cudaMemsetAsync(w + P.lay.sgrad, 0, sizeof(float4) * (size_t)std::max<long long>(P.lay.n_vrec, 1), s);
+    if (params->shade_mode == 2)
+        cudaMemsetAsync(w + P.lay.ngrad, 0, sizeof(float4) * (size_t)std::max<long long>(nvt, 1), s);
+    run_setup(g, P, w, layer_ids == nullptr, s);
+    launch_tile_profiled(g, true, s);
+    launch_vertex_bwd(g, (int)P.views.size(), P.max_nv_view, (int)P.meshes.size(), P.max_nf,
+                      params->shade_mode == 2, s);
+    return cudaGetLastError() == cudaSuccess ? DRESSI_OK : DRESSI_ERR_LAUNCH;
+}
+
+int dressi_l2_loss_grad(const float *out, const float *target, int64_t n, float *grad, float *loss_accum,
+                        void *stream)
+{
+    if (!out || !target || !grad || n < 0) return DRESSI_ERR_ARG;
+    cudaGetLastError();
+    if (n > 0) launch_l2(out, target, n, grad, loss_accum, static_cast<cudaStream_t>(stream));
+    return cudaGetLastError() == cudaSuccess ? DRESSI_OK : DRESSI_ERR_LAUNCH;
+}
+
+}  // extern "C"

@@ -1,0 +1,328 @@
+// dressi_core.cuh -- device-side data layout and the geometric core of HardSoftRas.
+//
+// Precision plan (GB300, FP32 pixel math):
+//   * the vertex transform runs in FP64 with explicitly rounded operations, and
+//     each pixel-space corner is kept as an unevaluated float pair hi + lo, so
+//     that p - V is accurate to one float ulp of |p - V| (not of |V|): the
+//     sigmoid of Sec. 3.3.3 is steep (sigma is a fraction of a pixel), so the
+//     distance must be accurate to ~1e-7 px even at 2048^2;
+//   * every geometric quantity of an edge is computed from its canonical
+//     (lexicographically smaller) endpoint, so two faces sharing an edge or a
+//     vertex get bit-identical distances and ties resolve by face id as in an
+//     exact evaluation;
+//   * the core uses __f*_rn intrinsics only, so the peel, the shading pass and
+//     the adjoint (separate kernels and call sites) reproduce identical values.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dressi.h"
+
+namespace dressi {
+
+constexpr int MAXK = DRESSI_MAX_K;
+constexpr int CHUNK = 128;   // faces staged in shared memory per round
+constexpr int FLAG_LIVE = 1 << 7;
+constexpr int FLAG_RANGE = 1 << 8;
+
+// ---------------------------------------------------------------------------
+// tables uploaded into the workspace
+// ---------------------------------------------------------------------------
+struct ViewK {
+    float mvp[16];
+    float light[3];
+    int mesh;
+    int W, H, tiles_x, tiles_y;
+    int tile_base;          // first global tile of this view
+    int rho;                // edge-mask window radius (pixels)
+    float r_px;             // r in pixels
+    float inv_sigma_px;     // 1 / (sigma in pixels)
+    float half_inv_S;       // 0.5 / max(W, H): soft key slope
+    float bin_R;            // bin growth radius in pixels (max(r_px, rho) + guard)
+    int pad;
+    long long pix_off;
+    long long vrec_off;     // first record of this view in the per-view vertex buffer
+};
+
+struct MeshK {
+    long long vert_off, face_off, tex_off;
+    int nV, nF, tex_w, tex_h;
+};
+
+// per (view, vertex): pixel-space position as float pairs, depth, 1/w
+struct __align__(16) VRec {
+    float xh, xl, yh, yl;
+    float z, iw;
+    int valid;   // w > 1e-6 and depth in [0, 1] and finite
+    int pad;
+};
+
+// per-face record used by every pixel evaluation
+struct FaceRec {
+    float xh[3], xl[3], yh[3], yl[3];
+    float invL[3];   // 1 / length of edge i (canonical)
+    float z[3];
+    float invA;      // 1 / |twice the signed area|
+    int flags;       // bit 0: orient > 0; bits 1-3: edge i swapped; bits 4-6: edge i owns;
+                     // FLAG_LIVE: not culled; FLAG_RANGE: a vertex index is out of range
+    int id;          // face index local to the mesh
+    int vi[3];       // vertex indices local to the mesh
+    float iw[3];     // 1 / w of the corners
+};
+
+struct Globals {
+    const ViewK *views;
+    const MeshK *meshes;
+    int n_views;
+    int K;
+    int edge_mode, shade_mode;
+    int tile;            // tile edge in pixels
+    int tile_shift;      // log2(tile)
+    int tex_f16;
+    int texgrad_mode;
+    long long n_verts_total;
+    long long n_pix;
+    long long list_cap;
+    int total_tiles;
+    int pad0;
+    const float *pos, *col, *uv;
+    const int *faces;
+    const void *tex;
+    VRec *vrec;
+    int *tile_count, *tile_off, *tile_cursor, *lists;
+    float4 *nrm;          // [n_verts_total] normalized vertex normals
+    float4 *nrm_sum;      // [n_verts_total] unnormalized sums
+    int *status;
+    // forward
+    float *out;
+    int *ids;             // [K][n_pix] or nullptr
+    // backward
+    const float *gin;
+    const int *ids_in;    // [K][n_pix] or nullptr (recompute)
+    float4 *sgrad;        // per (view, vertex): dX, dY, d(1/w)
+    float4 *ngrad;        // [n_verts_total] gradient of the normalized vertex normals
+    float *gpos, *gcol, *gtex;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool lex_less(float axh, float axl, float ayh, float ayl,
+                                         float bxh, float bxl, float byh, float byl)
+{
+    if (axh != bxh) return axh < bxh;
+    if (axl != bxl) return axl < bxl;
+    if (ayh != byh) return ayh < byh;
+    return ayl < byl;
+}
+
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// Builds the record of face f of mesh m as seen in the view whose vertex
+// records start at vr.  Returns false (live bit clear) for culled faces.
+__device__ __forceinline__ bool face_load(const Globals &g, const MeshK &m, const VRec *vr, int f,
+                                          FaceRec &R)
+{
+    R.id = f;
+    R.flags = 0;
+    if ((unsigned)f >= (unsigned)m.nF) {
+        R.flags = FLAG_RANGE;
+        return false;
+    }
+    const int *fv = g.faces + 3 * (m.face_off + f);
+    int v0 = __ldg(fv), v1 = __ldg(fv + 1), v2 = __ldg(fv + 2);
+    if ((unsigned)v0 >= (unsigned)m.nV || (unsigned)v1 >= (unsigned)m.nV || (unsigned)v2 >= (unsigned)m.nV) {
+        R.flags = FLAG_RANGE;
+        return false;
+    }
+    R.vi[0] = v0; R.vi[1] = v1; R.vi[2] = v2;
+    VRec a[3];
+    a[0] = vr[v0]; a[1] = vr[v1]; a[2] = vr[v2];
+    bool live = a[0].valid && a[1].valid && a[2].valid;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        R.xh[i] = a[i].xh; R.xl[i] = a[i].xl; R.yh[i] = a[i].yh; R.yl[i] = a[i].yl;
+        R.z[i] = a[i].z; R.iw[i] = a[i].iw;
+    }
+    // twice the signed area from accurate corner differences
+    float ux = fadd(fsub(a[1].xh, a[0].xh), fsub(a[1].xl, a[0].xl));
+    float uy = fadd(fsub(a[1].yh, a[0].yh), fsub(a[1].yl, a[0].yl));
+    float wx = fadd(fsub(a[2].xh, a[0].xh), fsub(a[2].xl, a[0].xl));
+    float wy = fadd(fsub(a[2].yh, a[0].yh), fsub(a[2].yl, a[0].yl));
+    float A2 = ffma(ux, wy, -fmul(uy, wx));
+    if (!(A2 != 0.f) || !isfinite(A2)) live = false;
+    bool orient = A2 > 0.f;
+    int flags = orient ? 1 : 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        int ia = i, ib = (i + 1) % 3;
+        bool sw = lex_less(a[ib].xh, a[ib].xl, a[ib].yh, a[ib].yl, a[ia].xh, a[ia].xl, a[ia].yh, a[ia].yl);
+        int P = sw ? ib : ia, Q = sw ? ia : ib;
+        float ex = fadd(fsub(a[Q].xh, a[P].xh), fsub(a[Q].xl, a[P].xl));
+        float ey = fadd(fsub(a[Q].yh, a[P].yh), fsub(a[Q].yl, a[P].yl));
+        float L = __fsqrt_rn(ffma(ex, ex, fmul(ey, ey)));
+        R.invL[i] = __fdiv_rn(1.f, L);
+        // oriented edge ia -> ib
+        float eox = sw ? -ex : ex, eoy = sw ? -ey : ey;
+        bool owns = orient ? (eoy < 0.f || (eoy == 0.f && eox > 0.f)) : (eoy > 0.f || (eoy == 0.f && eox < 0.f));
+        flags |= (sw ? 1 : 0) << (1 + i);
+        flags |= (owns ? 1 : 0) << (4 + i);
+    }
+    R.invA = __fdiv_rn(1.f, fabsf(A2));
+    if (live) flags |= FLAG_LIVE;
+    R.flags = flags;
+    return live;
+}
+
+// Result of evaluating one face at one pixel centre.
+struct Frag {
+    float dist;      // signed pixel distance (positive inside the hard face)
+    float key;       // Shift() key
+    float Fn[3];     // oriented edge numerators: lam_{(i+2)%3} = Fn[i] * invA
+    float t;         // soft fragment on edge `feat`: closest point = P + t (Q - P), canonical P, Q
+    int hard;
+    int feat;        // 0..2: edge i interior; 3..5: corner (feat - 3)
+};
+
+// SignedDist, candidate rule, hard test (top-left fill rule) and Shift (Eq. Shift) of
+// face R at pixel centre (px, py).  Returns false when the face is not a candidate
+// (farther than r_px outside).  Pure function of (R, px, py, r_px, half_inv_S).
+__device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, float r_px, float half_inv_S,
+                                          Frag &o)
+{
+    float dx[3], dy[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        dx[i] = fsub(fsub(px, R.xh[i]), R.xl[i]);
+        dy[i] = fsub(fsub(py, R.yh[i]), R.yl[i]);
+    }
+    const bool orient = R.flags & 1;
+    float c[3], F[3];
+    bool early_out = false;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const bool sw = (R.flags >> (1 + i)) & 1;
+        const int ia = i, ib = (i + 1) % 3;
+        const int P = sw ? ib : ia, Q = sw ? ia : ib;
+        // cross(Q - P, p - P) == cross(p - P, p - Q)
+        c[i] = ffma(dx[P], dy[Q], -fmul(dy[P], dx[Q]));
+        float fn = (orient != sw) ? c[i] : -c[i];
+        o.Fn[i] = fn;
+        F[i] = fmul(fn, R.invL[i]);
+        early_out |= F[i] < -r_px;
+    }
+    if (early_out) return false;
+    bool inside = true;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const bool owns = (R.flags >> (4 + i)) & 1;
+        inside &= (o.Fn[i] > 0.f) || (o.Fn[i] == 0.f && owns);
+    }
+    float dist, bt = 0.f;
+    int feat;
+    if (inside) {
+        dist = F[0]; feat = 0;
+        if (F[1] < dist) { dist = F[1]; feat = 1; }
+        if (F[2] < dist) { dist = F[2]; feat = 2; }
+    } else {
+        float best = 3.4e38f;
+        feat = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const bool sw = (R.flags >> (1 + i)) & 1;
+            const int ia = i, ib = (i + 1) % 3;
+            const int P = sw ? ib : ia, Q = sw ? ia : ib;
+            float ex = fsub(dx[P], dx[Q]), ey = fsub(dy[P], dy[Q]);   // V_Q - V_P
+            float tP = ffma(dx[P], ex, fmul(dy[P], ey));
+            float s, tt = 0.f;
+            int ft;
+            if (tP <= 0.f) {
+                s = __fsqrt_rn(ffma(dx[P], dx[P], fmul(dy[P], dy[P])));
+                ft = 3 + P;
+            } else {
+                float tQ = ffma(dx[Q], ex, fmul(dy[Q], ey));
+                if (tQ >= 0.f) {
+                    s = __fsqrt_rn(ffma(dx[Q], dx[Q], fmul(dy[Q], dy[Q])));
+                    ft = 3 + Q;
+                } else {
+                    s = fmul(fabsf(c[i]), R.invL[i]);
+                    ft = i;
+                    tt = __fdiv_rn(tP, ffma(ex, ex, fmul(ey, ey)));
+                }
+            }
+            if (s < best) { best = s; feat = ft; bt = tt; }
+        }
+        dist = -best;
+    }
+    if (!(dist >= -r_px)) return false;
+    o.dist = dist;
+    o.hard = inside;
+    o.feat = feat;
+    o.t = bt;
+    if (inside) {
+        // z(p) = sum lam_j z_j,  lam_{(i+2)%3} = Fn[i] / |A2|
+        float zs = ffma(o.Fn[1], R.z[0], ffma(o.Fn[2], R.z[1], fmul(o.Fn[0], R.z[2])));
+        o.key = fmul(0.5f, fmul(zs, R.invA));
+    } else {
+        o.key = ffma(-dist, half_inv_S, 0.5f);
+    }
+    return true;
+}
+
+// Hard test only (for S^H of halo pixels): true if p lies in the closed face under
+// the fill rule; hkey receives the Shift() key of the hard fragment.
+__device__ __forceinline__ bool hard_test(const FaceRec &R, float px, float py, float &hkey)
+{
+    float dx[3], dy[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        dx[i] = fsub(fsub(px, R.xh[i]), R.xl[i]);
+        dy[i] = fsub(fsub(py, R.yh[i]), R.yl[i]);
+    }
+    const bool orient = R.flags & 1;
+    float Fn[3];
+    bool inside = true;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const bool sw = (R.flags >> (1 + i)) & 1;
+        const int ia = i, ib = (i + 1) % 3;
+        const int P = sw ? ib : ia, Q = sw ? ia : ib;
+        float c = ffma(dx[P], dy[Q], -fmul(dy[P], dx[Q]));
+        Fn[i] = (orient != sw) ? c : -c;
+        const bool owns = (R.flags >> (4 + i)) & 1;
+        inside &= (Fn[i] > 0.f) || (Fn[i] == 0.f && owns);
+    }
+    if (!inside) return false;
+    float zs = ffma(Fn[1], R.z[0], ffma(Fn[2], R.z[1], fmul(Fn[0], R.z[2])));
+    hkey = fmul(0.5f, fmul(zs, R.invA));
+    return true;
+}
+
+__device__ __forceinline__ bool frag_less(float ka, int ia, float kb, int ib)
+{
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+// binary search of the view owning global tile t
+__device__ __forceinline__ int view_of_tile(const Globals &g, int t)
+{
+    int lo = 0, hi = g.n_views - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (g.views[mid].tile_base <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ float sigmoidf_stable(float x)
+{
+    if (x >= 0.f) return __fdiv_rn(1.f, 1.f + expf(-x));
+    float e = expf(x);
+    return __fdiv_rn(e, 1.f + e);
+}
+
+}  // namespace dressi

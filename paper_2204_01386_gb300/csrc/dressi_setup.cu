@@ -1,0 +1,318 @@
+// dressi_setup.cu -- per-vertex and per-face stages: FP64 vertex transform,
+// vertex normals, tile binning (count / scan / fill) and the per-vertex end of
+// the adjoint (screen -> clip -> object space, normals -> positions).
+#include "dressi_core.cuh"
+#include "dressi_launch.h"
+
+namespace dressi {
+
+// ---------------------------------------------------------------------------
+// vertex transform (render-graph listing: homogeneous position, MVP, face lookup)
+// clip = MVP (p, 1) in FP64 with each operation rounded as written, then
+// X = (x/w + 1)/2 W, Y = (y/w + 1)/2 H, depth z/w; stored as float pairs.
+// ---------------------------------------------------------------------------
+__global__ void k_vertex(Globals g)
+{
+    const ViewK &V = g.views[blockIdx.y];
+    const MeshK &M = g.meshes[V.mesh];
+    VRec *out = g.vrec + V.vrec_off;
+    const long long nvt = g.n_verts_total;
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M.nV; i += gridDim.x * blockDim.x) {
+        const long long gi = M.vert_off + i;
+        const double p0 = (double)__ldg(g.pos + gi), p1 = (double)__ldg(g.pos + nvt + gi),
+                     p2 = (double)__ldg(g.pos + 2 * nvt + gi);
+        double c[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float *m = V.mvp + 4 * r;
+            c[r] = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)m[0], p0), __dmul_rn((double)m[1], p1)),
+                                       __dmul_rn((double)m[2], p2)),
+                             (double)m[3]);
+        }
+        const double X = __dmul_rn(__dmul_rn(__dadd_rn(__ddiv_rn(c[0], c[3]), 1.0), 0.5), (double)V.W);
+        const double Y = __dmul_rn(__dmul_rn(__dadd_rn(__ddiv_rn(c[1], c[3]), 1.0), 0.5), (double)V.H);
+        const double Z = __ddiv_rn(c[2], c[3]);
+        VRec r;
+        r.xh = __double2float_rn(X);
+        r.xl = __double2float_rn(__dsub_rn(X, (double)r.xh));
+        r.yh = __double2float_rn(Y);
+        r.yl = __double2float_rn(__dsub_rn(Y, (double)r.yh));
+        r.z = __double2float_rn(Z);
+        r.iw = __double2float_rn(__ddiv_rn(1.0, c[3]));
+        const bool fin = isfinite(X) && isfinite(Y) && isfinite(Z);
+        r.valid = (c[3] > 1e-6) && (Z >= 0.0) && (Z <= 1.0) && fin && fabs(X) < 1e30 && fabs(Y) < 1e30;
+        r.pad = 0;
+        if (!(isfinite(p0) && isfinite(p1) && isfinite(p2))) bad = true;
+        out[i] = r;
+    }
+    if (bad) atomicOr(g.status, DRESSI_DEV_NONFINITE);
+}
+
+// ---------------------------------------------------------------------------
+// area-weighted vertex normals (listing BuildNormalCompute): m_v = sum of
+// (P1 - P0) x (P2 - P0) over the faces holding v, n_v = m_v / |m_v|
+// ---------------------------------------------------------------------------
+__global__ void k_normal_accum(Globals g)
+{
+    const MeshK &M = g.meshes[blockIdx.y];
+    const long long nvt = g.n_verts_total;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < M.nF; f += gridDim.x * blockDim.x) {
+        const int *fv = g.faces + 3 * (M.face_off + f);
+        int v[3] = {__ldg(fv), __ldg(fv + 1), __ldg(fv + 2)};
+        if ((unsigned)v[0] >= (unsigned)M.nV || (unsigned)v[1] >= (unsigned)M.nV || (unsigned)v[2] >= (unsigned)M.nV)
+            continue;
+        float P[3][3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) P[j][c] = __ldg(g.pos + c * nvt + M.vert_off + v[j]);
+        float u[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+        float w[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+        float4 a = make_float4(u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0], 0.f);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) atomicAdd(g.nrm_sum + M.vert_off + v[j], a);
+    }
+}
+
+__global__ void k_normal_finish(Globals g)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.n_verts_total;
+         i += (long long)gridDim.x * blockDim.x) {
+        float4 m = g.nrm_sum[i];
+        float l = sqrtf(m.x * m.x + m.y * m.y + m.z * m.z);
+        float s = l > 0.f ? 1.f / l : 0.f;
+        g.nrm[i] = make_float4(m.x * s, m.y * s, m.z * s, l);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tile binning: every live face goes into the list of each tile that its
+// bounding box, grown by bin_R pixels (r plus the edge-mask halo plus a guard),
+// touches.  pass 0 counts, pass 1 fills.  Order inside a list is irrelevant:
+// the peel keeps the K smallest (key, id) pairs.
+// ---------------------------------------------------------------------------
+template <int PASS>
+__global__ void k_bin(Globals g)
+{
+    const ViewK &V = g.views[blockIdx.y];
+    const MeshK &M = g.meshes[V.mesh];
+    const VRec *vr = g.vrec + V.vrec_off;
+    const int T = g.tile;
+    const float Tinv = 1.f / (float)T;
+    bool bad = false;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < M.nF; f += gridDim.x * blockDim.x) {
+        FaceRec R;
+        if (!face_load(g, M, vr, f, R)) {
+            if (R.flags & FLAG_RANGE) bad = true;
+            continue;
+        }
+        float x0 = fminf(R.xh[0], fminf(R.xh[1], R.xh[2])) - V.bin_R;
+        float x1 = fmaxf(R.xh[0], fmaxf(R.xh[1], R.xh[2])) + V.bin_R;
+        float y0 = fminf(R.yh[0], fminf(R.yh[1], R.yh[2])) - V.bin_R;
+        float y1 = fmaxf(R.yh[0], fmaxf(R.yh[1], R.yh[2])) + V.bin_R;
+        if (x1 < 0.f || y1 < 0.f || x0 > (float)V.W || y0 > (float)V.H) continue;
+        int tx0 = max(0, (int)floorf(x0 * Tinv)), tx1 = min(V.tiles_x - 1, (int)floorf(x1 * Tinv));
+        int ty0 = max(0, (int)floorf(y0 * Tinv)), ty1 = min(V.tiles_y - 1, (int)floorf(y1 * Tinv));
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) {
+                const int t = V.tile_base + ty * V.tiles_x + tx;
+                if (PASS == 0) {
+                    atomicAdd(g.tile_count + t, 1);
+                } else {
+                    const int slot = atomicAdd(g.tile_cursor + t, 1);
+                    const long long idx = (long long)g.tile_off[t] + slot;
+                    if (idx < g.list_cap) g.lists[idx] = f;
+                }
+            }
+    }
+    if (PASS == 0 && bad) atomicOr(g.status, DRESSI_DEV_FACE_RANGE);
+}
+
+// exclusive scan of the per-tile counts (one CTA of 1024 threads)
+__global__ void __launch_bounds__(1024) k_scan(Globals g)
+{
+    __shared__ long long warp_sums[32];
+    const int n = g.total_tiles;
+    const int tid = threadIdx.x;
+    const int per = (n + 1023) / 1024;
+    const int b = tid * per, e = min(n, b + per);
+    long long s = 0;
+    for (int i = b; i < e; ++i) s += g.tile_count[i];
+    // inclusive scan of s over the block
+    long long x = s;
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_sums[lane] = w;
+    }
+    __syncthreads();
+    long long run = x - s + (warp > 0 ? warp_sums[warp - 1] : 0);
+    for (int i = b; i < e; ++i) {
+        long long c = g.tile_count[i];
+        g.tile_off[i] = (int)min(run, (long long)0x7fffffff);
+        run += c;
+    }
+    if (tid == 1023) {
+        long long total = warp_sums[31];
+        g.tile_off[n] = (int)min(total, (long long)0x7fffffff);
+        if (total > g.list_cap) atomicOr(g.status, DRESSI_DEV_TILE_OVERFLOW);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// adjoint, per (view, vertex): (dX, dY, d(1/w)) -> clip -> object space
+// ---------------------------------------------------------------------------
+__global__ void k_vertex_bwd(Globals g)
+{
+    const ViewK &V = g.views[blockIdx.y];
+    const MeshK &M = g.meshes[V.mesh];
+    const float4 *sg = g.sgrad + V.vrec_off;
+    const long long nvt = g.n_verts_total;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M.nV; i += gridDim.x * blockDim.x) {
+        float4 s = sg[i];
+        if (s.x == 0.f && s.y == 0.f && s.z == 0.f) continue;
+        const long long gi = M.vert_off + i;
+        const float p[3] = {__ldg(g.pos + gi), __ldg(g.pos + nvt + gi), __ldg(g.pos + 2 * nvt + gi)};
+        float c[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float *m = V.mvp + 4 * r;
+            c[r] = m[0] * p[0] + m[1] * p[1] + m[2] * p[2] + m[3];
+        }
+        const float iw = 1.f / c[3];
+        const float hx = 0.5f * (float)V.W * iw, hy = 0.5f * (float)V.H * iw;
+        const float gcx = s.x * hx, gcy = s.y * hy;
+        const float gcw = -(s.x * hx * c[0] + s.y * hy * c[1]) * iw - s.z * iw * iw;
+#pragma unroll
+        for (int col = 0; col < 3; ++col) {
+            float gp = V.mvp[col] * gcx + V.mvp[4 + col] * gcy + V.mvp[12 + col] * gcw;
+            atomicAdd(g.gpos + col * nvt + gi, gp);
+        }
+    }
+}
+
+// normals -> positions: dm_v = (dn_v - n_v (n_v . dn_v)) / |m_v|; per face
+// da = sum of dm over its corners; a = u x w gives du = w x da, dw = da x u
+__global__ void k_normal_bwd(Globals g)
+{
+    const MeshK &M = g.meshes[blockIdx.y];
+    const long long nvt = g.n_verts_total;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < M.nF; f += gridDim.x * blockDim.x) {
+        const int *fv = g.faces + 3 * (M.face_off + f);
+        int v[3] = {__ldg(fv), __ldg(fv + 1), __ldg(fv + 2)};
+        if ((unsigned)v[0] >= (unsigned)M.nV || (unsigned)v[1] >= (unsigned)M.nV || (unsigned)v[2] >= (unsigned)M.nV)
+            continue;
+        float ga[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const long long gi = M.vert_off + v[j];
+            float4 n = g.nrm[gi];
+            float4 dn = g.ngrad[gi];
+            if (!(n.w > 0.f)) continue;
+            float nd = n.x * dn.x + n.y * dn.y + n.z * dn.z;
+            float il = 1.f / n.w;
+            ga[0] += (dn.x - n.x * nd) * il;
+            ga[1] += (dn.y - n.y * nd) * il;
+            ga[2] += (dn.z - n.z * nd) * il;
+        }
+        if (ga[0] == 0.f && ga[1] == 0.f && ga[2] == 0.f) continue;
+        float P[3][3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) P[j][c] = __ldg(g.pos + c * nvt + M.vert_off + v[j]);
+        float u[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+        float w[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+        float gu[3] = {w[1] * ga[2] - w[2] * ga[1], w[2] * ga[0] - w[0] * ga[2], w[0] * ga[1] - w[1] * ga[0]};
+        float gw[3] = {ga[1] * u[2] - ga[2] * u[1], ga[2] * u[0] - ga[0] * u[2], ga[0] * u[1] - ga[1] * u[0]};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            atomicAdd(g.gpos + c * nvt + M.vert_off + v[1], gu[c]);
+            atomicAdd(g.gpos + c * nvt + M.vert_off + v[2], gw[c]);
+            atomicAdd(g.gpos + c * nvt + M.vert_off + v[0], -(gu[c] + gw[c]));
+        }
+    }
+}
+
+// L2 loss helper
+__global__ void k_l2(const float *out, const float *tgt, long long n, float *grad, float *loss)
+{
+    float acc = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float d = out[i] - tgt[i];
+        grad[i] = 2.f * d;
+        acc += d * d;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, acc);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static int grid_x(long long n, int block, int cap)
+{
+    long long b = (n + block - 1) / block;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+void launch_vertex(const Globals &g, int n_views, int max_nv, cudaStream_t s)
+{
+    dim3 grid(grid_x(max_nv, 256, 1024), n_views);
+    k_vertex<<<grid, 256, 0, s>>>(g);
+    count_launch(1);
+}
+
+void launch_normals(const Globals &g, int n_meshes, int max_nf, cudaStream_t s)
+{
+    dim3 grid(grid_x(max_nf, 256, 2048), n_meshes);
+    k_normal_accum<<<grid, 256, 0, s>>>(g);
+    k_normal_finish<<<grid_x(g.n_verts_total, 256, 4096), 256, 0, s>>>(g);
+    count_launch(2);
+}
+
+void launch_bin(const Globals &g, int n_views, int max_nf, cudaStream_t s)
+{
+    dim3 grid(grid_x(max_nf, 256, 2048), n_views);
+    k_bin<0><<<grid, 256, 0, s>>>(g);
+    k_scan<<<1, 1024, 0, s>>>(g);
+    k_bin<1><<<grid, 256, 0, s>>>(g);
+    count_launch(3);
+}
+
+void launch_vertex_bwd(const Globals &g, int n_views, int max_nv, int n_meshes, int max_nf, bool normals,
+                       cudaStream_t s)
+{
+    dim3 grid(grid_x(max_nv, 256, 1024), n_views);
+    k_vertex_bwd<<<grid, 256, 0, s>>>(g);
+    count_launch(1);
+    if (normals) {
+        dim3 g2(grid_x(max_nf, 256, 2048), n_meshes);
+        k_normal_bwd<<<g2, 256, 0, s>>>(g);
+        count_launch(1);
+    }
+}
+
+void launch_l2(const float *out, const float *tgt, long long n, float *grad, float *loss, cudaStream_t s)
+{
+    k_l2<<<grid_x(n, 256, 152 * 8), 256, 0, s>>>(out, tgt, n, grad, loss);
+    count_launch(1);
+}
+
+}  // namespace dressi

@@ -1,0 +1,686 @@
+// dressi_tile.cu -- the per-tile hot kernel of HardSoftRas, forward and adjoint.
+//
+// One CTA owns one 16 x 16 pixel tile of one view (256 threads, one pixel each;
+// warp w owns the 16 x 2 block of rows 2w, 2w + 1).  Per CTA:
+//   1. the tile's face list is staged in shared memory, CHUNK faces at a time;
+//   2. each warp culls the staged faces against its pixel block with one
+//      conservative test per (face, warp) and a ballot, then every lane
+//      evaluates the surviving faces at its own pixel centre (SignedDist,
+//      hard test, Shift) and keeps the K smallest (key, id) pairs in registers
+//      (depth peeling of Alg. 2 done as a per-pixel K-selection);
+//   3. the hard stencil S^H of a ring of rho pixels around the tile is built
+//      from the same staged faces (hard test only), so the edge mask E of
+//      every tile pixel is known without a second pass over the image;
+//   4. forward: each layer is re-evaluated from its face id, shaded
+//      (perspective-correct interpolation, bilinear texture, Lambert) and
+//      blended (D_k = sigmoid(dist/sigma), colour and silhouette equations of
+//      Sec. 3.3.3); adjoint: the same values are rebuilt and dL/dI is pushed
+//      back to the screen-space corners, vertex colours, vertex normals and
+//      texels with red.global atomics.
+// With layer ids stored by the forward, the adjoint skips steps 1-3 and reads
+// them (S^H of the ring from the neighbours' stored front layer).
+#include "dressi_core.cuh"
+#include "dressi_launch.h"
+
+namespace dressi {
+
+constexpr int TT = 16;                 // tile edge
+constexpr int NT = TT * TT;            // threads per CTA
+constexpr int RHO_MAX = 8;             // largest supported edge-mask radius
+constexpr int HS_MAX = TT + 2 * RHO_MAX;
+
+// conservative tile-local culling data of a staged face
+struct Pre {
+    float nx[3], ny[3], c[3];    // F_i(p) ~ nx p.x + ny p.y + c, inward unit normal, tile-local
+    float bx0, bx1, by0, by1;    // bbox grown by r, tile-local
+};
+
+__device__ __forceinline__ void make_pre(const FaceRec &R, bool live, float tx0, float ty0, float r_px, Pre &P)
+{
+    if (!live) {
+        P.bx0 = 3.0e38f; P.bx1 = -3.0e38f; P.by0 = 3.0e38f; P.by1 = -3.0e38f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { P.nx[i] = 0.f; P.ny[i] = 0.f; P.c[i] = -3.0e38f; }
+        return;
+    }
+    const bool orient = R.flags & 1;
+    float vx[3], vy[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        vx[i] = (R.xh[i] - tx0) + R.xl[i];
+        vy[i] = (R.yh[i] - ty0) + R.yl[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int ib = (i + 1) % 3;
+        float ex = vx[ib] - vx[i], ey = vy[ib] - vy[i];
+        float nx = orient ? -ey : ey, ny = orient ? ex : -ex;
+        float l = sqrtf(nx * nx + ny * ny);
+        float s = l > 0.f ? 1.f / l : 0.f;
+        nx *= s; ny *= s;
+        P.nx[i] = nx; P.ny[i] = ny;
+        P.c[i] = -(nx * vx[i] + ny * vy[i]);
+    }
+    P.bx0 = fminf(vx[0], fminf(vx[1], vx[2])) - r_px;
+    P.bx1 = fmaxf(vx[0], fmaxf(vx[1], vx[2])) + r_px;
+    P.by0 = fminf(vy[0], fminf(vy[1], vy[2])) - r_px;
+    P.by1 = fmaxf(vy[0], fmaxf(vy[1], vy[2])) + r_px;
+}
+
+// may some pixel centre of the box (cx +- hx, cy +- hy) be within r of the face?
+__device__ __forceinline__ bool pretest(const Pre &P, float cx, float cy, float hx, float hy, float r_px)
+{
+    const float eps = 1e-2f;
+    if (P.bx1 < cx - hx - eps || P.bx0 > cx + hx + eps || P.by1 < cy - hy - eps || P.by0 > cy + hy + eps) return false;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float F = P.nx[i] * cx + P.ny[i] * cy + P.c[i] + fabsf(P.nx[i]) * hx + fabsf(P.ny[i]) * hy;
+        if (F < -r_px - eps) return false;
+    }
+    return true;
+}
+
+// position of halo pixel h in the ring of width rho around the tile (tile-local)
+__device__ __forceinline__ void halo_pos(int h, int rho, int &hx, int &hy)
+{
+    const int hs = TT + 2 * rho;
+    if (h < rho * hs) { hy = h / hs - rho; hx = h % hs - rho; return; }
+    h -= rho * hs;
+    if (h < rho * hs) { hy = TT + h / hs; hx = h % hs - rho; return; }
+    h -= rho * hs;
+    if (h < rho * TT) { hy = h / rho; hx = h % rho - rho; return; }
+    h -= rho * TT;
+    hy = h / rho;
+    hx = TT + h % rho;
+}
+
+template <int K>
+__device__ __forceinline__ void peel_insert(float (&kk)[K], int (&ii)[K], bool (&hh)[K], float key, int id, bool hard)
+{
+    if (!frag_less(key, id, kk[K - 1], ii[K - 1])) return;
+#pragma unroll
+    for (int t = K - 1; t > 0; --t) {
+        if (frag_less(key, id, kk[t - 1], ii[t - 1])) {
+            kk[t] = kk[t - 1]; ii[t] = ii[t - 1]; hh[t] = hh[t - 1];
+        } else {
+            kk[t] = key; ii[t] = id; hh[t] = hard;
+            return;
+        }
+    }
+    kk[0] = key; ii[0] = id; hh[0] = hard;
+}
+
+// ---------------------------------------------------------------------------
+// per-layer geometry and shading (Sec. 3.2.2 texture sampling, Sec. 3.3.3 shading)
+// ---------------------------------------------------------------------------
+struct Layer {
+    FaceRec R;
+    Frag fr;
+    float lam[3], b[3], Q;
+    float C[3];
+    float D;
+    // texture
+    int ix[2], iy[2];
+    float fx, fy;
+    float A[3];
+    float Xt[3], Yt[3];   // texel-space corner coordinates relative to corner 0
+    // Lambert
+    float n[3], mlen, ndl;
+};
+
+__device__ __forceinline__ float4 load_texel(const Globals &g, long long idx)
+{
+    if (g.tex_f16) {
+        uint2 raw = __ldg(reinterpret_cast<const uint2 *>(g.tex) + idx);
+        __half2 a = *reinterpret_cast<__half2 *>(&raw.x), b = *reinterpret_cast<__half2 *>(&raw.y);
+        float2 fa = __half22float2(a), fb = __half22float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+    return __ldg(reinterpret_cast<const float4 *>(g.tex) + idx);
+}
+
+__device__ __forceinline__ int wrapi(int i, int n)
+{
+    int m = i % n;
+    return m < 0 ? m + n : m;
+}
+
+// texel coordinate x = (sum b_i u_i) W - 1/2 without losing the fraction at large W:
+// corners as exact float pairs u_i W = hi_i + lo_i, offsets from corner 0 carry
+// the barycentric mix, the floor is split off exactly.
+__device__ __forceinline__ void texcoord(const float b[3], const float u[3], float Wt, int &i0, float &f, float rel[3])
+{
+    float hi[3], lo[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        hi[i] = u[i] * Wt;
+        lo[i] = fmaf(u[i], Wt, -hi[i]);
+    }
+    rel[0] = 0.f;
+    rel[1] = (hi[1] - hi[0]) + (lo[1] - lo[0]);
+    rel[2] = (hi[2] - hi[0]) + (lo[2] - lo[0]);
+    const float delta = fmaf(b[1], rel[1], fmaf(b[2], rel[2], lo[0]));
+    const float A = hi[0] - 0.5f;
+    const float fA = floorf(A);
+    const float t = (A - fA) + delta;
+    const float ft = floorf(t);
+    f = t - ft;
+    i0 = (int)fA + (int)ft;
+}
+
+__device__ __forceinline__ bool layer_build(const Globals &g, const ViewK &V, const MeshK &M, const VRec *vr, int id,
+                                            float px, float py, Layer &L)
+{
+    if (!face_load(g, M, vr, id, L.R)) return false;
+    if (!eval_face(L.R, px, py, V.r_px, V.half_inv_S, L.fr)) return false;
+    if (L.fr.hard) {
+        L.lam[0] = L.fr.Fn[1] * L.R.invA;
+        L.lam[1] = L.fr.Fn[2] * L.R.invA;
+        L.lam[2] = L.fr.Fn[0] * L.R.invA;
+    } else if (L.fr.feat >= 3) {
+        // soft fragment: barycentrics of its closest point of the hard face (a corner)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) L.lam[j] = (j == L.fr.feat - 3) ? 1.f : 0.f;
+    } else {
+        // ... or a point of edge feat, at parameter t from its canonical first endpoint
+        const int i = L.fr.feat;
+        const bool sw = (L.R.flags >> (1 + i)) & 1;
+        const int P = sw ? (i + 1) % 3 : i, Q = sw ? i : (i + 1) % 3;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) L.lam[j] = (j == P) ? 1.f - L.fr.t : ((j == Q) ? L.fr.t : 0.f);
+    }
+    float q[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) q[i] = L.lam[i] * L.R.iw[i];
+    L.Q = q[0] + q[1] + q[2];
+    const float iQ = 1.f / L.Q;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) L.b[i] = q[i] * iQ;
+    L.D = sigmoidf_stable(L.fr.dist * V.inv_sigma_px);
+    const long long nvt = g.n_verts_total;
+    if (g.shade_mode == 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float a = 0.f;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) a = fmaf(L.b[i], __ldg(g.col + c * nvt + M.vert_off + L.R.vi[i]), a);
+            L.C[c] = a;
+        }
+        return true;
+    }
+    float u[3], v[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        u[i] = __ldg(g.uv + M.vert_off + L.R.vi[i]);
+        v[i] = __ldg(g.uv + nvt + M.vert_off + L.R.vi[i]);
+    }
+    int x0, y0;
+    texcoord(L.b, u, (float)M.tex_w, x0, L.fx, L.Xt);
+    texcoord(L.b, v, (float)M.tex_h, y0, L.fy, L.Yt);
+    L.ix[0] = wrapi(x0, M.tex_w); L.ix[1] = wrapi(x0 + 1, M.tex_w);
+    L.iy[0] = wrapi(y0, M.tex_h); L.iy[1] = wrapi(y0 + 1, M.tex_h);
+    const long long tb = M.tex_off;
+    float4 t00 = load_texel(g, tb + (long long)L.iy[0] * M.tex_w + L.ix[0]);
+    float4 t10 = load_texel(g, tb + (long long)L.iy[0] * M.tex_w + L.ix[1]);
+    float4 t01 = load_texel(g, tb + (long long)L.iy[1] * M.tex_w + L.ix[0]);
+    float4 t11 = load_texel(g, tb + (long long)L.iy[1] * M.tex_w + L.ix[1]);
+    const float w00 = (1.f - L.fx) * (1.f - L.fy), w10 = L.fx * (1.f - L.fy), w01 = (1.f - L.fx) * L.fy,
+                w11 = L.fx * L.fy;
+    L.A[0] = w00 * t00.x + w10 * t10.x + w01 * t01.x + w11 * t11.x;
+    L.A[1] = w00 * t00.y + w10 * t10.y + w01 * t01.y + w11 * t11.y;
+    L.A[2] = w00 * t00.z + w10 * t10.z + w01 * t01.z + w11 * t11.z;
+    if (g.shade_mode == 1) {
+        L.C[0] = L.A[0]; L.C[1] = L.A[1]; L.C[2] = L.A[2];
+        return true;
+    }
+    float m[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float4 nv = g.nrm[M.vert_off + L.R.vi[i]];
+        m[0] = fmaf(L.b[i], nv.x, m[0]);
+        m[1] = fmaf(L.b[i], nv.y, m[1]);
+        m[2] = fmaf(L.b[i], nv.z, m[2]);
+    }
+    L.mlen = sqrtf(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+    const float il = L.mlen > 0.f ? 1.f / L.mlen : 0.f;
+    L.n[0] = m[0] * il; L.n[1] = m[1] * il; L.n[2] = m[2] * il;
+    L.ndl = L.n[0] * V.light[0] + L.n[1] * V.light[1] + L.n[2] * V.light[2];
+    const float s = fmaxf(L.ndl, 0.f);
+    L.C[0] = L.A[0] * s; L.C[1] = L.A[1] * s; L.C[2] = L.A[2] * s;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// adjoint of one layer: gC = dL/dC_k, gD = dL/dD_k
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, const MeshK &M, const Layer &L,
+                                              float px, float py, const float gC[3], float gD)
+{
+    const long long nvt = g.n_verts_total;
+    const FaceRec &R = L.R;
+    float dx[3], dy[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        dx[i] = (px - R.xh[i]) - R.xl[i];
+        dy[i] = (py - R.yh[i]) - R.yl[i];
+    }
+    float gX[3] = {0.f, 0.f, 0.f}, gY[3] = {0.f, 0.f, 0.f}, gW[3] = {0.f, 0.f, 0.f};
+    const float o = (R.flags & 1) ? 1.f : -1.f;
+
+    // sigmoid -> signed distance -> corners (closest feature)
+    const float gdist = gD * L.D * (1.f - L.D) * V.inv_sigma_px;
+    if (gdist != 0.f) {
+        const int ft = L.fr.feat;
+        if (ft < 3) {
+            const int a = ft, b = (ft + 1) % 3;
+            const float ex = dx[a] - dx[b], ey = dy[a] - dy[b];   // V_b - V_a
+            const float il = 1.f / sqrtf(ex * ex + ey * ey);
+            const float c = ex * dy[a] - ey * dx[a];
+            const float il3 = il * il * il;
+            const float gex = o * (dy[a] * il - c * ex * il3);
+            const float gey = o * (-dx[a] * il - c * ey * il3);
+            const float gdx = o * (-ey * il), gdy = o * (ex * il);
+            gX[b] += gdist * gex; gY[b] += gdist * gey;
+            gX[a] += gdist * (-gex - gdx); gY[a] += gdist * (-gey - gdy);
+        } else {
+            const int mm = ft - 3;
+            const float l = sqrtf(dx[mm] * dx[mm] + dy[mm] * dy[mm]);
+            if (l > 0.f) {
+                gX[mm] += gdist * dx[mm] / l;
+                gY[mm] += gdist * dy[mm] / l;
+            }
+        }
+    }
+
+    // shading -> barycentrics and attributes
+    float gb[3] = {0.f, 0.f, 0.f};
+    const bool anyC = gC[0] != 0.f || gC[1] != 0.f || gC[2] != 0.f;
+    if (anyC) {
+        if (g.shade_mode == 0) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const long long gi = M.vert_off + R.vi[i];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (g.gcol) atomicAdd(g.gcol + c * nvt + gi, L.b[i] * gC[c]);
+                    gb[i] = fmaf(gC[c], __ldg(g.col + c * nvt + gi), gb[i]);
+                }
+            }
+        } else {
+            float gA[3];
+            if (g.shade_mode == 1) {
+                gA[0] = gC[0]; gA[1] = gC[1]; gA[2] = gC[2];
+            } else {
+                const float s = fmaxf(L.ndl, 0.f);
+                gA[0] = gC[0] * s; gA[1] = gC[1] * s; gA[2] = gC[2] * s;
+                if (L.ndl > 0.f && L.mlen > 0.f) {
+                    const float gs = gC[0] * L.A[0] + gC[1] * L.A[1] + gC[2] * L.A[2];
+                    const float gn[3] = {gs * V.light[0], gs * V.light[1], gs * V.light[2]};
+                    const float nd = L.n[0] * gn[0] + L.n[1] * gn[1] + L.n[2] * gn[2];
+                    const float il = 1.f / L.mlen;
+                    const float gm[3] = {(gn[0] - L.n[0] * nd) * il, (gn[1] - L.n[1] * nd) * il,
+                                         (gn[2] - L.n[2] * nd) * il};
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const long long gi = M.vert_off + R.vi[i];
+                        const float4 nv = g.nrm[gi];
+                        atomicAdd(g.ngrad + gi, make_float4(L.b[i] * gm[0], L.b[i] * gm[1], L.b[i] * gm[2], 0.f));
+                        gb[i] += gm[0] * nv.x + gm[1] * nv.y + gm[2] * nv.z;
+                    }
+                }
+            }
+            // bilinear texture adjoint
+            const long long tb = M.tex_off;
+            const long long i00 = tb + (long long)L.iy[0] * M.tex_w + L.ix[0];
+            const long long i10 = tb + (long long)L.iy[0] * M.tex_w + L.ix[1];
+            const long long i01 = tb + (long long)L.iy[1] * M.tex_w + L.ix[0];
+            const long long i11 = tb + (long long)L.iy[1] * M.tex_w + L.ix[1];
+            const float w00 = (1.f - L.fx) * (1.f - L.fy), w10 = L.fx * (1.f - L.fy), w01 = (1.f - L.fx) * L.fy,
+                        w11 = L.fx * L.fy;
+            if (g.gtex) {
+                float4 *gt = reinterpret_cast<float4 *>(g.gtex);
+                atomicAdd(gt + i00, make_float4(w00 * gA[0], w00 * gA[1], w00 * gA[2], 0.f));
+                atomicAdd(gt + i10, make_float4(w10 * gA[0], w10 * gA[1], w10 * gA[2], 0.f));
+                atomicAdd(gt + i01, make_float4(w01 * gA[0], w01 * gA[1], w01 * gA[2], 0.f));
+                atomicAdd(gt + i11, make_float4(w11 * gA[0], w11 * gA[1], w11 * gA[2], 0.f));
+            }
+            const float4 t00 = load_texel(g, i00), t10 = load_texel(g, i10), t01 = load_texel(g, i01),
+                         t11 = load_texel(g, i11);
+            const float gx = gA[0] * ((1.f - L.fy) * (t10.x - t00.x) + L.fy * (t11.x - t01.x)) +
+                             gA[1] * ((1.f - L.fy) * (t10.y - t00.y) + L.fy * (t11.y - t01.y)) +
+                             gA[2] * ((1.f - L.fy) * (t10.z - t00.z) + L.fy * (t11.z - t01.z));
+            const float gy = gA[0] * ((1.f - L.fx) * (t01.x - t00.x) + L.fx * (t11.x - t10.x)) +
+                             gA[1] * ((1.f - L.fx) * (t01.y - t00.y) + L.fx * (t11.y - t10.y)) +
+                             gA[2] * ((1.f - L.fx) * (t01.z - t00.z) + L.fx * (t11.z - t10.z));
+            // x = sum b_i X_i - 1/2; adding a constant to every gb_i is invisible to the
+            // perspective step below (sum b = 1), so corner offsets from corner 0 are used
+#pragma unroll
+            for (int i = 0; i < 3; ++i) gb[i] += gx * L.Xt[i] + gy * L.Yt[i];
+        }
+        // perspective-correct barycentrics: b_i = q_i / Q, q_i = lam_i / w_i
+        const float bdot = L.b[0] * gb[0] + L.b[1] * gb[1] + L.b[2] * gb[2];
+        const float iQ = 1.f / L.Q;
+        float glam[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float gq = (gb[i] - bdot) * iQ;
+            glam[i] = gq * R.iw[i];
+            gW[i] += gq * L.lam[i];
+        }
+        if (L.fr.hard) {
+            // lam_i = cross(V_B - V_A, p - V_A) / A2,  A = i+1, B = i+2
+            const float iA2 = o * R.invA;
+            float gA2 = 0.f;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const int A = (i + 1) % 3, B = (i + 2) % 3;
+                const float gn = glam[i] * iA2;
+                gA2 -= glam[i] * L.lam[i] * iA2;
+                const float ex = dx[A] - dx[B], ey = dy[A] - dy[B];
+                const float gex = dy[A], gey = -dx[A], gdx = -ey, gdy = ex;
+                gX[B] += gn * gex; gY[B] += gn * gey;
+                gX[A] += gn * (-gex - gdx); gY[A] += gn * (-gey - gdy);
+            }
+            const float ux = dx[0] - dx[1], uy = dy[0] - dy[1];   // V1 - V0
+            const float wx = dx[0] - dx[2], wy = dy[0] - dy[2];   // V2 - V0
+            gX[1] += gA2 * wy; gY[1] -= gA2 * wx;
+            gX[2] -= gA2 * uy; gY[2] += gA2 * ux;
+            gX[0] += gA2 * (uy - wy); gY[0] += gA2 * (wx - ux);
+        } else if (L.fr.feat < 3) {
+            // lam_P = 1 - s, lam_Q = s, s = (p - P).(Q - P) / |Q - P|^2
+            const int i = L.fr.feat;
+            const bool sw = (R.flags >> (1 + i)) & 1;
+            const int P = sw ? (i + 1) % 3 : i, Q = sw ? i : (i + 1) % 3;
+            float dPx = 0.f, dPy = 0.f, dQx = 0.f, dQy = 0.f, gP = 0.f, gQ = 0.f;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if (j == P) { dPx = dx[j]; dPy = dy[j]; gP = glam[j]; }
+                if (j == Q) { dQx = dx[j]; dQy = dy[j]; gQ = glam[j]; }
+            }
+            const float ex = dPx - dQx, ey = dPy - dQy;            // Q - P
+            const float iee = 1.f / (ex * ex + ey * ey), s = L.fr.t;
+            const float gs = gQ - gP;
+            const float gex = (dPx - 2.f * s * ex) * iee, gey = (dPy - 2.f * s * ey) * iee;
+            const float gdx = ex * iee, gdy = ey * iee;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if (j == Q) { gX[j] += gs * gex; gY[j] += gs * gey; }
+                if (j == P) { gX[j] += gs * (-gex - gdx); gY[j] += gs * (-gey - gdy); }
+            }
+        }
+    }
+    float4 *sg = g.sgrad + V.vrec_off;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        if (gX[i] != 0.f || gY[i] != 0.f || gW[i] != 0.f) atomicAdd(sg + R.vi[i], make_float4(gX[i], gY[i], gW[i], 0.f));
+}
+
+// ---------------------------------------------------------------------------
+// the tile kernel
+// ---------------------------------------------------------------------------
+template <int K, bool BWD>
+__global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
+{
+    __shared__ FaceRec sF[CHUNK];
+    __shared__ Pre sP[CHUNK];
+    __shared__ unsigned char sSH[HS_MAX * HS_MAX];
+    __shared__ int s_view;
+
+    const int t = blockIdx.x;
+    if (threadIdx.x == 0) s_view = view_of_tile(g, t);
+    __syncthreads();
+    const ViewK &V = g.views[s_view];
+    const MeshK &M = g.meshes[V.mesh];
+    const VRec *vr = g.vrec + V.vrec_off;
+    const int lt = t - V.tile_base;
+    const int X0 = (lt % V.tiles_x) * TT, Y0 = (lt / V.tiles_x) * TT;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lx = lane & 15, ly = warp * 2 + (lane >> 4);
+    const int X = X0 + lx, Y = Y0 + ly;
+    const bool inimg = X < V.W && Y < V.H;
+    const float px = (float)X + 0.5f, py = (float)Y + 0.5f;
+    const int rho = (g.edge_mode == 0) ? min(V.rho, RHO_MAX) : 0;
+    const int hs = TT + 2 * rho;
+    const long long pix = V.pix_off + (long long)Y * V.W + X;
+
+    for (int i = threadIdx.x; i < hs * hs; i += NT) {
+        const int hx = X0 - rho + i % hs, hy = Y0 - rho + i / hs;
+        sSH[i] = (hx >= 0 && hy >= 0 && hx < V.W && hy < V.H) ? 0 : 2;
+    }
+
+    float kk[K];
+    int ii[K];
+    bool hh[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) { kk[k] = 3.0e38f; ii[k] = 0x7fffffff; hh[k] = false; }
+
+    const int hcount = rho > 0 ? hs * hs - NT : 0;
+    const int ngroups = (hcount + 31) >> 5;
+    const bool from_ids = BWD && g.ids_in != nullptr;
+
+    if (!from_ids) {
+        const long long lb = g.tile_off[t], le = g.tile_off[t + 1];
+        const bool fallback = le > g.list_cap;
+        const int n = fallback ? M.nF : (int)(le - lb);
+        if (fallback && threadIdx.x == 0) atomicOr(g.status, DRESSI_DEV_TILE_OVERFLOW);
+        const float cx = 8.f, cy = 2.f * warp + 1.f;   // centre of this warp's 16 x 2 block of pixel centres
+        for (int c0 = 0; c0 < n; c0 += CHUNK) {
+            const int nch = min(CHUNK, n - c0);
+            __syncthreads();
+            if (threadIdx.x < nch) {
+                const int f = fallback ? c0 + threadIdx.x : g.lists[lb + c0 + threadIdx.x];
+                FaceRec R;
+                const bool live = face_load(g, M, vr, f, R);
+                sF[threadIdx.x] = R;
+                make_pre(R, live, (float)X0, (float)Y0, V.r_px, sP[threadIdx.x]);
+            }
+            __syncthreads();
+            // peel over the staged faces
+            for (int b0 = 0; b0 < nch; b0 += 32) {
+                const int j = b0 + lane;
+                const bool ok = j < nch && pretest(sP[j], cx, cy, 7.5f, 0.5f, V.r_px);
+                unsigned m = __ballot_sync(0xffffffffu, ok);
+                while (m) {
+                    const int b = __ffs(m) - 1;
+                    m &= m - 1;
+                    Frag fr;
+                    if (inimg && eval_face(sF[b0 + b], px, py, V.r_px, V.half_inv_S, fr))
+                        peel_insert<K>(kk, ii, hh, fr.key, sF[b0 + b].id, fr.hard);
+                }
+            }
+            // S^H of the halo ring
+            for (int gi = warp; gi < ngroups; gi += NT / 32) {
+                const int h = gi * 32 + lane;
+                int hx = 0, hy = 0;
+                if (h < hcount) halo_pos(h, rho, hx, hy);
+                const int si = (hy + rho) * hs + (hx + rho);
+                bool need = h < hcount && sSH[si] == 0;
+                float fx = (float)hx + 0.5f, fy = (float)hy + 0.5f;
+                float mnx = h < hcount ? fx : 3.0e38f, mxx = h < hcount ? fx : -3.0e38f;
+                float mny = h < hcount ? fy : 3.0e38f, mxy = h < hcount ? fy : -3.0e38f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+                    mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+                    mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+                    mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+                }
+                const float gcx = 0.5f * (mnx + mxx), gcy = 0.5f * (mny + mxy);
+                const float ghx = 0.5f * (mxx - mnx), ghy = 0.5f * (mxy - mny);
+                for (int b0 = 0; b0 < nch; b0 += 32) {
+                    const int j = b0 + lane;
+                    // hard test only: r = 0 for the cull
+                    const bool ok = j < nch && pretest(sP[j], gcx, gcy, ghx, ghy, 0.f);
+                    unsigned m = __ballot_sync(0xffffffffu, ok);
+                    while (m) {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1;
+                        float hk;
+                        if (need && hard_test(sF[b0 + b], (float)(X0 + hx) + 0.5f, (float)(Y0 + hy) + 0.5f, hk)) {
+                            sSH[si] = 1;
+                            need = false;
+                        }
+                    }
+                }
+            }
+        }
+    } else {
+        // layers stored by the forward
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int id = inimg ? __ldg(g.ids_in + (long long)k * g.n_pix + pix) : -1;
+            if (id >= 0) { ii[k] = id; kk[k] = 0.f; } else { ii[k] = 0x7fffffff; kk[k] = 3.0e38f; }
+        }
+        if (inimg && ii[0] != 0x7fffffff) {
+            FaceRec R;
+            Frag fr;
+            hh[0] = face_load(g, M, vr, ii[0], R) && eval_face(R, px, py, V.r_px, V.half_inv_S, fr) && fr.hard;
+        }
+        for (int h = threadIdx.x; h < hcount; h += NT) {
+            int hx, hy;
+            halo_pos(h, rho, hx, hy);
+            const int si = (hy + rho) * hs + (hx + rho);
+            if (sSH[si] != 0) continue;
+            const long long hp = V.pix_off + (long long)(Y0 + hy) * V.W + (X0 + hx);
+            const int id = __ldg(g.ids_in + hp);
+            if (id < 0) continue;
+            FaceRec R;
+            float hk;
+            if (face_load(g, M, vr, id, R) && hard_test(R, (float)(X0 + hx) + 0.5f, (float)(Y0 + hy) + 0.5f, hk))
+                sSH[si] = 1;
+        }
+    }
+    int nl = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) nl += (ii[k] != 0x7fffffff) ? 1 : 0;
+    const bool SH = nl > 0 && hh[0];
+    __syncthreads();
+    if (inimg) sSH[(ly + rho) * hs + (lx + rho)] = SH ? 1 : 0;
+    __syncthreads();
+    if (!inimg) return;
+
+    // edge mask (Sec. 3.3.3): the window of radius rho sees both S^H = 0 and 1
+    bool E = g.edge_mode == 1;
+    if (g.edge_mode == 0) {
+        bool s0 = false, s1 = false;
+        for (int wy = 0; wy <= 2 * rho; ++wy)
+            for (int wx = 0; wx <= 2 * rho; ++wx) {
+                const unsigned char v = sSH[(ly + wy) * hs + (lx + wx)];
+                s0 |= v == 0;
+                s1 |= v == 1;
+            }
+        E = s0 && s1;
+    }
+
+    if (!BWD) {
+        if (g.ids) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) g.ids[(long long)k * g.n_pix + pix] = (k < nl) ? ii[k] : -1;
+        }
+        float Cs[3] = {0.f, 0.f, 0.f}, C1[3] = {0.f, 0.f, 0.f};
+        float Ds = 0.f, prod = 1.f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (k >= nl) break;
+            Layer L;
+            if (!layer_build(g, V, M, vr, ii[k], px, py, L)) continue;
+            Cs[0] = fmaf(L.D, L.C[0], Cs[0]);
+            Cs[1] = fmaf(L.D, L.C[1], Cs[1]);
+            Cs[2] = fmaf(L.D, L.C[2], Cs[2]);
+            Ds += L.D;
+            prod *= 1.f - L.D;
+            if (k == 0) { C1[0] = L.C[0]; C1[1] = L.C[1]; C1[2] = L.C[2]; }
+        }
+        float4 o;
+        if (E) {
+            const float iD = Ds > 0.f ? 1.f / Ds : 0.f;
+            o = make_float4(Cs[0] * iD, Cs[1] * iD, Cs[2] * iD, 1.f - prod);
+        } else {
+            o = SH ? make_float4(C1[0], C1[1], C1[2], 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        reinterpret_cast<float4 *>(g.out)[pix] = o;
+    } else {
+        if (nl == 0) return;
+        const float4 gi4 = __ldg(reinterpret_cast<const float4 *>(g.gin) + pix);
+        const float gc[3] = {gi4.x, gi4.y, gi4.z};
+        if (gc[0] == 0.f && gc[1] == 0.f && gc[2] == 0.f && gi4.w == 0.f) return;
+        // pass 1: D_k and C_k of every layer
+        float Dk[K], Ck[K][3];
+#pragma unroll
+        for (int k = 0; k < K; ++k) { Dk[k] = 0.f; Ck[k][0] = Ck[k][1] = Ck[k][2] = 0.f; }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (k >= nl) break;
+            Layer L;
+            if (!layer_build(g, V, M, vr, ii[k], px, py, L)) continue;
+            Dk[k] = L.D;
+            Ck[k][0] = L.C[0]; Ck[k][1] = L.C[1]; Ck[k][2] = L.C[2];
+        }
+        float gCk[K][3], gDk[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) { gDk[k] = 0.f; gCk[k][0] = gCk[k][1] = gCk[k][2] = 0.f; }
+        if (E) {
+            float Ds = 0.f, Ie[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                Ds += Dk[k];
+                Ie[0] = fmaf(Dk[k], Ck[k][0], Ie[0]);
+                Ie[1] = fmaf(Dk[k], Ck[k][1], Ie[1]);
+                Ie[2] = fmaf(Dk[k], Ck[k][2], Ie[2]);
+            }
+            if (Ds > 0.f) {
+                const float iD = 1.f / Ds;
+                Ie[0] *= iD; Ie[1] *= iD; Ie[2] *= iD;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    gCk[k][0] = Dk[k] * iD * gc[0];
+                    gCk[k][1] = Dk[k] * iD * gc[1];
+                    gCk[k][2] = Dk[k] * iD * gc[2];
+                    gDk[k] = (gc[0] * (Ck[k][0] - Ie[0]) + gc[1] * (Ck[k][1] - Ie[1]) + gc[2] * (Ck[k][2] - Ie[2])) * iD;
+                }
+            }
+            // silhouette 1 - prod_k (1 - D_k)
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                float others = 1.f;
+#pragma unroll
+                for (int j = 0; j < K; ++j)
+                    if (j != k && j < nl) others *= 1.f - Dk[j];
+                if (k < nl) gDk[k] += gi4.w * others;
+            }
+        } else if (SH) {
+            gCk[0][0] = gc[0]; gCk[0][1] = gc[1]; gCk[0][2] = gc[2];
+        }
+        // pass 2: per-layer adjoint
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (k >= nl) break;
+            if (gDk[k] == 0.f && gCk[k][0] == 0.f && gCk[k][1] == 0.f && gCk[k][2] == 0.f) continue;
+            Layer L;
+            if (!layer_build(g, V, M, vr, ii[k], px, py, L)) continue;
+            layer_adjoint(g, V, M, L, px, py, gCk[k], gDk[k]);
+        }
+    }
+}
+
+template <bool BWD>
+static void launch_k(const Globals &g, cudaStream_t s)
+{
+    const int grid = g.total_tiles;
+    switch (g.K) {
+    case 1: k_tile<1, BWD><<<grid, NT, 0, s>>>(g); break;
+    case 2: k_tile<2, BWD><<<grid, NT, 0, s>>>(g); break;
+    case 3: k_tile<3, BWD><<<grid, NT, 0, s>>>(g); break;
+    case 4: k_tile<4, BWD><<<grid, NT, 0, s>>>(g); break;
+    default: k_tile<5, BWD><<<grid, NT, 0, s>>>(g); break;
+    }
+}
+
+void launch_tile(const Globals &g, bool backward, cudaStream_t s)
+{
+    if (backward) launch_k<true>(g, s);
+    else launch_k<false>(g, s);
+    count_launch(1);
+}
+
+}  // namespace dressi

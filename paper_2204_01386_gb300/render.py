@@ -1,0 +1,212 @@
+"""Python face of libdressi: packed scenes, a renderer object and a
+``torch.autograd.Function``.  PyTorch provides device memory and the stream;
+all arithmetic runs in the library's kernels.
+
+Layouts (as the C ABI wants them):
+  positions / colours planar ``[3, V_total]`` float32, UVs ``[2, V_total]``,
+  faces ``[F_total, 3]`` int32 (indices local to their mesh), textures packed
+  ``[sum texels, 4]`` float32 or float16, images ``[n_pix, 4]`` float32 with the
+  views stacked row-major one after another.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+def _t(x, dtype, device):
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=dtype)
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device=device)
+
+
+class PackedScene:
+    """Meshes packed into ragged device buffers (one vertex plane set, one face
+    array, one texel buffer), plus the host-side mesh table."""
+
+    def __init__(self, meshes: Sequence, device="cuda", tex_dtype: Optional[torch.dtype] = None):
+        self.device = torch.device(device)
+        pos, col, uv, faces, tex = [], [], [], [], []
+        table = []
+        vo = fo = to = 0
+        has_col = all(getattr(m, "col", None) is not None for m in meshes)
+        has_uv = all(getattr(m, "uv", None) is not None for m in meshes)
+        has_tex = all(getattr(m, "tex", None) is not None for m in meshes)
+        if tex_dtype is None and has_tex:
+            t0 = meshes[0].tex
+            tex_dtype = torch.float16 if (str(getattr(t0, "dtype", "")) in ("float16", "torch.float16")) else torch.float32
+        self.tex_dtype = tex_dtype or torch.float32
+        for m in meshes:
+            p = _t(m.pos, torch.float32, self.device)
+            f = _t(m.faces, torch.int32, self.device)
+            pos.append(p.t())
+            faces.append(f)
+            if has_col:
+                col.append(_t(m.col, torch.float32, self.device).t())
+            if has_uv:
+                uv.append(_t(m.uv, torch.float32, self.device).t())
+            th = tw = 0
+            if has_tex:
+                tt = _t(m.tex, self.tex_dtype, self.device)
+                th, tw = int(tt.shape[0]), int(tt.shape[1])
+                tex.append(tt.reshape(-1, 4))
+            table.append(B.DressiMesh(int(p.shape[0]), int(f.shape[0]), vo, fo, to, tw, th))
+            vo += int(p.shape[0])
+            fo += int(f.shape[0])
+            to += th * tw
+        self.n_verts_total = vo
+        self.n_faces_total = fo
+        self.n_texels = to
+        self.pos = torch.cat(pos, 1).contiguous()
+        self.faces = torch.cat(faces, 0).contiguous()
+        self.col = torch.cat(col, 1).contiguous() if has_col else None
+        self.uv = torch.cat(uv, 1).contiguous() if has_uv else None
+        self.tex = torch.cat(tex, 0).contiguous() if has_tex else None
+        self.table = (B.DressiMesh * len(table))(*table)
+        self.n_meshes = len(table)
+
+    def c_struct(self, pos=None, col=None, tex=None) -> B.DressiScene:
+        """C view of the scene; ``pos``/``col``/``tex`` override the stored tensors
+        (same shapes), e.g. with tensors that require grad."""
+        pos = self.pos if pos is None else pos
+        col = self.col if col is None else col
+        tex = self.tex if tex is None else tex
+        for t in (pos, col, tex):
+            if t is not None:
+                assert t.is_cuda and t.is_contiguous()
+        return B.DressiScene(self.n_meshes, C.cast(self.table, C.POINTER(B.DressiMesh)), self.n_verts_total,
+                             pos.data_ptr(), col.data_ptr() if col is not None else None,
+                             self.uv.data_ptr() if self.uv is not None else None, self.faces.data_ptr(),
+                             tex.data_ptr() if tex is not None else None,
+                             B.TEX_F16 if self.tex_dtype == torch.float16 else B.TEX_F32)
+
+
+def make_views(views: Sequence) -> "C.Array":
+    """Host array of dressi_view from objects with mvp, light, mesh, width, height;
+    views are stacked one after another in the image buffers."""
+    arr = (B.DressiView * len(views))()
+    off = 0
+    for i, v in enumerate(views):
+        a = arr[i]
+        a.mvp[:] = [float(x) for x in np.asarray(v.mvp, np.float32).reshape(16)]
+        a.light[:] = [float(x) for x in np.asarray(v.light, np.float32).reshape(3)]
+        a.mesh, a.width, a.height, a.pix_off = int(v.mesh), int(v.width), int(v.height), off
+        off += int(v.width) * int(v.height)
+    return arr, off
+
+
+def make_params(p, list_cap: int = 0) -> B.DressiParams:
+    return B.DressiParams(int(p.K), float(p.r), float(p.sigma), float(p.delta), float(getattr(p, "gamma", 0.0)),
+                          int(p.edge_mode), int(p.shade_mode), int(getattr(p, "texgrad_mode", 0)), 0, int(list_cap))
+
+
+class Renderer:
+    """Owns the workspace and status word for one (scene, views, params) set."""
+
+    def __init__(self, scene: PackedScene, views: Sequence, params, list_cap: int = 0):
+        self.lib = B.load()
+        self.scene = scene
+        self.views, self.n_pix = make_views(views)
+        self.n_views = len(views)
+        self.params = make_params(params, list_cap)
+        self.K = int(params.K)
+        sc = scene.c_struct()
+        self.ws_bytes = int(self.lib.dressi_workspace_size(C.byref(sc), self.views, self.n_views, C.byref(self.params)))
+        if self.ws_bytes == 0:
+            raise B.DressiError("dressi_workspace_size rejected the arguments")
+        dev = scene.device
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def _stream(self):
+        return C.c_void_p(torch.cuda.current_stream(self.scene.device).cuda_stream)
+
+    def forward(self, store_layers: bool = True, out: Optional[torch.Tensor] = None,
+                ids: Optional[torch.Tensor] = None, pos=None, col=None, tex=None):
+        dev = self.scene.device
+        if out is None:
+            out = torch.empty(self.n_pix, 4, dtype=torch.float32, device=dev)
+        if store_layers and ids is None:
+            ids = torch.empty(self.K, self.n_pix, dtype=torch.int32, device=dev)
+        if not store_layers:
+            ids = None
+        sc = self.scene.c_struct(pos, col, tex)
+        code = self.lib.dressi_forward(C.byref(sc), self.views, self.n_views, C.byref(self.params), out.data_ptr(),
+                                       ids.data_ptr() if ids is not None else None, self.n_pix, self.ws.data_ptr(),
+                                       self.ws_bytes, self.status.data_ptr(), self._stream())
+        B.check(code, "dressi_forward")
+        return out, ids
+
+    def backward(self, grad_rgba: torch.Tensor, ids: Optional[torch.Tensor] = None, grad_pos=None, grad_col=None,
+                 grad_tex=None, pos=None, col=None, tex=None):
+        dev = self.scene.device
+        sc = self.scene.c_struct(pos, col, tex)
+        grad_rgba = grad_rgba.contiguous()
+        if grad_pos is None:
+            grad_pos = torch.empty(3, self.scene.n_verts_total, dtype=torch.float32, device=dev)
+        if grad_col is None and self.scene.col is not None and self.params.shade_mode == 0:
+            grad_col = torch.empty(3, self.scene.n_verts_total, dtype=torch.float32, device=dev)
+        if grad_tex is None and self.scene.tex is not None and self.params.shade_mode != 0:
+            grad_tex = torch.empty(self.scene.n_texels, 4, dtype=torch.float32, device=dev)
+        code = self.lib.dressi_backward(C.byref(sc), self.views, self.n_views, C.byref(self.params),
+                                        grad_rgba.data_ptr(), ids.data_ptr() if ids is not None else None,
+                                        self.n_pix, grad_pos.data_ptr(),
+                                        grad_col.data_ptr() if grad_col is not None else None,
+                                        grad_tex.data_ptr() if grad_tex is not None else None,
+                                        self.ws.data_ptr(), self.ws_bytes, self.status.data_ptr(), self._stream())
+        B.check(code, "dressi_backward")
+        return grad_pos, grad_col, grad_tex
+
+    def l2_grad(self, out: torch.Tensor, target: torch.Tensor, grad: Optional[torch.Tensor] = None,
+                loss: Optional[torch.Tensor] = None):
+        if grad is None:
+            grad = torch.empty_like(out)
+        code = self.lib.dressi_l2_loss_grad(out.data_ptr(), target.data_ptr(), out.numel(), grad.data_ptr(),
+                                            loss.data_ptr() if loss is not None else None, self._stream())
+        B.check(code, "dressi_l2_loss_grad")
+        return grad
+
+    def device_status(self) -> int:
+        return int(self.status.item())
+
+    def view_image(self, img: torch.Tensor, i: int) -> torch.Tensor:
+        v = self.views[i]
+        return img[v.pix_off: v.pix_off + v.width * v.height].view(v.height, v.width, -1)
+
+
+class DressiFn(torch.autograd.Function):
+    """out = HardSoftRas(pos, col, tex) for a fixed renderer (faces, UVs, views, params).
+
+    ``pos`` [3, V_total] and ``col`` [3, V_total] planar float32 and ``tex``
+    [texels, 4] as packed in the renderer's scene; returns ``[n_pix, 4]``.
+    With ``store_layers`` the forward keeps the per-pixel layer ids for the
+    backward, otherwise the backward re-rasterizes (checkpointing)."""
+
+    @staticmethod
+    def forward(ctx, pos, col, tex, renderer: Renderer, store_layers: bool = True):
+        pos = pos.detach().contiguous()
+        col = None if col is None else col.detach().contiguous()
+        tex = None if tex is None else tex.detach().contiguous()
+        out, ids = renderer.forward(store_layers=store_layers, pos=pos, col=col, tex=tex)
+        ctx.renderer = renderer
+        ctx.ids = ids
+        ctx.save_for_backward(pos, col if col is not None else torch.empty(0), tex if tex is not None else torch.empty(0))
+        ctx.has = (col is not None, tex is not None)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        pos, col, tex = ctx.saved_tensors
+        col = col if ctx.has[0] else None
+        tex = tex if ctx.has[1] else None
+        gp, gc, gt = ctx.renderer.backward(grad_out, ids=ctx.ids, pos=pos, col=col, tex=tex)
+        return gp, (gc if col is not None else None), (gt if tex is not None else None), None, None
+
+
+def render(pos, col, tex, renderer: Renderer, store_layers: bool = True):
+    return DressiFn.apply(pos, col, tex, renderer, store_layers)

@@ -1,0 +1,167 @@
+"""Helpers that run the CUDA path (through the C ABI) and the FP64 oracle on the
+same seeded scene and compare them.
+
+Tolerances:
+  * layer ids: bit-exact on every pixel whose discrete decisions have margin:
+    every face within r of the pixel is >= TAU_PX pixels from its hard/soft
+    boundary and from the candidate boundary dist = -r, and consecutive keys of
+    the K+1 best fragments differ by 0 (an exact tie, broken by face id on both
+    sides) or by >= TAU_KEY;
+  * forward rgba: max-abs <= 1e-5 on pixels that are stable and whose edge-mask
+    window holds only stable S^H pixels;
+  * gradients: relative L2 <= 1e-4 for dL/d(rgba) that is zero on unstable pixels.
+"""
+import numpy as np
+import torch
+from scipy import ndimage
+
+import oracle
+from paper_2204_01386_gb300 import PackedScene, Renderer
+
+TAU_PX = 1e-4
+TAU_KEY = 1e-6
+FWD_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+def rho_of(params, view):
+    S = max(view.width, view.height)
+    return max(1, int(np.floor(params.delta * S + 0.5)))
+
+
+def masks(o, params, view):
+    """(stable_ids, stable_values) boolean [h, w] from the oracle's margins."""
+    keys = o["key"]
+    gaps = np.diff(keys, axis=0)
+    with np.errstate(invalid="ignore"):
+        key_bad = ((gaps > 0) & (gaps < TAU_KEY)).any(0)
+    unstable = (o["margin_hard"] < TAU_PX) | (o["margin_cand"] < TAU_PX) | key_bad
+    sh_bad = o["margin_hard"] < TAU_PX
+    if params.edge_mode == 0:
+        r = rho_of(params, view)
+        sh_bad = ndimage.binary_dilation(sh_bad, structure=np.ones((2 * r + 1, 2 * r + 1), bool))
+    return ~unstable, ~(unstable | sh_bad)
+
+
+class GpuRun:
+    def __init__(self, scene, device="cuda", list_cap=0):
+        self.scene = scene
+        self.ps = PackedScene(scene.meshes, device)
+        self.r = Renderer(self.ps, scene.views, scene.params, list_cap=list_cap)
+
+    def forward(self, store_layers=True):
+        # layer ids are always kept here so they can be compared; whether the
+        # backward re-rasterizes is chosen in backward()
+        out, ids = self.r.forward(store_layers=True)
+        torch.cuda.synchronize()
+        self.out, self.ids = out, ids
+        return out, ids
+
+    def view_rgba(self, i):
+        return self.r.view_image(self.out, i).cpu().numpy().astype(np.float64)
+
+    def view_ids(self, i):
+        v = self.r.views[i]
+        return self.ids[:, v.pix_off: v.pix_off + v.width * v.height].view(-1, v.height, v.width).cpu().numpy()
+
+    def backward(self, grads_per_view, use_ids=True):
+        g = torch.zeros(self.r.n_pix, 4, dtype=torch.float32, device=self.ps.device)
+        for i, gv in enumerate(grads_per_view):
+            v = self.r.views[i]
+            g[v.pix_off: v.pix_off + v.width * v.height] = torch.as_tensor(
+                np.asarray(gv, np.float32).reshape(-1, 4), device=self.ps.device)
+        gp, gc, gt = self.r.backward(g, ids=self.ids if use_ids else None)
+        torch.cuda.synchronize()
+        return self.split(gp, gc, gt)
+
+    def split(self, gp, gc, gt):
+        """Per-mesh numpy gradients [V,3], [V,3] or None, [Ht,Wt,4] or None."""
+        res = []
+        for m, t in zip(self.scene.meshes, self.ps.table):
+            a, n = t.vert_off, t.n_verts
+            p = gp[:, a:a + n].t().cpu().numpy().astype(np.float64)
+            c = gc[:, a:a + n].t().cpu().numpy().astype(np.float64) if gc is not None else None
+            x = None
+            if gt is not None:
+                x = gt[t.tex_off: t.tex_off + t.tex_w * t.tex_h].view(t.tex_h, t.tex_w, 4).cpu().numpy().astype(np.float64)
+            res.append((p, c, x))
+        return res
+
+    def status(self):
+        return self.r.device_status()
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a)
+
+
+def window_of(view, win):
+    return (0, 0, view.width, view.height) if win is None else win
+
+
+def compare_scene(scene, windows=None, seed=0, grad_from_target=None, store_layers=True, list_cap=0,
+                  check_grads=True, report=None):
+    """Runs both paths on every view (restricted to ``windows``) and asserts parity.
+    Returns a dict of the measured errors."""
+    gpu = GpuRun(scene, list_cap=list_cap)
+    gpu.forward(store_layers=store_layers)
+    rng = np.random.default_rng(seed)
+    stats = dict(ids_checked=0, ids_unstable=0, fwd_err=0.0, fwd_checked=0)
+    grads = []
+    for i, v in enumerate(scene.views):
+        win = windows[i] if windows is not None else None
+        x0, y0, w, h = window_of(v, win)
+        o = oracle.render(scene.meshes[v.mesh], v, scene.params, window=win)
+        s_ids, s_val = masks(o, scene.params, v)
+        gi = gpu.view_ids(i)[:, y0:y0 + h, x0:x0 + w]
+        gi = np.where(gi < 0, -1, gi)
+        bad = (gi != o["ids"]).any(0) & s_ids
+        stats["ids_checked"] += int(s_ids.sum())
+        stats["ids_unstable"] += int((~s_ids).sum())
+        assert not bad.any(), f"view {i}: {bad.sum()} stable pixels with different layer ids, first at {np.argwhere(bad)[:3]}"
+        rgba = gpu.view_rgba(i)[y0:y0 + h, x0:x0 + w]
+        err = np.abs(rgba - o["rgba"])[s_val]
+        if err.size:
+            stats["fwd_err"] = max(stats["fwd_err"], float(err.max()))
+        stats["fwd_checked"] += int(s_val.sum())
+        # pixel gradient: L2 to a target image if given, else seeded noise; zero on unstable pixels
+        if grad_from_target is not None:
+            gv = 2.0 * (o["rgba"] - grad_from_target[i])
+        else:
+            gv = rng.normal(size=(h, w, 4))
+        gv = np.where(s_val[..., None], gv, 0.0)
+        full = np.zeros((v.height, v.width, 4))
+        full[y0:y0 + h, x0:x0 + w] = gv
+        grads.append(full)
+        stats.setdefault("per_view", []).append((gv, win))
+    assert stats["fwd_err"] <= FWD_TOL, f"forward max-abs error {stats['fwd_err']:.3e} > {FWD_TOL}"
+    if check_grads:
+        g_gpu = gpu.backward(grads, use_ids=store_layers)
+        res = [[np.zeros(m.pos.shape), None if m.col is None else np.zeros(m.col.shape),
+                None if m.tex is None else np.zeros(m.tex.shape)] for m in scene.meshes]
+        for i, v in enumerate(scene.views):
+            gv, win = stats["per_view"][i]
+            gp, gc, gt = oracle.backward(scene.meshes[v.mesh], v, scene.params, gv, window=win)
+            res[v.mesh][0] += gp
+            if gc is not None:
+                res[v.mesh][1] += gc
+            if gt is not None:
+                res[v.mesh][2] += gt
+        errs = {}
+        for mi, (o_, g_) in enumerate(zip(res, g_gpu)):
+            for name, a, b in (("pos", g_[0], o_[0]), ("col", g_[1], o_[1]), ("tex", g_[2], o_[2])):
+                if a is None or b is None or not np.any(b):
+                    continue
+                if name == "tex" and scene.params.shade_mode == 0:
+                    continue
+                e = rel_l2(a, b)
+                errs[f"{name}{mi}"] = e
+                assert e <= GRAD_TOL, f"mesh {mi} grad_{name} rel-L2 {e:.3e} > {GRAD_TOL}"
+        stats["grad_err"] = errs
+    stats.pop("per_view", None)
+    assert (gpu.status() & ~1) == 0, gpu.status()
+    stats["status"] = gpu.status()
+    if report is not None:
+        report.update(stats)
+    return stats

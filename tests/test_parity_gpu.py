@@ -1,0 +1,184 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from parity import GpuRun, compare_scene, masks, rel_l2
+from scenes_small import grid_mesh, pixel_mesh, pixel_scene
+
+pytestmark = pytest.mark.gpu
+
+
+def _target_images(scene, target, windows=None):
+    out = []
+    for i, v in enumerate(target.views):
+        win = None if windows is None else windows[i]
+        out.append(oracle.render(target.meshes[v.mesh], v, target.params, window=win)["rgba"])
+    return out
+
+
+@pytest.mark.parametrize("store_layers", [True, False])
+def test_config1_icosphere_vertex_colour(store_layers):
+    s = synth.config1()
+    t = synth.config1_target()
+    st = compare_scene(s, grad_from_target=_target_images(s, t), store_layers=store_layers)
+    assert st["ids_checked"] > 4000
+
+
+@pytest.mark.parametrize("store_layers", [True, False])
+def test_config2_textured_lambert(store_layers):
+    s = synth.config2()
+    t = synth.perturbed(s, 99)
+    st = compare_scene(s, grad_from_target=_target_images(s, t), store_layers=store_layers)
+    assert st["ids_checked"] > 60000
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 5])
+@pytest.mark.parametrize("edge_mode", [0, 1, 2])
+def test_layers_and_edge_modes(K, edge_mode):
+    s = synth.config1()
+    s.params = synth.Params(K=K, r=3 / 64, sigma=3 / 64 / 7, delta=2 / 64, edge_mode=edge_mode, shade_mode=0)
+    compare_scene(s, seed=K * 10 + edge_mode)
+
+
+@pytest.mark.parametrize("shade_mode", [1, 2])
+def test_unlit_and_lambert_small(shade_mode):
+    g = synth.rng(5)
+    pos, faces = synth.icosphere(3)
+    pos = synth.displace(pos, 0.1, 3)
+    pos, faces, uv = synth.icosphere_uv(pos, faces)
+    tex = np.zeros((96, 160, 4), np.float32)  # non-square, non power of two
+    tex[..., :3] = g.random((96, 160, 3))
+    m = synth.Mesh(pos.astype(np.float32), faces, uv=uv.astype(np.float32), tex=tex)
+    v = synth.View(synth.camera_mvp((1.0, 0.5, 2.6), 77, 53), 0, 77, 53)
+    p = synth.soft_params_px(77, shade_mode=shade_mode)
+    compare_scene(synth.Scene("small", [m], [v], p))
+
+
+def test_fp16_texture_storage():
+    s = synth.config5(subdiv=4, n_views=2, res=128, tex_side=256)
+    assert s.meshes[0].tex.dtype == np.float16
+    st = compare_scene(s, store_layers=False)
+    assert st["ids_checked"] > 10000
+
+
+def test_ragged_multi_mesh_multi_view():
+    g = synth.rng(3)
+    meshes, views = [], []
+    for m, (sl, st_, res) in enumerate([(12, 7, 40), (30, 17, 96), (8, 5, 23)]):
+        pos, faces, uv = synth.uv_sphere(sl, st_)
+        pos = synth.displace(pos, 0.1, m)
+        side = [64, 32, 48][m]
+        tex = np.zeros((side, side, 4), np.float32)
+        tex[..., :3] = g.random((side, side, 3))
+        meshes.append(synth.Mesh(pos.astype(np.float32), faces, uv=uv.astype(np.float32), tex=tex))
+        d = g.normal(size=3)
+        d /= np.linalg.norm(d)
+        views.append(synth.View(synth.camera_mvp(2.8 * d, res, res), m, res, res))
+    views.append(synth.View(synth.camera_mvp((0, 0, 3), 50, 31), 1, 50, 31))
+    s = synth.Scene("ragged", meshes, views, synth.soft_params_px(64, shade_mode=2))
+    compare_scene(s)
+
+
+def test_tile_list_overflow_falls_back_exactly():
+    s = synth.config1()
+    full = GpuRun(s)
+    out_a, _ = full.forward()
+    tiny = GpuRun(s, list_cap=16)
+    out_b, _ = tiny.forward()
+    assert tiny.status() & 1
+    assert torch.equal(out_a, out_b)
+    st = compare_scene(s, list_cap=16, check_grads=False)
+    assert st["status"] & 1
+
+
+def test_face_index_out_of_range_is_skipped():
+    s = synth.config1()
+    f = s.meshes[0].faces.copy()
+    f[7] = (0, 1, 10 ** 6)
+    s.meshes[0].faces = f
+    gpu = GpuRun(s)
+    gpu.forward()
+    assert gpu.status() & 2
+    o = oracle.render(s.meshes[0], s.views[0], s.params)
+    assert o["status"] & 4
+    si, sv = masks(o, s.params, s.views[0])
+    assert (gpu.view_ids(0)[:, si] == o["ids"][:, si]).all()
+    assert np.abs(gpu.view_rgba(0)[sv] - o["rgba"][sv]).max() <= 1e-5
+
+
+def test_nonfinite_vertex_skips_its_faces():
+    s = synth.config1()
+    p = s.meshes[0].pos.copy()
+    p[5, 1] = np.nan
+    s.meshes[0].pos = p
+    gpu = GpuRun(s)
+    gpu.forward()
+    assert gpu.status() & 4
+    o = oracle.render(s.meshes[0], s.views[0], s.params)
+    si, sv = masks(o, s.params, s.views[0])
+    assert (gpu.view_ids(0)[:, si] == o["ids"][:, si]).all()
+
+
+def test_empty_view_renders_nothing():
+    s = synth.config1()
+    s.views[0].mvp = synth.camera_mvp((0, 0, -0.5), 64, 64)  # inside the sphere looking out: faces behind / clipped
+    s.views = [synth.View(synth.camera_mvp((0, 0, 30.0), 64, 64), 0, 64, 64)]
+    s.views[0].mvp = (s.views[0].mvp.reshape(4, 4) @ np.diag([1, 1, 1, 1]).astype(np.float32)).reshape(16)
+    far = synth.Mesh(s.meshes[0].pos + np.float32(100.0), s.meshes[0].faces, col=s.meshes[0].col)
+    s.meshes = [far]
+    gpu = GpuRun(s)
+    out, ids = gpu.forward()
+    assert torch.count_nonzero(out) == 0
+    assert (ids == -1).all()
+    g = gpu.backward([np.ones((64, 64, 4))])
+    assert not np.any(g[0][0]) and not np.any(g[0][1])
+
+
+def test_exact_fill_rule_on_gpu():
+    """Pixel centres exactly on shared diagonals: every pixel has one hard face."""
+    W = H = 40
+    V, F = grid_mesh(9, W, H)
+    V = np.round(V)
+    s = pixel_scene(pixel_mesh(V, F, W, H), W, H, K=2, r=1 / 40, sigma=0.3 / 40, delta=1 / 40)
+    gpu = GpuRun(s)
+    gpu.forward()
+    o = oracle.render(s.meshes[0], s.views[0], s.params)
+    assert (gpu.view_ids(0) == o["ids"]).all()
+    assert (gpu.view_rgba(0)[..., 3] == 1.0).all()
+
+
+def test_store_and_recompute_backward_agree():
+    s = synth.config2()
+    gpu = GpuRun(s)
+    gpu.forward(store_layers=True)
+    g = [np.random.default_rng(1).normal(size=(256, 256, 4))]
+    a = gpu.backward(g, use_ids=True)
+    b = gpu.backward(g, use_ids=False)
+    for x, y in zip(a[0], b[0]):
+        if x is not None:
+            assert rel_l2(x, y) < 1e-6
+
+
+@pytest.mark.parametrize("views", [[0, 37]])
+def test_config3_full_size_sampled(views):
+    """64 views x 512^2, 20,480 tris, 1024^2 texture, run in full on the GPU;
+    checked on 48 x 48 crops of two views (gradients with dL/dI zero elsewhere)."""
+    s = synth.config3()
+    wins = []
+    for i, v in enumerate(s.views):
+        wins.append((232, 200, 48, 48) if i in views else (0, 0, 0, 0))
+    # views outside the sample get zero-size windows (no pixels compared, zero gradient)
+    st = compare_scene(s, windows=wins)
+    assert st["ids_checked"] > 2000
+
+
+def test_config5_full_size_crop():
+    """1.31M tris, 4096^2 FP16 texture, 8 views at 2048^2, recompute backward;
+    checked on a 64 x 64 crop of one view."""
+    s = synth.config5()
+    wins = [(992, 1000, 64, 64)] + [(0, 0, 0, 0)] * (len(s.views) - 1)
+    st = compare_scene(s, windows=wins, store_layers=False)
+    assert st["ids_checked"] > 3000
