@@ -112,7 +112,7 @@ def time_oracle(scene, n_views, seed=0):
 def reference_arm(args, rank, world):
     if rank != 0:
         return
-    s = workload_scene(0, 1)
+    s = workload_scene(0, 1, n_views=args.views)
     views_per_step = 1
     for _ in range(args.warmup):
         time_oracle(s, views_per_step)
@@ -168,7 +168,7 @@ def ours(args, rank, world, local_rank):
     dist = None
     if world > 1:
         import torch.distributed as dist
-    s = workload_scene(rank, world)
+    s = workload_scene(rank, world, n_views=args.views)
     tgt_scene = synth.perturbed(s, 4321 + rank)
     ps = PackedScene(s.meshes, dev)
     r = Renderer(ps, s.views, s.params)
@@ -321,6 +321,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-views", type=int, default=12)
+    ap.add_argument("--views", type=int, default=64, help="views per rank (64 = the benchmark workload)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))

@@ -61,7 +61,8 @@ class _FwdOut(C.Structure):
                 ("hard", C.POINTER(C.c_int32)), ("dist", C.POINTER(C.c_double)),
                 ("key", C.POINTER(C.c_double)), ("sh", C.POINTER(C.c_uint8)),
                 ("edge", C.POINTER(C.c_uint8)), ("margin_hard", C.POINTER(C.c_double)),
-                ("margin_cand", C.POINTER(C.c_double)), ("n_hard", C.POINTER(C.c_int32))]
+                ("margin_cand", C.POINTER(C.c_double)), ("n_hard", C.POINTER(C.c_int32)),
+                ("feat_hash", C.POINTER(C.c_uint64))]
 
 
 def _load():
@@ -139,7 +140,8 @@ def render(mesh, view, params, window=None, brute_force=False):
 
     Returns a dict with ``rgba [h,w,4]``, ``ids``/``hard``/``dist`` ``[K,h,w]``,
     ``key [K+1,h,w]``, ``sh``/``edge [h,w]``, ``margin_hard``/``margin_cand``
-    (pixel units) and ``n_hard`` plus the oracle's status word.
+    (pixel units), ``n_hard``, ``feat_hash [K+1,h,w]`` (identity of each
+    fragment's closest feature) plus the oracle's status word.
     """
     lib = _load()
     inp = _Inputs(mesh, view, params, brute_force)
@@ -149,10 +151,12 @@ def render(mesh, view, params, window=None, brute_force=False):
                hard=np.zeros((K, h, w), np.int32), dist=np.zeros((K, h, w)),
                key=np.zeros((K + 1, h, w)), sh=np.zeros((h, w), np.uint8),
                edge=np.zeros((h, w), np.uint8), margin_hard=np.zeros((h, w)),
-               margin_cand=np.zeros((h, w)), n_hard=np.zeros((h, w), np.int32))
+               margin_cand=np.zeros((h, w)), n_hard=np.zeros((h, w), np.int32),
+               feat_hash=np.zeros((K + 1, h, w), np.uint64))
     o = _FwdOut(_dp(res["rgba"]), _ip(res["ids"]), _ip(res["hard"]), _dp(res["dist"]),
                 _dp(res["key"]), _up(res["sh"]), _up(res["edge"]), _dp(res["margin_hard"]),
-                _dp(res["margin_cand"]), _ip(res["n_hard"]))
+                _dp(res["margin_cand"]), _ip(res["n_hard"]),
+                res["feat_hash"].ctypes.data_as(C.POINTER(C.c_uint64)))
     st = lib.orc_forward(C.byref(inp.view), C.byref(inp.params), C.byref(win), C.byref(o))
     if st & 1:
         raise ValueError("oracle: invalid argument")

@@ -80,6 +80,10 @@ typedef struct {           /* every pointer optional; sizes in units of the wind
     double *margin_hard;   /* [h][w] min |dist| in pixels over faces within r of p */
     double *margin_cand;   /* [h][w] min |dist + r| in pixels over faces */
     int32_t *n_hard;       /* [h][w] number of faces whose hard region holds p */
+    uint64_t *feat_hash;   /* [K+1][h][w] identity of each fragment's closest boundary feature
+                              (hash of the corner, or of the two corners of the edge, in pixel
+                              coordinates; hard fragments hash their face id) -- tells exact ties
+                              of one shared feature from coincidences of distinct features */
 } orc_fwd_out;
 
 enum { ORC_OK = 0, ORC_BAD_ARG = 1, ORC_FACE_RANGE = 4 };
@@ -241,6 +245,26 @@ static double eval_face(const face_t *t, int id, double px, double py, double S,
         fr->key = 0.5 * fabs(dist / S) + 0.5;
     }
     return dist;
+}
+
+static uint64_t mix64(uint64_t h, double x)
+{
+    uint64_t b;
+    memcpy(&b, &x, sizeof b);
+    h ^= b + 0x9E3779B97F4A7C15ULL + (h << 6) + (h >> 2);
+    h ^= h >> 31;
+    h *= 0xBF58476D1CE4E5B9ULL;
+    return h ^ (h >> 29);
+}
+
+static uint64_t feature_hash(const face_t *t, const frag_t *fr)
+{
+    if (fr->hard) return mix64(0x1234567ULL, (double)fr->id);
+    if (fr->feat >= 3) {
+        int m = fr->feat - 3;
+        return mix64(mix64(0x77ULL, t->X[m]), t->Y[m]);
+    }
+    return mix64(mix64(mix64(mix64(0x99ULL, t->X[fr->segP]), t->Y[fr->segP]), t->X[fr->segQ]), t->Y[fr->segQ]);
 }
 
 static int frag_less(const frag_t *a, const frag_t *b)
@@ -566,6 +590,9 @@ int orc_forward(const orc_view *v, const orc_params *prm, const orc_window *w, o
             }
             if (out->key)
                 for (int k = 0; k <= K; ++k) out->key[k * plane + o] = k < P->n ? P->f[k].key : INFINITY;
+            if (out->feat_hash)
+                for (int k = 0; k <= K; ++k)
+                    out->feat_hash[k * plane + o] = k < P->n ? feature_hash(&c.F[P->f[k].id], &P->f[k]) : 0;
             if (out->sh) out->sh[o] = (uint8_t)SH;
             if (out->edge) out->edge[o] = (uint8_t)E;
             if (out->margin_hard) out->margin_hard[o] = P->m_hard;

@@ -61,7 +61,8 @@ struct __align__(16) VRec {
 // per-face record used by every pixel evaluation
 struct FaceRec {
     float xh[3], xl[3], yh[3], yl[3];
-    float invL[3];   // 1 / length of edge i (canonical)
+    float L[3];      // length of edge i (canonical)
+    float invL[3];   // 1 / L
     float z[3];
     float invA;      // 1 / |twice the signed area|
     int flags;       // bit 0: orient > 0; bits 1-3: edge i swapped; bits 4-6: edge i owns;
@@ -165,6 +166,7 @@ __device__ __forceinline__ bool face_load(const Globals &g, const MeshK &m, cons
         float ex = fadd(fsub(a[Q].xh, a[P].xh), fsub(a[Q].xl, a[P].xl));
         float ey = fadd(fsub(a[Q].yh, a[P].yh), fsub(a[Q].yl, a[P].yl));
         float L = __fsqrt_rn(ffma(ex, ex, fmul(ey, ey)));
+        R.L[i] = L;
         R.invL[i] = __fdiv_rn(1.f, L);
         // oriented edge ia -> ib
         float eox = sw ? -ex : ex, eoy = sw ? -ey : ey;
@@ -225,9 +227,15 @@ __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, 
     float dist, bt = 0.f;
     int feat;
     if (inside) {
-        dist = F[0]; feat = 0;
-        if (F[1] < dist) { dist = F[1]; feat = 1; }
-        if (F[2] < dist) { dist = F[2]; feat = 2; }
+        float a = F[0];
+        feat = 0;
+        if (F[1] < a) { a = F[1]; feat = 1; }
+        if (F[2] < a) { a = F[2]; feat = 2; }
+        // the selected distance itself correctly rounded: Fn / L
+        float fnw = o.Fn[0], Lw = R.L[0];
+        if (feat == 1) { fnw = o.Fn[1]; Lw = R.L[1]; }
+        if (feat == 2) { fnw = o.Fn[2]; Lw = R.L[2]; }
+        dist = __fdiv_rn(fnw, Lw);
     } else {
         float best = 3.4e38f;
         feat = 0;
@@ -255,6 +263,13 @@ __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, 
                 }
             }
             if (s < best) { best = s; feat = ft; bt = tt; }
+        }
+        if (feat < 3) {
+            // edge interior: recompute the selected distance correctly rounded, |c| / L
+            float cw = c[0], Lw = R.L[0];
+            if (feat == 1) { cw = c[1]; Lw = R.L[1]; }
+            if (feat == 2) { cw = c[2]; Lw = R.L[2]; }
+            best = __fdiv_rn(fabsf(cw), Lw);
         }
         dist = -best;
     }

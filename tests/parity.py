@@ -5,8 +5,8 @@ Tolerances:
   * layer ids: bit-exact on every pixel whose discrete decisions have margin:
     every face within r of the pixel is >= TAU_PX pixels from its hard/soft
     boundary and from the candidate boundary dist = -r, and consecutive keys of
-    the K+1 best fragments differ by 0 (an exact tie, broken by face id on both
-    sides) or by >= TAU_KEY;
+    the K+1 best fragments differ by >= TAU_KEY, or by exactly 0 with the same
+    closest feature (a shared edge or corner, broken by face id on both sides);
   * forward rgba: max-abs <= 1e-5 on pixels that are stable and whose edge-mask
     window holds only stable S^H pixels;
   * gradients: relative L2 <= 1e-4 for dL/d(rgba) that is zero on unstable pixels.
@@ -33,8 +33,12 @@ def masks(o, params, view):
     """(stable_ids, stable_values) boolean [h, w] from the oracle's margins."""
     keys = o["key"]
     gaps = np.diff(keys, axis=0)
+    fh = o["feat_hash"]
+    same_feature = fh[1:] == fh[:-1]
     with np.errstate(invalid="ignore"):
-        key_bad = ((gaps > 0) & (gaps < TAU_KEY)).any(0)
+        # an exact tie of one shared edge / corner is computed identically on both sides;
+        # a tie (or near tie) of distinct features is decided by rounding
+        key_bad = ((gaps < TAU_KEY) & ~((gaps == 0) & same_feature)).any(0)
     unstable = (o["margin_hard"] < TAU_PX) | (o["margin_cand"] < TAU_PX) | key_bad
     sh_bad = o["margin_hard"] < TAU_PX
     if params.edge_mode == 0:

@@ -123,12 +123,11 @@ def test_nonfinite_vertex_skips_its_faces():
 
 
 def test_empty_view_renders_nothing():
+    """Mesh moved far outside the frustum: nothing is binned, the image and all
+    gradients are zero."""
     s = synth.config1()
-    s.views[0].mvp = synth.camera_mvp((0, 0, -0.5), 64, 64)  # inside the sphere looking out: faces behind / clipped
-    s.views = [synth.View(synth.camera_mvp((0, 0, 30.0), 64, 64), 0, 64, 64)]
-    s.views[0].mvp = (s.views[0].mvp.reshape(4, 4) @ np.diag([1, 1, 1, 1]).astype(np.float32)).reshape(16)
-    far = synth.Mesh(s.meshes[0].pos + np.float32(100.0), s.meshes[0].faces, col=s.meshes[0].col)
-    s.meshes = [far]
+    m = s.meshes[0]
+    s.meshes = [synth.Mesh(m.pos + np.float32(100.0), m.faces, col=m.col)]
     gpu = GpuRun(s)
     out, ids = gpu.forward()
     assert torch.count_nonzero(out) == 0
@@ -138,15 +137,19 @@ def test_empty_view_renders_nothing():
 
 
 def test_exact_fill_rule_on_gpu():
-    """Pixel centres exactly on shared diagonals: every pixel has one hard face."""
-    W = H = 40
+    """Pixel centres exactly on shared diagonals: every pixel has one hard face.
+    W = 64 keeps the object-space corners X/32 - 1 exact in float32."""
+    W = H = 64
     V, F = grid_mesh(9, W, H)
     V = np.round(V)
-    s = pixel_scene(pixel_mesh(V, F, W, H), W, H, K=2, r=1 / 40, sigma=0.3 / 40, delta=1 / 40)
+    s = pixel_scene(pixel_mesh(V, F, W, H), W, H, K=2, r=1 / 64, sigma=0.3 / 64, delta=1 / 64)
     gpu = GpuRun(s)
     gpu.forward()
     o = oracle.render(s.meshes[0], s.views[0], s.params)
-    assert (gpu.view_ids(0) == o["ids"]).all()
+    assert (gpu.view_ids(0)[0] == o["ids"][0]).all()      # the owning face, everywhere
+    si, _ = masks(o, s.params, s.views[0])
+    assert si.mean() > 0.5
+    assert (gpu.view_ids(0)[:, si] == o["ids"][:, si]).all()
     assert (gpu.view_rgba(0)[..., 3] == 1.0).all()
 
 
