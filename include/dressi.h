@@ -153,6 +153,29 @@ DRESSI_API int dressi_backward(const dressi_scene *scene, const dressi_view *vie
                     int64_t n_pix, float *grad_pos, float *grad_col, float *grad_tex,
                     void *ws, size_t ws_bytes, int32_t *dev_status, void *stream);
 
+/* Size of the library's static device scratch array used by
+   dressi_forward_static_scratch (bytes; held on every GPU that loads the library). */
+#define DRESSI_STATIC_SCRATCH_BYTES (32u << 20)
+
+/* dressi_forward without a caller workspace (the paper has no counterpart: this is
+   an interface for callers that cannot allocate device memory, e.g. a plugin whose
+   host application owns every device allocation, or a frame loop that must not pay
+   cudaMalloc's implicit device synchronisation).  Same arguments and results as
+   dressi_forward; the scratch space is a file-scope device array of
+   DRESSI_STATIC_SCRATCH_BYTES inside the library instead of `ws`.
+     - Scenes whose dressi_workspace_size() exceeds DRESSI_STATIC_SCRATCH_BYTES are
+       rejected with DRESSI_ERR_WORKSPACE before anything is enqueued.
+     - The first call on a device looks up the array's device address on the current
+       device (once per device); make that first call before any stream capture.
+     - The library allocates nothing here (no cudaMalloc / cudaFree); the counters the
+       pass needs zeroed are cleared on `stream` at every call.
+     - All calls on a device share the one array, which keeps the last call's
+       contents: calls that overlap on the GPU (different streams, or different host
+       threads) race on it and must be serialised by the caller. */
+DRESSI_API int dressi_forward_static_scratch(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
+                                             const dressi_params *params, float *out_rgba, int32_t *layer_ids,
+                                             int64_t n_pix, int32_t *dev_status, void *stream);
+
 /* L2 loss helper for training loops: grad[i] = 2 (out[i] - target[i]) over n floats and
    *loss_accum += sum (out - target)^2 (DEVICE float, accumulated atomically). */
 DRESSI_API int dressi_l2_loss_grad(const float *out, const float *target, int64_t n, float *grad,

@@ -51,6 +51,9 @@ SIGNATURES = {
     "dressi_backward": (C.c_int, [C.POINTER(DressiScene), C.POINTER(DressiView), C.c_int32, C.POINTER(DressiParams),
                                   C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
+    "dressi_forward_static_scratch": (C.c_int, [C.POINTER(DressiScene), C.POINTER(DressiView), C.c_int32,
+                                                C.POINTER(DressiParams), C.c_void_p, C.c_void_p, C.c_int64,
+                                                C.c_void_p, C.c_void_p]),
     "dressi_l2_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dressi_status_string": (C.c_char_p, [C.c_int]),
     "dressi_dev_status_string": (C.c_char_p, [C.c_int]),

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "dressi_core.cuh"
@@ -247,6 +248,32 @@ static void run_setup(const Globals &g, const Plan &P, char *ws, bool need_bins,
     }
 }
 
+// ---------------------------------------------------------------------------
+// static scratch for dressi_forward_static_scratch: callers that cannot allocate
+// device memory get the workspace from this file-scope device array.  In host code
+// the array's name is only a host-side stand-in, so its device address is looked up
+// once per device (with that device current) and cached.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_static_scratch[DRESSI_STATIC_SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+static void *g_static_scratch_addr[MAX_DEVICES] = {};
+static std::mutex g_static_scratch_mu;
+
+// device address of g_static_scratch on the current device, or nullptr on failure
+static void *static_scratch_address()
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return nullptr;
+    std::lock_guard<std::mutex> lock(g_static_scratch_mu);
+    if (!g_static_scratch_addr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) return nullptr;
+        g_static_scratch_addr[dev] = ptr;
+    }
+    return g_static_scratch_addr[dev];
+}
+
 }  // namespace dressi
 
 using namespace dressi;
@@ -313,6 +340,20 @@ int dressi_forward(const dressi_scene *scene, const dressi_view *views, int32_t 
     run_setup(g, P, w, true, s);
     launch_tile_profiled(g, false, s);
     return cudaGetLastError() == cudaSuccess ? DRESSI_OK : DRESSI_ERR_LAUNCH;
+}
+
+int dressi_forward_static_scratch(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
+                                  const dressi_params *params, float *out_rgba, int32_t *layer_ids, int64_t n_pix,
+                                  int32_t *dev_status, void *stream)
+{
+    Plan P;
+    if (!out_rgba || !dev_status || n_pix < 1) return DRESSI_ERR_ARG;
+    if (!make_plan(scene, views, n_views, params, n_pix, P)) return DRESSI_ERR_ARG;
+    if (P.lay.total > (size_t)DRESSI_STATIC_SCRATCH_BYTES) return DRESSI_ERR_WORKSPACE;
+    void *ws = static_scratch_address();
+    if (!ws) return DRESSI_ERR_LAUNCH;
+    return dressi_forward(scene, views, n_views, params, out_rgba, layer_ids, n_pix, ws,
+                          (size_t)DRESSI_STATIC_SCRATCH_BYTES, dev_status, stream);
 }
 
 int dressi_backward(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
