@@ -141,36 +141,42 @@ __device__ __forceinline__ bool face_load(const Globals &g, const MeshK &m, cons
         return false;
     }
     R.vi[0] = v0; R.vi[1] = v1; R.vi[2] = v2;
-    VRec a[3];
-    a[0] = vr[v0]; a[1] = vr[v1]; a[2] = vr[v2];
-    bool live = a[0].valid && a[1].valid && a[2].valid;
+    // two 16-byte loads per corner, kept in scalars (an array of records would live in local memory)
+    bool live = true;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        R.xh[i] = a[i].xh; R.xl[i] = a[i].xl; R.yh[i] = a[i].yh; R.yl[i] = a[i].yl;
-        R.z[i] = a[i].z; R.iw[i] = a[i].iw;
+        const float4 *rec = reinterpret_cast<const float4 *>(vr + R.vi[i]);
+        const float4 p = rec[0], q = rec[1];
+        R.xh[i] = p.x; R.xl[i] = p.y; R.yh[i] = p.z; R.yl[i] = p.w;
+        R.z[i] = q.x; R.iw[i] = q.y;
+        live = live && (__float_as_int(q.z) != 0);
     }
     // twice the signed area from accurate corner differences
-    float ux = fadd(fsub(a[1].xh, a[0].xh), fsub(a[1].xl, a[0].xl));
-    float uy = fadd(fsub(a[1].yh, a[0].yh), fsub(a[1].yl, a[0].yl));
-    float wx = fadd(fsub(a[2].xh, a[0].xh), fsub(a[2].xl, a[0].xl));
-    float wy = fadd(fsub(a[2].yh, a[0].yh), fsub(a[2].yl, a[0].yl));
-    float A2 = ffma(ux, wy, -fmul(uy, wx));
+    const float ux = fadd(fsub(R.xh[1], R.xh[0]), fsub(R.xl[1], R.xl[0]));
+    const float uy = fadd(fsub(R.yh[1], R.yh[0]), fsub(R.yl[1], R.yl[0]));
+    const float wx = fadd(fsub(R.xh[2], R.xh[0]), fsub(R.xl[2], R.xl[0]));
+    const float wy = fadd(fsub(R.yh[2], R.yh[0]), fsub(R.yl[2], R.yl[0]));
+    const float A2 = ffma(ux, wy, -fmul(uy, wx));
     if (!(A2 != 0.f) || !isfinite(A2)) live = false;
-    bool orient = A2 > 0.f;
+    const bool orient = A2 > 0.f;
     int flags = orient ? 1 : 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        int ia = i, ib = (i + 1) % 3;
-        bool sw = lex_less(a[ib].xh, a[ib].xl, a[ib].yh, a[ib].yl, a[ia].xh, a[ia].xl, a[ia].yh, a[ia].yl);
-        int P = sw ? ib : ia, Q = sw ? ia : ib;
-        float ex = fadd(fsub(a[Q].xh, a[P].xh), fsub(a[Q].xl, a[P].xl));
-        float ey = fadd(fsub(a[Q].yh, a[P].yh), fsub(a[Q].yl, a[P].yl));
-        float L = __fsqrt_rn(ffma(ex, ex, fmul(ey, ey)));
+        const int ia = i, ib = (i + 1) % 3;
+        const bool sw = lex_less(R.xh[ib], R.xl[ib], R.yh[ib], R.yl[ib], R.xh[ia], R.xl[ia], R.yh[ia], R.yl[ia]);
+        // canonical edge P -> Q
+        const float Pxh = sw ? R.xh[ib] : R.xh[ia], Pxl = sw ? R.xl[ib] : R.xl[ia];
+        const float Pyh = sw ? R.yh[ib] : R.yh[ia], Pyl = sw ? R.yl[ib] : R.yl[ia];
+        const float Qxh = sw ? R.xh[ia] : R.xh[ib], Qxl = sw ? R.xl[ia] : R.xl[ib];
+        const float Qyh = sw ? R.yh[ia] : R.yh[ib], Qyl = sw ? R.yl[ia] : R.yl[ib];
+        const float ex = fadd(fsub(Qxh, Pxh), fsub(Qxl, Pxl));
+        const float ey = fadd(fsub(Qyh, Pyh), fsub(Qyl, Pyl));
+        const float L = __fsqrt_rn(ffma(ex, ex, fmul(ey, ey)));
         R.L[i] = L;
         R.invL[i] = __fdiv_rn(1.f, L);
         // oriented edge ia -> ib
-        float eox = sw ? -ex : ex, eoy = sw ? -ey : ey;
-        bool owns = orient ? (eoy < 0.f || (eoy == 0.f && eox > 0.f)) : (eoy > 0.f || (eoy == 0.f && eox < 0.f));
+        const float eox = sw ? -ex : ex, eoy = sw ? -ey : ey;
+        const bool owns = orient ? (eoy < 0.f || (eoy == 0.f && eox > 0.f)) : (eoy > 0.f || (eoy == 0.f && eox < 0.f));
         flags |= (sw ? 1 : 0) << (1 + i);
         flags |= (owns ? 1 : 0) << (4 + i);
     }
@@ -193,6 +199,8 @@ struct Frag {
 // SignedDist, candidate rule, hard test (top-left fill rule) and Shift (Eq. Shift) of
 // face R at pixel centre (px, py).  Returns false when the face is not a candidate
 // (farther than r_px outside).  Pure function of (R, px, py, r_px, half_inv_S).
+// Every array index below is a compile-time constant (canonical endpoints are
+// chosen by selects), so nothing spills to local memory.
 __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, float r_px, float half_inv_S,
                                           Frag &o)
 {
@@ -203,16 +211,18 @@ __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, 
         dy[i] = fsub(fsub(py, R.yh[i]), R.yl[i]);
     }
     const bool orient = R.flags & 1;
-    float c[3], F[3];
+    // canonical endpoint offsets p - P and p - Q of every edge
+    float pX[3], pY[3], qX[3], qY[3], c[3], F[3];
     bool early_out = false;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const bool sw = (R.flags >> (1 + i)) & 1;
         const int ia = i, ib = (i + 1) % 3;
-        const int P = sw ? ib : ia, Q = sw ? ia : ib;
+        pX[i] = sw ? dx[ib] : dx[ia]; pY[i] = sw ? dy[ib] : dy[ia];
+        qX[i] = sw ? dx[ia] : dx[ib]; qY[i] = sw ? dy[ia] : dy[ib];
         // cross(Q - P, p - P) == cross(p - P, p - Q)
-        c[i] = ffma(dx[P], dy[Q], -fmul(dy[P], dx[Q]));
-        float fn = (orient != sw) ? c[i] : -c[i];
+        c[i] = ffma(pX[i], qY[i], -fmul(pY[i], qX[i]));
+        const float fn = (orient != sw) ? c[i] : -c[i];
         o.Fn[i] = fn;
         F[i] = fmul(fn, R.invL[i]);
         early_out |= F[i] < -r_px;
@@ -237,39 +247,42 @@ __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, 
         if (feat == 2) { fnw = o.Fn[2]; Lw = R.L[2]; }
         dist = __fdiv_rn(fnw, Lw);
     } else {
-        float best = 3.4e38f;
+        float best = 3.4e38f, btn = 0.f, btd = 1.f;
         feat = 0;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const bool sw = (R.flags >> (1 + i)) & 1;
             const int ia = i, ib = (i + 1) % 3;
-            const int P = sw ? ib : ia, Q = sw ? ia : ib;
-            float ex = fsub(dx[P], dx[Q]), ey = fsub(dy[P], dy[Q]);   // V_Q - V_P
-            float tP = ffma(dx[P], ex, fmul(dy[P], ey));
-            float s, tt = 0.f;
+            const float ex = fsub(pX[i], qX[i]), ey = fsub(pY[i], qY[i]);   // V_Q - V_P
+            const float tP = ffma(pX[i], ex, fmul(pY[i], ey));
+            float s;
             int ft;
             if (tP <= 0.f) {
-                s = __fsqrt_rn(ffma(dx[P], dx[P], fmul(dy[P], dy[P])));
-                ft = 3 + P;
+                s = __fsqrt_rn(ffma(pX[i], pX[i], fmul(pY[i], pY[i])));
+                ft = 3 + (sw ? ib : ia);
             } else {
-                float tQ = ffma(dx[Q], ex, fmul(dy[Q], ey));
+                const float tQ = ffma(qX[i], ex, fmul(qY[i], ey));
                 if (tQ >= 0.f) {
-                    s = __fsqrt_rn(ffma(dx[Q], dx[Q], fmul(dy[Q], dy[Q])));
-                    ft = 3 + Q;
+                    s = __fsqrt_rn(ffma(qX[i], qX[i], fmul(qY[i], qY[i])));
+                    ft = 3 + (sw ? ia : ib);
                 } else {
                     s = fmul(fabsf(c[i]), R.invL[i]);
                     ft = i;
-                    tt = __fdiv_rn(tP, ffma(ex, ex, fmul(ey, ey)));
                 }
             }
-            if (s < best) { best = s; feat = ft; bt = tt; }
+            if (s < best) {
+                best = s; feat = ft;
+                btn = tP; btd = ffma(ex, ex, fmul(ey, ey));
+            }
         }
         if (feat < 3) {
-            // edge interior: recompute the selected distance correctly rounded, |c| / L
+            // edge interior: recompute the selected distance correctly rounded, |c| / L,
+            // and the closest point's parameter along the edge
             float cw = c[0], Lw = R.L[0];
             if (feat == 1) { cw = c[1]; Lw = R.L[1]; }
             if (feat == 2) { cw = c[2]; Lw = R.L[2]; }
             best = __fdiv_rn(fabsf(cw), Lw);
+            bt = __fdiv_rn(btn, btd);
         }
         dist = -best;
     }
@@ -288,9 +301,32 @@ __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, 
     return true;
 }
 
+// Screen-space barycentrics of a fragment: area ratios inside the hard face; for a
+// soft fragment those of its closest point of the hard face (a corner, or the point
+// at parameter t along the canonical edge P -> Q).
+__device__ __forceinline__ void frag_lambda(const FaceRec &R, const Frag &fr, float lam[3])
+{
+    if (fr.hard) {
+        lam[0] = fr.Fn[1] * R.invA;
+        lam[1] = fr.Fn[2] * R.invA;
+        lam[2] = fr.Fn[0] * R.invA;
+        return;
+    }
+    if (fr.feat >= 3) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) lam[j] = (j == fr.feat - 3) ? 1.f : 0.f;
+        return;
+    }
+    const int i = fr.feat;
+    const bool sw = (R.flags >> (1 + i)) & 1;
+    const int P = sw ? (i + 1) % 3 : i, Q = sw ? i : (i + 1) % 3;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) lam[j] = (j == P) ? 1.f - fr.t : ((j == Q) ? fr.t : 0.f);
+}
+
 // Hard test only (for S^H of halo pixels): true if p lies in the closed face under
-// the fill rule; hkey receives the Shift() key of the hard fragment.
-__device__ __forceinline__ bool hard_test(const FaceRec &R, float px, float py, float &hkey)
+// the fill rule.
+__device__ __forceinline__ bool hard_test(const FaceRec &R, float px, float py)
 {
     float dx[3], dy[3];
 #pragma unroll
@@ -299,22 +335,19 @@ __device__ __forceinline__ bool hard_test(const FaceRec &R, float px, float py, 
         dy[i] = fsub(fsub(py, R.yh[i]), R.yl[i]);
     }
     const bool orient = R.flags & 1;
-    float Fn[3];
     bool inside = true;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const bool sw = (R.flags >> (1 + i)) & 1;
         const int ia = i, ib = (i + 1) % 3;
-        const int P = sw ? ib : ia, Q = sw ? ia : ib;
-        float c = ffma(dx[P], dy[Q], -fmul(dy[P], dx[Q]));
-        Fn[i] = (orient != sw) ? c : -c;
+        const float pX = sw ? dx[ib] : dx[ia], pY = sw ? dy[ib] : dy[ia];
+        const float qX = sw ? dx[ia] : dx[ib], qY = sw ? dy[ia] : dy[ib];
+        const float c = ffma(pX, qY, -fmul(pY, qX));
+        const float fn = (orient != sw) ? c : -c;
         const bool owns = (R.flags >> (4 + i)) & 1;
-        inside &= (Fn[i] > 0.f) || (Fn[i] == 0.f && owns);
+        inside &= (fn > 0.f) || (fn == 0.f && owns);
     }
-    if (!inside) return false;
-    float zs = ffma(Fn[1], R.z[0], ffma(Fn[2], R.z[1], fmul(Fn[0], R.z[2])));
-    hkey = fmul(0.5f, fmul(zs, R.invA));
-    return true;
+    return inside;
 }
 
 __device__ __forceinline__ bool frag_less(float ka, int ia, float kb, int ib)

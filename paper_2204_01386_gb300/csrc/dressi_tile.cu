@@ -28,11 +28,15 @@ constexpr int TT = 16;                 // tile edge
 constexpr int NT = TT * TT;            // threads per CTA
 constexpr int RHO_MAX = 8;             // largest supported edge-mask radius
 constexpr int HS_MAX = TT + 2 * RHO_MAX;
+constexpr float APPROX_EPS = 1e-3f;    // pixel slack of the tile-local (approximate) edge equations
 
-// conservative tile-local culling data of a staged face
+// conservative tile-local data of a staged face: edge equations and bbox in pixels
+// relative to the tile origin (FP32, a few 1e-6 px of error), and the smallest depth
 struct Pre {
-    float nx[3], ny[3], c[3];    // F_i(p) ~ nx p.x + ny p.y + c, inward unit normal, tile-local
-    float bx0, bx1, by0, by1;    // bbox grown by r, tile-local
+    float nx[3], ny[3], c[3];    // F_i(p) ~ nx p.x + ny p.y + c, inward unit normal
+    float bx0, bx1, by0, by1;    // bbox grown by r
+    float zmin;
+    float pad[2];
 };
 
 __device__ __forceinline__ void make_pre(const FaceRec &R, bool live, float tx0, float ty0, float r_px, Pre &P)
@@ -41,6 +45,7 @@ __device__ __forceinline__ void make_pre(const FaceRec &R, bool live, float tx0,
         P.bx0 = 3.0e38f; P.bx1 = -3.0e38f; P.by0 = 3.0e38f; P.by1 = -3.0e38f;
 #pragma unroll
         for (int i = 0; i < 3; ++i) { P.nx[i] = 0.f; P.ny[i] = 0.f; P.c[i] = -3.0e38f; }
+        P.zmin = 3.0e38f;
         return;
     }
     const bool orient = R.flags & 1;
@@ -53,10 +58,10 @@ __device__ __forceinline__ void make_pre(const FaceRec &R, bool live, float tx0,
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const int ib = (i + 1) % 3;
-        float ex = vx[ib] - vx[i], ey = vy[ib] - vy[i];
+        const float ex = vx[ib] - vx[i], ey = vy[ib] - vy[i];
         float nx = orient ? -ey : ey, ny = orient ? ex : -ex;
-        float l = sqrtf(nx * nx + ny * ny);
-        float s = l > 0.f ? 1.f / l : 0.f;
+        const float l = sqrtf(nx * nx + ny * ny);
+        const float s = l > 0.f ? 1.f / l : 0.f;
         nx *= s; ny *= s;
         P.nx[i] = nx; P.ny[i] = ny;
         P.c[i] = -(nx * vx[i] + ny * vy[i]);
@@ -65,18 +70,44 @@ __device__ __forceinline__ void make_pre(const FaceRec &R, bool live, float tx0,
     P.bx1 = fmaxf(vx[0], fmaxf(vx[1], vx[2])) + r_px;
     P.by0 = fminf(vy[0], fminf(vy[1], vy[2])) - r_px;
     P.by1 = fmaxf(vy[0], fmaxf(vy[1], vy[2])) + r_px;
+    P.zmin = fminf(R.z[0], fminf(R.z[1], R.z[2]));
 }
 
 // may some pixel centre of the box (cx +- hx, cy +- hy) be within r of the face?
-__device__ __forceinline__ bool pretest(const Pre &P, float cx, float cy, float hx, float hy, float r_px)
+__device__ __forceinline__ bool pretest_box(const Pre &P, float cx, float cy, float hx, float hy, float r_px)
 {
-    const float eps = 1e-2f;
+    const float eps = APPROX_EPS;
     if (P.bx1 < cx - hx - eps || P.bx0 > cx + hx + eps || P.by1 < cy - hy - eps || P.by0 > cy + hy + eps) return false;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        float F = P.nx[i] * cx + P.ny[i] * cy + P.c[i] + fabsf(P.nx[i]) * hx + fabsf(P.ny[i]) * hy;
+        const float F = P.nx[i] * cx + P.ny[i] * cy + P.c[i] + fabsf(P.nx[i]) * hx + fabsf(P.ny[i]) * hy;
         if (F < -r_px - eps) return false;
     }
+    return true;
+}
+
+// smallest approximate edge value of the face at one tile-local pixel centre
+__device__ __forceinline__ float approx_fmin(const Pre &P, float lx, float ly)
+{
+    const float f0 = fmaf(P.nx[0], lx, fmaf(P.ny[0], ly, P.c[0]));
+    const float f1 = fmaf(P.nx[1], lx, fmaf(P.ny[1], ly, P.c[1]));
+    const float f2 = fmaf(P.nx[2], lx, fmaf(P.ny[2], ly, P.c[2]));
+    return fminf(f0, fminf(f1, f2));
+}
+
+// Per-pixel pre-test: false when the face is certainly farther than r; otherwise a
+// lower bound of its Shift() key (outside: the distance is at least the largest
+// edge-line distance; inside: the depth is at least the smallest corner depth).
+__device__ __forceinline__ bool approx_candidate(const Pre &P, float lx, float ly, float r_px, float half_inv_S,
+                                                 float &klb)
+{
+    const float eps = APPROX_EPS;
+    if (lx < P.bx0 - eps || lx > P.bx1 + eps || ly < P.by0 - eps || ly > P.by1 + eps) return false;
+    const float fmin = approx_fmin(P, lx, ly);
+    if (fmin < -r_px - eps) return false;
+    if (fmin > eps) klb = 0.5f * P.zmin * (1.f - 1e-6f);
+    else if (fmin < -eps) klb = fmaf(-fmin - eps, half_inv_S, 0.5f);
+    else klb = 0.f;
     return true;
 }
 
@@ -94,28 +125,54 @@ __device__ __forceinline__ void halo_pos(int h, int rho, int &hx, int &hy)
     hx = TT + h % rho;
 }
 
-template <int K>
-__device__ __forceinline__ void peel_insert(float (&kk)[K], int (&ii)[K], bool (&hh)[K], float key, int id, bool hard)
-{
-    if (!frag_less(key, id, kk[K - 1], ii[K - 1])) return;
+// per-pixel K-selection of the peel; with CARRY the distance and barycentrics of
+// every kept fragment travel along, so shading does not re-evaluate the face
+template <int K, bool CARRY>
+struct PeelState {
+    float key[K];
+    int id[K];
+    bool hard[K];
+    float dist[CARRY ? K : 1], l0[CARRY ? K : 1], l1[CARRY ? K : 1], l2[CARRY ? K : 1];
+
+    __device__ __forceinline__ void init()
+    {
 #pragma unroll
-    for (int t = K - 1; t > 0; --t) {
-        if (frag_less(key, id, kk[t - 1], ii[t - 1])) {
-            kk[t] = kk[t - 1]; ii[t] = ii[t - 1]; hh[t] = hh[t - 1];
-        } else {
-            kk[t] = key; ii[t] = id; hh[t] = hard;
-            return;
-        }
+        for (int k = 0; k < K; ++k) { key[k] = 3.0e38f; id[k] = 0x7fffffff; hard[k] = false; }
     }
-    kk[0] = key; ii[0] = id; hh[0] = hard;
-}
+    __device__ __forceinline__ void put(int k, float ky, int i, bool h, float d, float a0, float a1, float a2)
+    {
+        key[k] = ky; id[k] = i; hard[k] = h;
+        if (CARRY) { dist[k] = d; l0[k] = a0; l1[k] = a1; l2[k] = a2; }
+    }
+    __device__ __forceinline__ void move(int to, int from)
+    {
+        key[to] = key[from]; id[to] = id[from]; hard[to] = hard[from];
+        if (CARRY) { dist[to] = dist[from]; l0[to] = l0[from]; l1[to] = l1[from]; l2[to] = l2[from]; }
+    }
+    // keeps the K smallest (key, id) pairs
+    __device__ __forceinline__ void insert(float ky, int i, bool h, float d, float a0, float a1, float a2)
+    {
+        if (!frag_less(ky, i, key[K - 1], id[K - 1])) return;
+        bool done = false;
+#pragma unroll
+        for (int t = K - 1; t > 0; --t) {
+            const bool lt = frag_less(ky, i, key[t - 1], id[t - 1]);
+            if (!done) {
+                if (lt) move(t, t - 1);
+                else put(t, ky, i, h, d, a0, a1, a2);
+            }
+            done = done || !lt;
+        }
+        if (!done) put(0, ky, i, h, d, a0, a1, a2);
+    }
+};
 
 // ---------------------------------------------------------------------------
-// per-layer geometry and shading (Sec. 3.2.2 texture sampling, Sec. 3.3.3 shading)
+// per-layer shading (Sec. 3.2.2 texture sampling, Sec. 3.3.3 shading)
 // ---------------------------------------------------------------------------
-struct Layer {
-    FaceRec R;
-    Frag fr;
+struct Shade {
+    int vi[3];
+    float iw[3];
     float lam[3], b[3], Q;
     float C[3];
     float D;
@@ -168,85 +225,85 @@ __device__ __forceinline__ void texcoord(const float b[3], const float u[3], flo
     i0 = (int)fA + (int)ft;
 }
 
-__device__ __forceinline__ bool layer_build(const Globals &g, const ViewK &V, const MeshK &M, const VRec *vr, int id,
-                                            float px, float py, Layer &L)
+// b, C, D and the sampling state of one layer from S.vi, S.iw, S.lam and dist
+__device__ __forceinline__ void shade(const Globals &g, const ViewK &V, const MeshK &M, float dist, Shade &S)
 {
-    if (!face_load(g, M, vr, id, L.R)) return false;
-    if (!eval_face(L.R, px, py, V.r_px, V.half_inv_S, L.fr)) return false;
-    if (L.fr.hard) {
-        L.lam[0] = L.fr.Fn[1] * L.R.invA;
-        L.lam[1] = L.fr.Fn[2] * L.R.invA;
-        L.lam[2] = L.fr.Fn[0] * L.R.invA;
-    } else if (L.fr.feat >= 3) {
-        // soft fragment: barycentrics of its closest point of the hard face (a corner)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) L.lam[j] = (j == L.fr.feat - 3) ? 1.f : 0.f;
-    } else {
-        // ... or a point of edge feat, at parameter t from its canonical first endpoint
-        const int i = L.fr.feat;
-        const bool sw = (L.R.flags >> (1 + i)) & 1;
-        const int P = sw ? (i + 1) % 3 : i, Q = sw ? i : (i + 1) % 3;
-#pragma unroll
-        for (int j = 0; j < 3; ++j) L.lam[j] = (j == P) ? 1.f - L.fr.t : ((j == Q) ? L.fr.t : 0.f);
-    }
     float q[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) q[i] = L.lam[i] * L.R.iw[i];
-    L.Q = q[0] + q[1] + q[2];
-    const float iQ = 1.f / L.Q;
+    for (int i = 0; i < 3; ++i) q[i] = S.lam[i] * S.iw[i];
+    S.Q = q[0] + q[1] + q[2];
+    const float iQ = 1.f / S.Q;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) L.b[i] = q[i] * iQ;
-    L.D = sigmoidf_stable(L.fr.dist * V.inv_sigma_px);
+    for (int i = 0; i < 3; ++i) S.b[i] = q[i] * iQ;
+    S.D = sigmoidf_stable(dist * V.inv_sigma_px);
     const long long nvt = g.n_verts_total;
     if (g.shade_mode == 0) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             float a = 0.f;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) a = fmaf(L.b[i], __ldg(g.col + c * nvt + M.vert_off + L.R.vi[i]), a);
-            L.C[c] = a;
+            for (int i = 0; i < 3; ++i) a = fmaf(S.b[i], __ldg(g.col + c * nvt + M.vert_off + S.vi[i]), a);
+            S.C[c] = a;
         }
-        return true;
+        return;
     }
     float u[3], v[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        u[i] = __ldg(g.uv + M.vert_off + L.R.vi[i]);
-        v[i] = __ldg(g.uv + nvt + M.vert_off + L.R.vi[i]);
+        u[i] = __ldg(g.uv + M.vert_off + S.vi[i]);
+        v[i] = __ldg(g.uv + nvt + M.vert_off + S.vi[i]);
     }
     int x0, y0;
-    texcoord(L.b, u, (float)M.tex_w, x0, L.fx, L.Xt);
-    texcoord(L.b, v, (float)M.tex_h, y0, L.fy, L.Yt);
-    L.ix[0] = wrapi(x0, M.tex_w); L.ix[1] = wrapi(x0 + 1, M.tex_w);
-    L.iy[0] = wrapi(y0, M.tex_h); L.iy[1] = wrapi(y0 + 1, M.tex_h);
+    texcoord(S.b, u, (float)M.tex_w, x0, S.fx, S.Xt);
+    texcoord(S.b, v, (float)M.tex_h, y0, S.fy, S.Yt);
+    S.ix[0] = wrapi(x0, M.tex_w); S.ix[1] = wrapi(x0 + 1, M.tex_w);
+    S.iy[0] = wrapi(y0, M.tex_h); S.iy[1] = wrapi(y0 + 1, M.tex_h);
     const long long tb = M.tex_off;
-    float4 t00 = load_texel(g, tb + (long long)L.iy[0] * M.tex_w + L.ix[0]);
-    float4 t10 = load_texel(g, tb + (long long)L.iy[0] * M.tex_w + L.ix[1]);
-    float4 t01 = load_texel(g, tb + (long long)L.iy[1] * M.tex_w + L.ix[0]);
-    float4 t11 = load_texel(g, tb + (long long)L.iy[1] * M.tex_w + L.ix[1]);
-    const float w00 = (1.f - L.fx) * (1.f - L.fy), w10 = L.fx * (1.f - L.fy), w01 = (1.f - L.fx) * L.fy,
-                w11 = L.fx * L.fy;
-    L.A[0] = w00 * t00.x + w10 * t10.x + w01 * t01.x + w11 * t11.x;
-    L.A[1] = w00 * t00.y + w10 * t10.y + w01 * t01.y + w11 * t11.y;
-    L.A[2] = w00 * t00.z + w10 * t10.z + w01 * t01.z + w11 * t11.z;
+    const float4 t00 = load_texel(g, tb + (long long)S.iy[0] * M.tex_w + S.ix[0]);
+    const float4 t10 = load_texel(g, tb + (long long)S.iy[0] * M.tex_w + S.ix[1]);
+    const float4 t01 = load_texel(g, tb + (long long)S.iy[1] * M.tex_w + S.ix[0]);
+    const float4 t11 = load_texel(g, tb + (long long)S.iy[1] * M.tex_w + S.ix[1]);
+    const float w00 = (1.f - S.fx) * (1.f - S.fy), w10 = S.fx * (1.f - S.fy), w01 = (1.f - S.fx) * S.fy,
+                w11 = S.fx * S.fy;
+    S.A[0] = w00 * t00.x + w10 * t10.x + w01 * t01.x + w11 * t11.x;
+    S.A[1] = w00 * t00.y + w10 * t10.y + w01 * t01.y + w11 * t11.y;
+    S.A[2] = w00 * t00.z + w10 * t10.z + w01 * t01.z + w11 * t11.z;
     if (g.shade_mode == 1) {
-        L.C[0] = L.A[0]; L.C[1] = L.A[1]; L.C[2] = L.A[2];
-        return true;
+        S.C[0] = S.A[0]; S.C[1] = S.A[1]; S.C[2] = S.A[2];
+        return;
     }
     float m[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        float4 nv = g.nrm[M.vert_off + L.R.vi[i]];
-        m[0] = fmaf(L.b[i], nv.x, m[0]);
-        m[1] = fmaf(L.b[i], nv.y, m[1]);
-        m[2] = fmaf(L.b[i], nv.z, m[2]);
+        const float4 nv = g.nrm[M.vert_off + S.vi[i]];
+        m[0] = fmaf(S.b[i], nv.x, m[0]);
+        m[1] = fmaf(S.b[i], nv.y, m[1]);
+        m[2] = fmaf(S.b[i], nv.z, m[2]);
     }
-    L.mlen = sqrtf(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
-    const float il = L.mlen > 0.f ? 1.f / L.mlen : 0.f;
-    L.n[0] = m[0] * il; L.n[1] = m[1] * il; L.n[2] = m[2] * il;
-    L.ndl = L.n[0] * V.light[0] + L.n[1] * V.light[1] + L.n[2] * V.light[2];
-    const float s = fmaxf(L.ndl, 0.f);
-    L.C[0] = L.A[0] * s; L.C[1] = L.A[1] * s; L.C[2] = L.A[2] * s;
+    S.mlen = sqrtf(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+    const float il = S.mlen > 0.f ? 1.f / S.mlen : 0.f;
+    S.n[0] = m[0] * il; S.n[1] = m[1] * il; S.n[2] = m[2] * il;
+    S.ndl = S.n[0] * V.light[0] + S.n[1] * V.light[1] + S.n[2] * V.light[2];
+    const float sl = fmaxf(S.ndl, 0.f);
+    S.C[0] = S.A[0] * sl; S.C[1] = S.A[1] * sl; S.C[2] = S.A[2] * sl;
+}
+
+// a layer rebuilt from its face id (adjoint): record, fragment, shading
+struct Layer {
+    FaceRec R;
+    Frag fr;
+    Shade S;
+};
+
+__device__ __forceinline__ bool layer_build(const Globals &g, const ViewK &V, const MeshK &M, const VRec *vr, int id,
+                                            float px, float py, Layer &L)
+{
+    if (!face_load(g, M, vr, id, L.R)) return false;
+    if (!eval_face(L.R, px, py, V.r_px, V.half_inv_S, L.fr)) return false;
+    frag_lambda(L.R, L.fr, L.S.lam);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { L.S.vi[i] = L.R.vi[i]; L.S.iw[i] = L.R.iw[i]; }
+    shade(g, V, M, L.fr.dist, L.S);
     return true;
 }
 
@@ -258,6 +315,7 @@ __device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, 
 {
     const long long nvt = g.n_verts_total;
     const FaceRec &R = L.R;
+    const Shade &S = L.S;
     float dx[3], dy[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -268,26 +326,31 @@ __device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, 
     const float o = (R.flags & 1) ? 1.f : -1.f;
 
     // sigmoid -> signed distance -> corners (closest feature)
-    const float gdist = gD * L.D * (1.f - L.D) * V.inv_sigma_px;
+    const float gdist = gD * S.D * (1.f - S.D) * V.inv_sigma_px;
     if (gdist != 0.f) {
         const int ft = L.fr.feat;
-        if (ft < 3) {
-            const int a = ft, b = (ft + 1) % 3;
-            const float ex = dx[a] - dx[b], ey = dy[a] - dy[b];   // V_b - V_a
-            const float il = 1.f / sqrtf(ex * ex + ey * ey);
-            const float c = ex * dy[a] - ey * dx[a];
-            const float il3 = il * il * il;
-            const float gex = o * (dy[a] * il - c * ex * il3);
-            const float gey = o * (-dx[a] * il - c * ey * il3);
-            const float gdx = o * (-ey * il), gdy = o * (ex * il);
-            gX[b] += gdist * gex; gY[b] += gdist * gey;
-            gX[a] += gdist * (-gex - gdx); gY[a] += gdist * (-gey - gdy);
-        } else {
-            const int mm = ft - 3;
-            const float l = sqrtf(dx[mm] * dx[mm] + dy[mm] * dy[mm]);
-            if (l > 0.f) {
-                gX[mm] += gdist * dx[mm] / l;
-                gY[mm] += gdist * dy[mm] / l;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int b = (a + 1) % 3;
+            if (ft == a) {
+                // F = o cross(V_b - V_a, p - V_a) / |V_b - V_a|
+                const float ex = dx[a] - dx[b], ey = dy[a] - dy[b];
+                const float il = 1.f / sqrtf(ex * ex + ey * ey);
+                const float c = ex * dy[a] - ey * dx[a];
+                const float il3 = il * il * il;
+                const float gex = o * (dy[a] * il - c * ex * il3);
+                const float gey = o * (-dx[a] * il - c * ey * il3);
+                const float gdx = o * (-ey * il), gdy = o * (ex * il);
+                gX[b] += gdist * gex; gY[b] += gdist * gey;
+                gX[a] += gdist * (-gex - gdx); gY[a] += gdist * (-gey - gdy);
+            }
+            if (ft == 3 + a) {
+                // dist = -|p - V_a|
+                const float l = sqrtf(dx[a] * dx[a] + dy[a] * dy[a]);
+                if (l > 0.f) {
+                    gX[a] += gdist * dx[a] / l;
+                    gY[a] += gdist * dy[a] / l;
+                }
             }
         }
     }
@@ -299,10 +362,10 @@ __device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, 
         if (g.shade_mode == 0) {
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                const long long gi = M.vert_off + R.vi[i];
+                const long long gi = M.vert_off + S.vi[i];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    if (g.gcol) atomicAdd(g.gcol + c * nvt + gi, L.b[i] * gC[c]);
+                    if (g.gcol) atomicAdd(g.gcol + c * nvt + gi, S.b[i] * gC[c]);
                     gb[i] = fmaf(gC[c], __ldg(g.col + c * nvt + gi), gb[i]);
                 }
             }
@@ -311,32 +374,32 @@ __device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, 
             if (g.shade_mode == 1) {
                 gA[0] = gC[0]; gA[1] = gC[1]; gA[2] = gC[2];
             } else {
-                const float s = fmaxf(L.ndl, 0.f);
-                gA[0] = gC[0] * s; gA[1] = gC[1] * s; gA[2] = gC[2] * s;
-                if (L.ndl > 0.f && L.mlen > 0.f) {
-                    const float gs = gC[0] * L.A[0] + gC[1] * L.A[1] + gC[2] * L.A[2];
+                const float sl = fmaxf(S.ndl, 0.f);
+                gA[0] = gC[0] * sl; gA[1] = gC[1] * sl; gA[2] = gC[2] * sl;
+                if (S.ndl > 0.f && S.mlen > 0.f) {
+                    const float gs = gC[0] * S.A[0] + gC[1] * S.A[1] + gC[2] * S.A[2];
                     const float gn[3] = {gs * V.light[0], gs * V.light[1], gs * V.light[2]};
-                    const float nd = L.n[0] * gn[0] + L.n[1] * gn[1] + L.n[2] * gn[2];
-                    const float il = 1.f / L.mlen;
-                    const float gm[3] = {(gn[0] - L.n[0] * nd) * il, (gn[1] - L.n[1] * nd) * il,
-                                         (gn[2] - L.n[2] * nd) * il};
+                    const float nd = S.n[0] * gn[0] + S.n[1] * gn[1] + S.n[2] * gn[2];
+                    const float il = 1.f / S.mlen;
+                    const float gm[3] = {(gn[0] - S.n[0] * nd) * il, (gn[1] - S.n[1] * nd) * il,
+                                         (gn[2] - S.n[2] * nd) * il};
 #pragma unroll
                     for (int i = 0; i < 3; ++i) {
-                        const long long gi = M.vert_off + R.vi[i];
+                        const long long gi = M.vert_off + S.vi[i];
                         const float4 nv = g.nrm[gi];
-                        atomicAdd(g.ngrad + gi, make_float4(L.b[i] * gm[0], L.b[i] * gm[1], L.b[i] * gm[2], 0.f));
+                        atomicAdd(g.ngrad + gi, make_float4(S.b[i] * gm[0], S.b[i] * gm[1], S.b[i] * gm[2], 0.f));
                         gb[i] += gm[0] * nv.x + gm[1] * nv.y + gm[2] * nv.z;
                     }
                 }
             }
             // bilinear texture adjoint
             const long long tb = M.tex_off;
-            const long long i00 = tb + (long long)L.iy[0] * M.tex_w + L.ix[0];
-            const long long i10 = tb + (long long)L.iy[0] * M.tex_w + L.ix[1];
-            const long long i01 = tb + (long long)L.iy[1] * M.tex_w + L.ix[0];
-            const long long i11 = tb + (long long)L.iy[1] * M.tex_w + L.ix[1];
-            const float w00 = (1.f - L.fx) * (1.f - L.fy), w10 = L.fx * (1.f - L.fy), w01 = (1.f - L.fx) * L.fy,
-                        w11 = L.fx * L.fy;
+            const long long i00 = tb + (long long)S.iy[0] * M.tex_w + S.ix[0];
+            const long long i10 = tb + (long long)S.iy[0] * M.tex_w + S.ix[1];
+            const long long i01 = tb + (long long)S.iy[1] * M.tex_w + S.ix[0];
+            const long long i11 = tb + (long long)S.iy[1] * M.tex_w + S.ix[1];
+            const float w00 = (1.f - S.fx) * (1.f - S.fy), w10 = S.fx * (1.f - S.fy), w01 = (1.f - S.fx) * S.fy,
+                        w11 = S.fx * S.fy;
             if (g.gtex) {
                 float4 *gt = reinterpret_cast<float4 *>(g.gtex);
                 atomicAdd(gt + i00, make_float4(w00 * gA[0], w00 * gA[1], w00 * gA[2], 0.f));
@@ -346,26 +409,26 @@ __device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, 
             }
             const float4 t00 = load_texel(g, i00), t10 = load_texel(g, i10), t01 = load_texel(g, i01),
                          t11 = load_texel(g, i11);
-            const float gx = gA[0] * ((1.f - L.fy) * (t10.x - t00.x) + L.fy * (t11.x - t01.x)) +
-                             gA[1] * ((1.f - L.fy) * (t10.y - t00.y) + L.fy * (t11.y - t01.y)) +
-                             gA[2] * ((1.f - L.fy) * (t10.z - t00.z) + L.fy * (t11.z - t01.z));
-            const float gy = gA[0] * ((1.f - L.fx) * (t01.x - t00.x) + L.fx * (t11.x - t10.x)) +
-                             gA[1] * ((1.f - L.fx) * (t01.y - t00.y) + L.fx * (t11.y - t10.y)) +
-                             gA[2] * ((1.f - L.fx) * (t01.z - t00.z) + L.fx * (t11.z - t10.z));
+            const float gx = gA[0] * ((1.f - S.fy) * (t10.x - t00.x) + S.fy * (t11.x - t01.x)) +
+                             gA[1] * ((1.f - S.fy) * (t10.y - t00.y) + S.fy * (t11.y - t01.y)) +
+                             gA[2] * ((1.f - S.fy) * (t10.z - t00.z) + S.fy * (t11.z - t01.z));
+            const float gy = gA[0] * ((1.f - S.fx) * (t01.x - t00.x) + S.fx * (t11.x - t10.x)) +
+                             gA[1] * ((1.f - S.fx) * (t01.y - t00.y) + S.fx * (t11.y - t10.y)) +
+                             gA[2] * ((1.f - S.fx) * (t01.z - t00.z) + S.fx * (t11.z - t10.z));
             // x = sum b_i X_i - 1/2; adding a constant to every gb_i is invisible to the
             // perspective step below (sum b = 1), so corner offsets from corner 0 are used
 #pragma unroll
-            for (int i = 0; i < 3; ++i) gb[i] += gx * L.Xt[i] + gy * L.Yt[i];
+            for (int i = 0; i < 3; ++i) gb[i] += gx * S.Xt[i] + gy * S.Yt[i];
         }
         // perspective-correct barycentrics: b_i = q_i / Q, q_i = lam_i / w_i
-        const float bdot = L.b[0] * gb[0] + L.b[1] * gb[1] + L.b[2] * gb[2];
-        const float iQ = 1.f / L.Q;
+        const float bdot = S.b[0] * gb[0] + S.b[1] * gb[1] + S.b[2] * gb[2];
+        const float iQ = 1.f / S.Q;
         float glam[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const float gq = (gb[i] - bdot) * iQ;
-            glam[i] = gq * R.iw[i];
-            gW[i] += gq * L.lam[i];
+            glam[i] = gq * S.iw[i];
+            gW[i] += gq * S.lam[i];
         }
         if (L.fr.hard) {
             // lam_i = cross(V_B - V_A, p - V_A) / A2,  A = i+1, B = i+2
@@ -375,7 +438,7 @@ __device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, 
             for (int i = 0; i < 3; ++i) {
                 const int A = (i + 1) % 3, B = (i + 2) % 3;
                 const float gn = glam[i] * iA2;
-                gA2 -= glam[i] * L.lam[i] * iA2;
+                gA2 -= glam[i] * S.lam[i] * iA2;
                 const float ex = dx[A] - dx[B], ey = dy[A] - dy[B];
                 const float gex = dy[A], gey = -dx[A], gdx = -ey, gdy = ex;
                 gX[B] += gn * gex; gY[B] += gn * gey;
@@ -386,33 +449,34 @@ __device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, 
             gX[1] += gA2 * wy; gY[1] -= gA2 * wx;
             gX[2] -= gA2 * uy; gY[2] += gA2 * ux;
             gX[0] += gA2 * (uy - wy); gY[0] += gA2 * (wx - ux);
-        } else if (L.fr.feat < 3) {
-            // lam_P = 1 - s, lam_Q = s, s = (p - P).(Q - P) / |Q - P|^2
-            const int i = L.fr.feat;
-            const bool sw = (R.flags >> (1 + i)) & 1;
-            const int P = sw ? (i + 1) % 3 : i, Q = sw ? i : (i + 1) % 3;
-            float dPx = 0.f, dPy = 0.f, dQx = 0.f, dQy = 0.f, gP = 0.f, gQ = 0.f;
+        } else {
+            // lam_P = 1 - s, lam_Q = s, s = (p - P).(Q - P) / |Q - P|^2 on the closest edge
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                if (j == P) { dPx = dx[j]; dPy = dy[j]; gP = glam[j]; }
-                if (j == Q) { dQx = dx[j]; dQy = dy[j]; gQ = glam[j]; }
-            }
-            const float ex = dPx - dQx, ey = dPy - dQy;            // Q - P
-            const float iee = 1.f / (ex * ex + ey * ey), s = L.fr.t;
-            const float gs = gQ - gP;
-            const float gex = (dPx - 2.f * s * ex) * iee, gey = (dPy - 2.f * s * ey) * iee;
-            const float gdx = ex * iee, gdy = ey * iee;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                if (j == Q) { gX[j] += gs * gex; gY[j] += gs * gey; }
-                if (j == P) { gX[j] += gs * (-gex - gdx); gY[j] += gs * (-gey - gdy); }
+            for (int i = 0; i < 3; ++i) {
+                if (L.fr.feat != i) continue;
+                const bool sw = (R.flags >> (1 + i)) & 1;
+                const int ia = i, ib = (i + 1) % 3;
+                const float dPx = sw ? dx[ib] : dx[ia], dPy = sw ? dy[ib] : dy[ia];
+                const float dQx = sw ? dx[ia] : dx[ib], dQy = sw ? dy[ia] : dy[ib];
+                const float gP = sw ? glam[ib] : glam[ia], gQ = sw ? glam[ia] : glam[ib];
+                const float ex = dPx - dQx, ey = dPy - dQy;            // Q - P
+                const float iee = 1.f / (ex * ex + ey * ey), s = L.fr.t;
+                const float gs = gQ - gP;
+                const float gex = (dPx - 2.f * s * ex) * iee, gey = (dPy - 2.f * s * ey) * iee;
+                const float gdx = ex * iee, gdy = ey * iee;
+                const float gPx = gs * (-gex - gdx), gPy = gs * (-gey - gdy), gQx = gs * gex, gQy = gs * gey;
+                if (sw) {
+                    gX[ib] += gPx; gY[ib] += gPy; gX[ia] += gQx; gY[ia] += gQy;
+                } else {
+                    gX[ia] += gPx; gY[ia] += gPy; gX[ib] += gQx; gY[ib] += gQy;
+                }
             }
         }
     }
     float4 *sg = g.sgrad + V.vrec_off;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-        if (gX[i] != 0.f || gY[i] != 0.f || gW[i] != 0.f) atomicAdd(sg + R.vi[i], make_float4(gX[i], gY[i], gW[i], 0.f));
+        if (gX[i] != 0.f || gY[i] != 0.f || gW[i] != 0.f) atomicAdd(sg + S.vi[i], make_float4(gX[i], gY[i], gW[i], 0.f));
 }
 
 // ---------------------------------------------------------------------------
@@ -421,6 +485,7 @@ __device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, 
 template <int K, bool BWD>
 __global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
 {
+    constexpr bool CARRY = !BWD;
     __shared__ FaceRec sF[CHUNK];
     __shared__ Pre sP[CHUNK];
     __shared__ unsigned char sSH[HS_MAX * HS_MAX];
@@ -435,10 +500,13 @@ __global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
     const int lt = t - V.tile_base;
     const int X0 = (lt % V.tiles_x) * TT, Y0 = (lt / V.tiles_x) * TT;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int lx = lane & 15, ly = warp * 2 + (lane >> 4);
+    // warp w owns the 8 x 4 block at (8 (w & 1), 4 (w >> 1)) of the tile
+    const int bx = 8 * (warp & 1), by = 4 * (warp >> 1);
+    const int lx = bx + (lane & 7), ly = by + (lane >> 3);
     const int X = X0 + lx, Y = Y0 + ly;
     const bool inimg = X < V.W && Y < V.H;
     const float px = (float)X + 0.5f, py = (float)Y + 0.5f;
+    const float lpx = (float)lx + 0.5f, lpy = (float)ly + 0.5f;
     const int rho = (g.edge_mode == 0) ? min(V.rho, RHO_MAX) : 0;
     const int hs = TT + 2 * rho;
     const long long pix = V.pix_off + (long long)Y * V.W + X;
@@ -448,11 +516,8 @@ __global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
         sSH[i] = (hx >= 0 && hy >= 0 && hx < V.W && hy < V.H) ? 0 : 2;
     }
 
-    float kk[K];
-    int ii[K];
-    bool hh[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) { kk[k] = 3.0e38f; ii[k] = 0x7fffffff; hh[k] = false; }
+    PeelState<K, CARRY> ps;
+    ps.init();
 
     const int hcount = rho > 0 ? hs * hs - NT : 0;
     const int ngroups = (hcount + 31) >> 5;
@@ -463,29 +528,35 @@ __global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
         const bool fallback = le > g.list_cap;
         const int n = fallback ? M.nF : (int)(le - lb);
         if (fallback && threadIdx.x == 0) atomicOr(g.status, DRESSI_DEV_TILE_OVERFLOW);
-        const float cx = 8.f, cy = 2.f * warp + 1.f;   // centre of this warp's 16 x 2 block of pixel centres
+        const float cx = (float)bx + 4.f, cy = (float)by + 2.f;   // centre of this warp's block of pixel centres
         for (int c0 = 0; c0 < n; c0 += CHUNK) {
             const int nch = min(CHUNK, n - c0);
             __syncthreads();
             if (threadIdx.x < nch) {
                 const int f = fallback ? c0 + threadIdx.x : g.lists[lb + c0 + threadIdx.x];
-                FaceRec R;
-                const bool live = face_load(g, M, vr, f, R);
-                sF[threadIdx.x] = R;
-                make_pre(R, live, (float)X0, (float)Y0, V.r_px, sP[threadIdx.x]);
+                const bool live = face_load(g, M, vr, f, sF[threadIdx.x]);
+                make_pre(sF[threadIdx.x], live, (float)X0, (float)Y0, V.r_px, sP[threadIdx.x]);
             }
             __syncthreads();
             // peel over the staged faces
             for (int b0 = 0; b0 < nch; b0 += 32) {
                 const int j = b0 + lane;
-                const bool ok = j < nch && pretest(sP[j], cx, cy, 7.5f, 0.5f, V.r_px);
+                const bool ok = j < nch && pretest_box(sP[j], cx, cy, 3.5f, 1.5f, V.r_px);
                 unsigned m = __ballot_sync(0xffffffffu, ok);
                 while (m) {
                     const int b = __ffs(m) - 1;
                     m &= m - 1;
-                    Frag fr;
-                    if (inimg && eval_face(sF[b0 + b], px, py, V.r_px, V.half_inv_S, fr))
-                        peel_insert<K>(kk, ii, hh, fr.key, sF[b0 + b].id, fr.hard);
+                    float klb;
+                    if (inimg && approx_candidate(sP[b0 + b], lpx, lpy, V.r_px, V.half_inv_S, klb) &&
+                        !(klb > ps.key[K - 1])) {
+                        const FaceRec &R = sF[b0 + b];
+                        Frag fr;
+                        if (eval_face(R, px, py, V.r_px, V.half_inv_S, fr)) {
+                            float lam[3] = {0.f, 0.f, 0.f};
+                            if (CARRY) frag_lambda(R, fr, lam);
+                            ps.insert(fr.key, R.id, fr.hard, fr.dist, lam[0], lam[1], lam[2]);
+                        }
+                    }
                 }
             }
             // S^H of the halo ring
@@ -495,7 +566,7 @@ __global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
                 if (h < hcount) halo_pos(h, rho, hx, hy);
                 const int si = (hy + rho) * hs + (hx + rho);
                 bool need = h < hcount && sSH[si] == 0;
-                float fx = (float)hx + 0.5f, fy = (float)hy + 0.5f;
+                const float fx = (float)hx + 0.5f, fy = (float)hy + 0.5f;
                 float mnx = h < hcount ? fx : 3.0e38f, mxx = h < hcount ? fx : -3.0e38f;
                 float mny = h < hcount ? fy : 3.0e38f, mxy = h < hcount ? fy : -3.0e38f;
 #pragma unroll
@@ -510,13 +581,20 @@ __global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
                 for (int b0 = 0; b0 < nch; b0 += 32) {
                     const int j = b0 + lane;
                     // hard test only: r = 0 for the cull
-                    const bool ok = j < nch && pretest(sP[j], gcx, gcy, ghx, ghy, 0.f);
+                    const bool ok = j < nch && pretest_box(sP[j], gcx, gcy, ghx, ghy, 0.f);
                     unsigned m = __ballot_sync(0xffffffffu, ok);
                     while (m) {
                         const int b = __ffs(m) - 1;
                         m &= m - 1;
-                        float hk;
-                        if (need && hard_test(sF[b0 + b], (float)(X0 + hx) + 0.5f, (float)(Y0 + hy) + 0.5f, hk)) {
+                        if (!need) continue;
+                        const Pre &P = sP[b0 + b];
+                        if (fx < P.bx0 || fx > P.bx1 || fy < P.by0 || fy > P.by1) continue;
+                        const float fmin = approx_fmin(P, fx, fy);
+                        if (fmin < -APPROX_EPS) continue;
+                        // clearly inside (margin far above the FP32 error of either test) or
+                        // decided by the exact fill-rule test
+                        if (fmin > APPROX_EPS ||
+                            hard_test(sF[b0 + b], (float)(X0 + hx) + 0.5f, (float)(Y0 + hy) + 0.5f)) {
                             sSH[si] = 1;
                             need = false;
                         }
@@ -529,12 +607,12 @@ __global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int id = inimg ? __ldg(g.ids_in + (long long)k * g.n_pix + pix) : -1;
-            if (id >= 0) { ii[k] = id; kk[k] = 0.f; } else { ii[k] = 0x7fffffff; kk[k] = 3.0e38f; }
+            if (id >= 0) { ps.id[k] = id; ps.key[k] = 0.f; }
         }
-        if (inimg && ii[0] != 0x7fffffff) {
+        if (inimg && ps.id[0] != 0x7fffffff) {
             FaceRec R;
             Frag fr;
-            hh[0] = face_load(g, M, vr, ii[0], R) && eval_face(R, px, py, V.r_px, V.half_inv_S, fr) && fr.hard;
+            ps.hard[0] = face_load(g, M, vr, ps.id[0], R) && eval_face(R, px, py, V.r_px, V.half_inv_S, fr) && fr.hard;
         }
         for (int h = threadIdx.x; h < hcount; h += NT) {
             int hx, hy;
@@ -545,15 +623,14 @@ __global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
             const int id = __ldg(g.ids_in + hp);
             if (id < 0) continue;
             FaceRec R;
-            float hk;
-            if (face_load(g, M, vr, id, R) && hard_test(R, (float)(X0 + hx) + 0.5f, (float)(Y0 + hy) + 0.5f, hk))
+            if (face_load(g, M, vr, id, R) && hard_test(R, (float)(X0 + hx) + 0.5f, (float)(Y0 + hy) + 0.5f))
                 sSH[si] = 1;
         }
     }
     int nl = 0;
 #pragma unroll
-    for (int k = 0; k < K; ++k) nl += (ii[k] != 0x7fffffff) ? 1 : 0;
-    const bool SH = nl > 0 && hh[0];
+    for (int k = 0; k < K; ++k) nl += (ps.id[k] != 0x7fffffff) ? 1 : 0;
+    const bool SH = nl > 0 && ps.hard[0];
     __syncthreads();
     if (inimg) sSH[(ly + rho) * hs + (lx + rho)] = SH ? 1 : 0;
     __syncthreads();
@@ -575,21 +652,29 @@ __global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
     if (!BWD) {
         if (g.ids) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) g.ids[(long long)k * g.n_pix + pix] = (k < nl) ? ii[k] : -1;
+            for (int k = 0; k < K; ++k) g.ids[(long long)k * g.n_pix + pix] = (k < nl) ? ps.id[k] : -1;
         }
         float Cs[3] = {0.f, 0.f, 0.f}, C1[3] = {0.f, 0.f, 0.f};
         float Ds = 0.f, prod = 1.f;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            if (k >= nl) break;
-            Layer L;
-            if (!layer_build(g, V, M, vr, ii[k], px, py, L)) continue;
-            Cs[0] = fmaf(L.D, L.C[0], Cs[0]);
-            Cs[1] = fmaf(L.D, L.C[1], Cs[1]);
-            Cs[2] = fmaf(L.D, L.C[2], Cs[2]);
-            Ds += L.D;
-            prod *= 1.f - L.D;
-            if (k == 0) { C1[0] = L.C[0]; C1[1] = L.C[1]; C1[2] = L.C[2]; }
+            // outside the edge mask only the front layer is seen
+            if (!(k < nl && (E || k == 0))) continue;
+            Shade S;
+            const int *fv = g.faces + 3 * (M.face_off + ps.id[k]);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                S.vi[i] = __ldg(fv + i);
+                S.iw[i] = __ldg(&vr[S.vi[i]].iw);
+            }
+            if (CARRY) { S.lam[0] = ps.l0[k]; S.lam[1] = ps.l1[k]; S.lam[2] = ps.l2[k]; }
+            shade(g, V, M, CARRY ? ps.dist[k] : 0.f, S);
+            Cs[0] = fmaf(S.D, S.C[0], Cs[0]);
+            Cs[1] = fmaf(S.D, S.C[1], Cs[1]);
+            Cs[2] = fmaf(S.D, S.C[2], Cs[2]);
+            Ds += S.D;
+            prod *= 1.f - S.D;
+            if (k == 0) { C1[0] = S.C[0]; C1[1] = S.C[1]; C1[2] = S.C[2]; }
         }
         float4 o;
         if (E) {
@@ -604,22 +689,22 @@ __global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
         const float4 gi4 = __ldg(reinterpret_cast<const float4 *>(g.gin) + pix);
         const float gc[3] = {gi4.x, gi4.y, gi4.z};
         if (gc[0] == 0.f && gc[1] == 0.f && gc[2] == 0.f && gi4.w == 0.f) return;
-        // pass 1: D_k and C_k of every layer
-        float Dk[K], Ck[K][3];
-#pragma unroll
-        for (int k = 0; k < K; ++k) { Dk[k] = 0.f; Ck[k][0] = Ck[k][1] = Ck[k][2] = 0.f; }
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            if (k >= nl) break;
-            Layer L;
-            if (!layer_build(g, V, M, vr, ii[k], px, py, L)) continue;
-            Dk[k] = L.D;
-            Ck[k][0] = L.C[0]; Ck[k][1] = L.C[1]; Ck[k][2] = L.C[2];
-        }
         float gCk[K][3], gDk[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) { gDk[k] = 0.f; gCk[k][0] = gCk[k][1] = gCk[k][2] = 0.f; }
         if (E) {
+            // pass 1: D_k and C_k of every layer
+            float Dk[K], Ck[K][3];
+#pragma unroll
+            for (int k = 0; k < K; ++k) { Dk[k] = 0.f; Ck[k][0] = Ck[k][1] = Ck[k][2] = 0.f; }
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                Layer L;
+                if (k < nl && layer_build(g, V, M, vr, ps.id[k], px, py, L)) {
+                    Dk[k] = L.S.D;
+                    Ck[k][0] = L.S.C[0]; Ck[k][1] = L.S.C[1]; Ck[k][2] = L.S.C[2];
+                }
+            }
             float Ds = 0.f, Ie[3] = {0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -654,11 +739,10 @@ __global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
         // pass 2: per-layer adjoint
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            if (k >= nl) break;
-            if (gDk[k] == 0.f && gCk[k][0] == 0.f && gCk[k][1] == 0.f && gCk[k][2] == 0.f) continue;
+            const bool any = gDk[k] != 0.f || gCk[k][0] != 0.f || gCk[k][1] != 0.f || gCk[k][2] != 0.f;
             Layer L;
-            if (!layer_build(g, V, M, vr, ii[k], px, py, L)) continue;
-            layer_adjoint(g, V, M, L, px, py, gCk[k], gDk[k]);
+            if (k < nl && any && layer_build(g, V, M, vr, ps.id[k], px, py, L))
+                layer_adjoint(g, V, M, L, px, py, gCk[k], gDk[k]);
         }
     }
 }
