@@ -29,6 +29,9 @@ constexpr int NT = TT * TT;            // threads per CTA
 constexpr int RHO_MAX = 8;             // largest supported edge-mask radius
 constexpr int HS_MAX = TT + 2 * RHO_MAX;
 constexpr float APPROX_EPS = 1e-3f;    // pixel slack of the tile-local (approximate) edge equations
+constexpr int CH = 256;                // faces staged per round (one per thread)
+constexpr int HASH = 2 * CH;           // face id -> staged slot, open addressing
+constexpr unsigned long long EMPTY = ~0ULL;
 
 // conservative tile-local data of a staged face: edge equations and bbox in pixels
 // relative to the tile origin (FP32, a few 1e-6 px of error), and the smallest depth
@@ -481,158 +484,281 @@ __device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, 
 
 // ---------------------------------------------------------------------------
 // the tile kernel
+//
+// Raster phase, per staged chunk of faces: every face contributes the (face,
+// pixel) pairs of its r-grown bbox inside the tile, and the (face, pixel) pairs
+// of its bbox inside the rho-ring around the tile; the pairs are spread evenly
+// over all threads.  A pair that survives the approximate test is evaluated
+// exactly and merged into the pixel's K-list in shared memory: each slot holds a
+// 64-bit (Shift key, face id) and takes atomicMin; the displaced larger value
+// moves on to the next slot.  Every value passes slot 0, the values leaving slot
+// k are all values but slot k's minimum, so the slots end up holding the K
+// smallest pairs in order, whatever the interleaving.
 // ---------------------------------------------------------------------------
-template <int K, bool BWD>
-__global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
+struct Smem {
+    FaceRec F[CH];
+    Pre P[CH];
+    int rect[CH];        // tile pairs: x0 | y0 << 8 | w << 16 | h << 24 (tile-local, x0/y0 >= 0)
+    int hrect[CH];       // ring pairs: (x0 + 16) | (y0 + 16) << 8 | w << 16 | h << 24
+    int start[CH];       // exclusive prefix of tile pairs
+    int hstart[CH];      // exclusive prefix of ring pairs
+    int2 hash[HASH];     // (face id, slot) of the last staged chunk
+    int wsum[2][NT / 32];
+    int view, totals[2];
+    unsigned char sh[HS_MAX * HS_MAX];
+};
+
+__device__ __forceinline__ unsigned long long pack_frag(float key, int id)
 {
-    constexpr bool CARRY = !BWD;
-    __shared__ FaceRec sF[CHUNK];
-    __shared__ Pre sP[CHUNK];
-    __shared__ unsigned char sSH[HS_MAX * HS_MAX];
-    __shared__ int s_view;
+    const unsigned int kb = __float_as_uint(key) & 0x7fffffffu;   // keys are >= 0; folds -0 into +0
+    return ((unsigned long long)kb << 32) | (unsigned int)id;
+}
+
+template <int K>
+__device__ __forceinline__ void kbuf_insert(unsigned long long *slots, unsigned long long v)
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const unsigned long long old = atomicMin(slots + k, v);
+        if (old == EMPTY) return;
+        v = old > v ? old : v;
+    }
+}
+
+__device__ __forceinline__ int find_slot(const Smem &S, int id)
+{
+    unsigned h = ((unsigned)id * 2654435761u) & (HASH - 1);
+    for (int probe = 0; probe < HASH; ++probe) {
+        const int2 e = S.hash[h];
+        if (e.x == id) return e.y;
+        if (e.x < 0) return -1;
+        h = (h + 1) & (HASH - 1);
+    }
+    return -1;
+}
+
+// largest f < n with start[f] <= i
+__device__ __forceinline__ int search_start(const int *start, int n, int i)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// per-layer values of one pixel after the raster phase
+struct LayerVal {
+    float dist, l0, l1, l2;
+    bool hard;
+};
+
+template <int K, bool BWD>
+__global__ void __launch_bounds__(NT, BWD ? 2 : 3) k_tile(Globals g)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    unsigned long long *kbuf = reinterpret_cast<unsigned long long *>(smem_raw + sizeof(Smem));
 
     const int t = blockIdx.x;
-    if (threadIdx.x == 0) s_view = view_of_tile(g, t);
+    if (threadIdx.x == 0) S.view = view_of_tile(g, t);
     __syncthreads();
-    const ViewK &V = g.views[s_view];
+    const ViewK &V = g.views[S.view];
     const MeshK &M = g.meshes[V.mesh];
     const VRec *vr = g.vrec + V.vrec_off;
     const int lt = t - V.tile_base;
     const int X0 = (lt % V.tiles_x) * TT, Y0 = (lt / V.tiles_x) * TT;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // warp w owns the 8 x 4 block at (8 (w & 1), 4 (w >> 1)) of the tile
-    const int bx = 8 * (warp & 1), by = 4 * (warp >> 1);
-    const int lx = bx + (lane & 7), ly = by + (lane >> 3);
+    const int tid = threadIdx.x;
+    const int lx = tid & (TT - 1), ly = tid >> 4;
     const int X = X0 + lx, Y = Y0 + ly;
     const bool inimg = X < V.W && Y < V.H;
     const float px = (float)X + 0.5f, py = (float)Y + 0.5f;
-    const float lpx = (float)lx + 0.5f, lpy = (float)ly + 0.5f;
     const int rho = (g.edge_mode == 0) ? min(V.rho, RHO_MAX) : 0;
     const int hs = TT + 2 * rho;
     const long long pix = V.pix_off + (long long)Y * V.W + X;
+    const int wlim = min(TT, V.W - X0), hlim = min(TT, V.H - Y0);   // tile part inside the image
 
-    for (int i = threadIdx.x; i < hs * hs; i += NT) {
+    for (int i = tid; i < hs * hs; i += NT) {
         const int hx = X0 - rho + i % hs, hy = Y0 - rho + i / hs;
-        sSH[i] = (hx >= 0 && hy >= 0 && hx < V.W && hy < V.H) ? 0 : 2;
+        S.sh[i] = (hx >= 0 && hy >= 0 && hx < V.W && hy < V.H) ? 0 : 2;
     }
+#pragma unroll
+    for (int k = 0; k < K; ++k) kbuf[tid * K + k] = EMPTY;
 
-    PeelState<K, CARRY> ps;
-    ps.init();
-
-    const int hcount = rho > 0 ? hs * hs - NT : 0;
-    const int ngroups = (hcount + 31) >> 5;
     const bool from_ids = BWD && g.ids_in != nullptr;
-
+    int ids[K];
+    bool single_chunk = false;
     if (!from_ids) {
         const long long lb = g.tile_off[t], le = g.tile_off[t + 1];
         const bool fallback = le > g.list_cap;
         const int n = fallback ? M.nF : (int)(le - lb);
-        if (fallback && threadIdx.x == 0) atomicOr(g.status, DRESSI_DEV_TILE_OVERFLOW);
-        const float cx = (float)bx + 4.f, cy = (float)by + 2.f;   // centre of this warp's block of pixel centres
-        for (int c0 = 0; c0 < n; c0 += CHUNK) {
-            const int nch = min(CHUNK, n - c0);
+        if (fallback && tid == 0) atomicOr(g.status, DRESSI_DEV_TILE_OVERFLOW);
+        single_chunk = n <= CH;
+        for (int c0 = 0; c0 < n; c0 += CH) {
+            const int nch = min(CH, n - c0);
+            __syncthreads();   // previous chunk consumed
+            for (int i = tid; i < HASH; i += NT) S.hash[i] = make_int2(-1, -1);
             __syncthreads();
-            if (threadIdx.x < nch) {
-                const int f = fallback ? c0 + threadIdx.x : g.lists[lb + c0 + threadIdx.x];
-                const bool live = face_load(g, M, vr, f, sF[threadIdx.x]);
-                make_pre(sF[threadIdx.x], live, (float)X0, (float)Y0, V.r_px, sP[threadIdx.x]);
-            }
-            __syncthreads();
-            // peel over the staged faces
-            for (int b0 = 0; b0 < nch; b0 += 32) {
-                const int j = b0 + lane;
-                const bool ok = j < nch && pretest_box(sP[j], cx, cy, 3.5f, 1.5f, V.r_px);
-                unsigned m = __ballot_sync(0xffffffffu, ok);
-                while (m) {
-                    const int b = __ffs(m) - 1;
-                    m &= m - 1;
-                    float klb;
-                    if (inimg && approx_candidate(sP[b0 + b], lpx, lpy, V.r_px, V.half_inv_S, klb) &&
-                        !(klb > ps.key[K - 1])) {
-                        const FaceRec &R = sF[b0 + b];
-                        Frag fr;
-                        if (eval_face(R, px, py, V.r_px, V.half_inv_S, fr)) {
-                            float lam[3] = {0.f, 0.f, 0.f};
-                            if (CARRY) frag_lambda(R, fr, lam);
-                            ps.insert(fr.key, R.id, fr.hard, fr.dist, lam[0], lam[1], lam[2]);
+            int cnt = 0, hcnt = 0;
+            if (tid < nch) {
+                const int f = fallback ? c0 + tid : g.lists[lb + c0 + tid];
+                FaceRec &R = S.F[tid];
+                const bool live = face_load(g, M, vr, f, R);
+                Pre &P = S.P[tid];
+                make_pre(R, live, (float)X0, (float)Y0, V.r_px, P);
+                if (live) {
+                    // pixel centres lx + 1/2 inside [bx0, bx1] (grown by r), clipped to the tile and image
+                    const int x0 = max(0, (int)ceilf(P.bx0 - 0.5f - APPROX_EPS));
+                    const int x1 = min(wlim - 1, (int)floorf(P.bx1 - 0.5f + APPROX_EPS));
+                    const int y0 = max(0, (int)ceilf(P.by0 - 0.5f - APPROX_EPS));
+                    const int y1 = min(hlim - 1, (int)floorf(P.by1 - 0.5f + APPROX_EPS));
+                    const int w = x1 - x0 + 1, h = y1 - y0 + 1;
+                    if (w > 0 && h > 0) {
+                        cnt = w * h;
+                        S.rect[tid] = x0 | (y0 << 8) | (w << 16) | (h << 24);
+                    }
+                    if (rho > 0) {
+                        // hard bbox (without r) against the ring [-rho, TT + rho), clipped to the image
+                        const float r = V.r_px;
+                        const int hx0 = max(max(-rho, -X0), (int)ceilf(P.bx0 + r - 0.5f - APPROX_EPS));
+                        const int hx1 = min(min(TT + rho, V.W - X0) - 1, (int)floorf(P.bx1 - r - 0.5f + APPROX_EPS));
+                        const int hy0 = max(max(-rho, -Y0), (int)ceilf(P.by0 + r - 0.5f - APPROX_EPS));
+                        const int hy1 = min(min(TT + rho, V.H - Y0) - 1, (int)floorf(P.by1 - r - 0.5f + APPROX_EPS));
+                        const int hw = hx1 - hx0 + 1, hh = hy1 - hy0 + 1;
+                        // only faces reaching outside the tile interior have ring pixels
+                        const bool ring = hx0 < 0 || hy0 < 0 || hx1 >= TT || hy1 >= TT;
+                        if (hw > 0 && hh > 0 && ring) {
+                            hcnt = hw * hh;
+                            S.hrect[tid] = (hx0 + 16) | ((hy0 + 16) << 8) | (hw << 16) | (hh << 24);
                         }
+                    }
+                    // id -> slot for the shading phase
+                    unsigned hsh = ((unsigned)R.id * 2654435761u) & (HASH - 1);
+                    for (int probe = 0; probe < HASH; ++probe) {
+                        const int prev = atomicCAS(&S.hash[hsh].x, -1, R.id);
+                        if (prev == -1 || prev == R.id) { S.hash[hsh].y = tid; break; }
+                        hsh = (hsh + 1) & (HASH - 1);
                     }
                 }
             }
-            // S^H of the halo ring
-            for (int gi = warp; gi < ngroups; gi += NT / 32) {
-                const int h = gi * 32 + lane;
-                int hx = 0, hy = 0;
-                if (h < hcount) halo_pos(h, rho, hx, hy);
-                const int si = (hy + rho) * hs + (hx + rho);
-                bool need = h < hcount && sSH[si] == 0;
-                const float fx = (float)hx + 0.5f, fy = (float)hy + 0.5f;
-                float mnx = h < hcount ? fx : 3.0e38f, mxx = h < hcount ? fx : -3.0e38f;
-                float mny = h < hcount ? fy : 3.0e38f, mxy = h < hcount ? fy : -3.0e38f;
+            // exclusive prefix of the two pair counts over the chunk
+            {
+                const int lane = tid & 31, wp = tid >> 5;
+                int a = cnt, b = hcnt;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
-                    mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
-                    mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, o));
-                    mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int ya = __shfl_up_sync(0xffffffffu, a, o), yb = __shfl_up_sync(0xffffffffu, b, o);
+                    if (lane >= o) { a += ya; b += yb; }
                 }
-                const float gcx = 0.5f * (mnx + mxx), gcy = 0.5f * (mny + mxy);
-                const float ghx = 0.5f * (mxx - mnx), ghy = 0.5f * (mxy - mny);
-                for (int b0 = 0; b0 < nch; b0 += 32) {
-                    const int j = b0 + lane;
-                    // hard test only: r = 0 for the cull
-                    const bool ok = j < nch && pretest_box(sP[j], gcx, gcy, ghx, ghy, 0.f);
-                    unsigned m = __ballot_sync(0xffffffffu, ok);
-                    while (m) {
-                        const int b = __ffs(m) - 1;
-                        m &= m - 1;
-                        if (!need) continue;
-                        const Pre &P = sP[b0 + b];
-                        if (fx < P.bx0 || fx > P.bx1 || fy < P.by0 || fy > P.by1) continue;
-                        const float fmin = approx_fmin(P, fx, fy);
-                        if (fmin < -APPROX_EPS) continue;
-                        // clearly inside (margin far above the FP32 error of either test) or
-                        // decided by the exact fill-rule test
-                        if (fmin > APPROX_EPS ||
-                            hard_test(sF[b0 + b], (float)(X0 + hx) + 0.5f, (float)(Y0 + hy) + 0.5f)) {
-                            sSH[si] = 1;
-                            need = false;
-                        }
-                    }
+                if (lane == 31) { S.wsum[0][wp] = a; S.wsum[1][wp] = b; }
+                __syncthreads();
+                int oa = 0, ob = 0, ta = 0, tb = 0;
+#pragma unroll
+                for (int w = 0; w < NT / 32; ++w) {
+                    const int va = S.wsum[0][w], vb = S.wsum[1][w];
+                    if (w < wp) { oa += va; ob += vb; }
+                    ta += va; tb += vb;
                 }
+                if (tid < CH) { S.start[tid] = oa + a - cnt; S.hstart[tid] = ob + b - hcnt; }
+                if (tid == 0) { S.totals[0] = ta; S.totals[1] = tb; }
             }
+            __syncthreads();
+            const int total = S.totals[0], htotal = S.totals[1];
+            // (face, pixel) pairs of the tile
+            for (int i = tid; i < total; i += NT) {
+                const int f = search_start(S.start, nch, i);
+                const int rc = S.rect[f];
+                const int w = (rc >> 16) & 0xff;
+                const int q = i - S.start[f];
+                const int qy = q / w;
+                const int x = (rc & 0xff) + (q - qy * w), y = ((rc >> 8) & 0xff) + qy;
+                const Pre &P = S.P[f];
+                unsigned long long *slots = kbuf + (y * TT + x) * K;
+                float klb;
+                if (!approx_candidate(P, (float)x + 0.5f, (float)y + 0.5f, V.r_px, V.half_inv_S, klb)) continue;
+                const unsigned long long last = *reinterpret_cast<volatile unsigned long long *>(slots + K - 1);
+                if (klb > __uint_as_float((unsigned int)(last >> 32))) continue;
+                Frag fr;
+                if (eval_face(S.F[f], (float)(X0 + x) + 0.5f, (float)(Y0 + y) + 0.5f, V.r_px, V.half_inv_S, fr))
+                    kbuf_insert<K>(slots, pack_frag(fr.key, S.F[f].id));
+            }
+            // (face, pixel) pairs of the ring: hard test only
+            for (int i = tid; i < htotal; i += NT) {
+                const int f = search_start(S.hstart, nch, i);
+                const int rc = S.hrect[f];
+                const int w = (rc >> 16) & 0xff;
+                const int q = i - S.hstart[f];
+                const int qy = q / w;
+                const int x = (rc & 0xff) - 16 + (q - qy * w), y = ((rc >> 8) & 0xff) - 16 + qy;
+                if (x >= 0 && x < TT && y >= 0 && y < TT) continue;   // interior: decided by the peel
+                const int si = (y + rho) * hs + (x + rho);
+                if (S.sh[si] != 0) continue;
+                const Pre &P = S.P[f];
+                const float fx = (float)x + 0.5f, fy = (float)y + 0.5f;
+                const float fmin = approx_fmin(P, fx, fy);
+                if (fmin < -APPROX_EPS) continue;
+                // clearly inside (margin far above the FP32 error of either test) or
+                // decided by the exact fill-rule test
+                if (fmin > APPROX_EPS || hard_test(S.F[f], (float)(X0 + x) + 0.5f, (float)(Y0 + y) + 0.5f))
+                    S.sh[si] = 1;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const unsigned long long v = kbuf[tid * K + k];
+            ids[k] = (v == EMPTY) ? 0x7fffffff : (int)(unsigned int)(v & 0xffffffffu);
         }
     } else {
         // layers stored by the forward
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int id = inimg ? __ldg(g.ids_in + (long long)k * g.n_pix + pix) : -1;
-            if (id >= 0) { ps.id[k] = id; ps.key[k] = 0.f; }
+            ids[k] = id >= 0 ? id : 0x7fffffff;
         }
-        if (inimg && ps.id[0] != 0x7fffffff) {
-            FaceRec R;
-            Frag fr;
-            ps.hard[0] = face_load(g, M, vr, ps.id[0], R) && eval_face(R, px, py, V.r_px, V.half_inv_S, fr) && fr.hard;
-        }
-        for (int h = threadIdx.x; h < hcount; h += NT) {
+        for (int h = tid; h < (rho > 0 ? hs * hs - NT : 0); h += NT) {
             int hx, hy;
             halo_pos(h, rho, hx, hy);
             const int si = (hy + rho) * hs + (hx + rho);
-            if (sSH[si] != 0) continue;
+            if (S.sh[si] != 0) continue;
             const long long hp = V.pix_off + (long long)(Y0 + hy) * V.W + (X0 + hx);
             const int id = __ldg(g.ids_in + hp);
             if (id < 0) continue;
             FaceRec R;
             if (face_load(g, M, vr, id, R) && hard_test(R, (float)(X0 + hx) + 0.5f, (float)(Y0 + hy) + 0.5f))
-                sSH[si] = 1;
+                S.sh[si] = 1;
         }
     }
     int nl = 0;
 #pragma unroll
-    for (int k = 0; k < K; ++k) nl += (ps.id[k] != 0x7fffffff) ? 1 : 0;
-    const bool SH = nl > 0 && ps.hard[0];
+    for (int k = 0; k < K; ++k) nl += (ids[k] != 0x7fffffff) ? 1 : 0;
+    if (!inimg) nl = 0;
+
+    // re-evaluate the kept layers at this pixel (from shared memory when the whole
+    // tile list was staged at once): hard flag, distance, barycentrics
+    LayerVal lv[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        lv[k].dist = 0.f; lv[k].l0 = lv[k].l1 = lv[k].l2 = 0.f; lv[k].hard = false;
+        if (k < nl && (!BWD || k == 0)) {
+            const int slot = single_chunk ? find_slot(S, ids[k]) : -1;
+            FaceRec Rg;
+            const FaceRec *R = nullptr;
+            if (slot >= 0) R = &S.F[slot];
+            else if (face_load(g, M, vr, ids[k], Rg)) R = &Rg;
+            Frag fr;
+            if (R && eval_face(*R, px, py, V.r_px, V.half_inv_S, fr)) {
+                float lam[3];
+                frag_lambda(*R, fr, lam);
+                lv[k].dist = fr.dist; lv[k].l0 = lam[0]; lv[k].l1 = lam[1]; lv[k].l2 = lam[2];
+                lv[k].hard = fr.hard;
+            }
+        }
+    }
+    const bool SH = nl > 0 && lv[0].hard;
     __syncthreads();
-    if (inimg) sSH[(ly + rho) * hs + (lx + rho)] = SH ? 1 : 0;
+    if (inimg) S.sh[(ly + rho) * hs + (lx + rho)] = SH ? 1 : 0;
     __syncthreads();
     if (!inimg) return;
 
@@ -642,7 +768,7 @@ __global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
         bool s0 = false, s1 = false;
         for (int wy = 0; wy <= 2 * rho; ++wy)
             for (int wx = 0; wx <= 2 * rho; ++wx) {
-                const unsigned char v = sSH[(ly + wy) * hs + (lx + wx)];
+                const unsigned char v = S.sh[(ly + wy) * hs + (lx + wx)];
                 s0 |= v == 0;
                 s1 |= v == 1;
             }
@@ -652,7 +778,7 @@ __global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
     if (!BWD) {
         if (g.ids) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) g.ids[(long long)k * g.n_pix + pix] = (k < nl) ? ps.id[k] : -1;
+            for (int k = 0; k < K; ++k) g.ids[(long long)k * g.n_pix + pix] = (k < nl) ? ids[k] : -1;
         }
         float Cs[3] = {0.f, 0.f, 0.f}, C1[3] = {0.f, 0.f, 0.f};
         float Ds = 0.f, prod = 1.f;
@@ -660,21 +786,21 @@ __global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
         for (int k = 0; k < K; ++k) {
             // outside the edge mask only the front layer is seen
             if (!(k < nl && (E || k == 0))) continue;
-            Shade S;
-            const int *fv = g.faces + 3 * (M.face_off + ps.id[k]);
+            Shade Sh;
+            const int *fv = g.faces + 3 * (M.face_off + ids[k]);
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                S.vi[i] = __ldg(fv + i);
-                S.iw[i] = __ldg(&vr[S.vi[i]].iw);
+                Sh.vi[i] = __ldg(fv + i);
+                Sh.iw[i] = __ldg(&vr[Sh.vi[i]].iw);
             }
-            if (CARRY) { S.lam[0] = ps.l0[k]; S.lam[1] = ps.l1[k]; S.lam[2] = ps.l2[k]; }
-            shade(g, V, M, CARRY ? ps.dist[k] : 0.f, S);
-            Cs[0] = fmaf(S.D, S.C[0], Cs[0]);
-            Cs[1] = fmaf(S.D, S.C[1], Cs[1]);
-            Cs[2] = fmaf(S.D, S.C[2], Cs[2]);
-            Ds += S.D;
-            prod *= 1.f - S.D;
-            if (k == 0) { C1[0] = S.C[0]; C1[1] = S.C[1]; C1[2] = S.C[2]; }
+            Sh.lam[0] = lv[k].l0; Sh.lam[1] = lv[k].l1; Sh.lam[2] = lv[k].l2;
+            shade(g, V, M, lv[k].dist, Sh);
+            Cs[0] = fmaf(Sh.D, Sh.C[0], Cs[0]);
+            Cs[1] = fmaf(Sh.D, Sh.C[1], Cs[1]);
+            Cs[2] = fmaf(Sh.D, Sh.C[2], Cs[2]);
+            Ds += Sh.D;
+            prod *= 1.f - Sh.D;
+            if (k == 0) { C1[0] = Sh.C[0]; C1[1] = Sh.C[1]; C1[2] = Sh.C[2]; }
         }
         float4 o;
         if (E) {
@@ -700,7 +826,7 @@ __global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 Layer L;
-                if (k < nl && layer_build(g, V, M, vr, ps.id[k], px, py, L)) {
+                if (k < nl && layer_build(g, V, M, vr, ids[k], px, py, L)) {
                     Dk[k] = L.S.D;
                     Ck[k][0] = L.S.C[0]; Ck[k][1] = L.S.C[1]; Ck[k][2] = L.S.C[2];
                 }
@@ -741,22 +867,39 @@ __global__ void __launch_bounds__(NT, 2) k_tile(Globals g)
         for (int k = 0; k < K; ++k) {
             const bool any = gDk[k] != 0.f || gCk[k][0] != 0.f || gCk[k][1] != 0.f || gCk[k][2] != 0.f;
             Layer L;
-            if (k < nl && any && layer_build(g, V, M, vr, ps.id[k], px, py, L))
+            if (k < nl && any && layer_build(g, V, M, vr, ids[k], px, py, L))
                 layer_adjoint(g, V, M, L, px, py, gCk[k], gDk[k]);
         }
     }
 }
 
+template <int K>
+static size_t tile_smem_bytes()
+{
+    return sizeof(Smem) + sizeof(unsigned long long) * NT * K;
+}
+
+template <int K, bool BWD>
+static void launch_kk(const Globals &g, cudaStream_t s)
+{
+    static bool configured = false;   // per process; the attribute is per function
+    const size_t smem = tile_smem_bytes<K>();
+    if (!configured) {
+        cudaFuncSetAttribute(k_tile<K, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = true;
+    }
+    k_tile<K, BWD><<<g.total_tiles, NT, smem, s>>>(g);
+}
+
 template <bool BWD>
 static void launch_k(const Globals &g, cudaStream_t s)
 {
-    const int grid = g.total_tiles;
     switch (g.K) {
-    case 1: k_tile<1, BWD><<<grid, NT, 0, s>>>(g); break;
-    case 2: k_tile<2, BWD><<<grid, NT, 0, s>>>(g); break;
-    case 3: k_tile<3, BWD><<<grid, NT, 0, s>>>(g); break;
-    case 4: k_tile<4, BWD><<<grid, NT, 0, s>>>(g); break;
-    default: k_tile<5, BWD><<<grid, NT, 0, s>>>(g); break;
+    case 1: launch_kk<1, BWD>(g, s); break;
+    case 2: launch_kk<2, BWD>(g, s); break;
+    case 3: launch_kk<3, BWD>(g, s); break;
+    case 4: launch_kk<4, BWD>(g, s); break;
+    default: launch_kk<5, BWD>(g, s); break;
     }
 }
 
