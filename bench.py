@@ -171,7 +171,7 @@ def ours(args, rank, world, local_rank):
     s = workload_scene(rank, world, n_views=args.views)
     tgt_scene = synth.perturbed(s, 4321 + rank)
     ps = PackedScene(s.meshes, dev)
-    r = Renderer(ps, s.views, s.params)
+    r = Renderer(ps, s.views, s.params, tile=args.tile)
     # target images (inputs of the loss), rendered once outside the timed region
     pt = PackedScene(tgt_scene.meshes, dev)
     rt = Renderer(pt, tgt_scene.views, tgt_scene.params)
@@ -322,6 +322,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-views", type=int, default=12)
     ap.add_argument("--views", type=int, default=64, help="views per rank (64 = the benchmark workload)")
+    ap.add_argument("--tile", type=int, default=16, choices=[16, 32], help="screen tile edge in pixels")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))

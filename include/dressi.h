@@ -114,7 +114,7 @@ typedef struct {
     int32_t edge_mode;  /* 0 edge mask from S^H, 1 E = 1 everywhere (SoftRas-like), 2 E = 0 (hard) */
     int32_t shade_mode; /* 0 vertex colour, 1 unlit texture, 2 texture * max(0, n.l) */
     int32_t texgrad_mode; /* 0 warp-aggregated atomics, 1 texel-space gather (deterministic) */
-    int32_t tile;       /* tile edge in pixels: 8, 16 or 32; 0 = 16 */
+    int32_t tile;       /* tile edge in pixels: 16 or 32; 0 = 16 */
     int64_t list_cap;   /* tile-list capacity in entries; 0 = library default (see header of
                            dressi_workspace_size) */
 } dressi_params;

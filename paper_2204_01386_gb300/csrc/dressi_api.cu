@@ -58,7 +58,7 @@ static bool check_params(const dressi_params *p)
     if (p->edge_mode < 0 || p->edge_mode > 2) return false;
     if (p->shade_mode < 0 || p->shade_mode > 2) return false;
     if (p->texgrad_mode < 0 || p->texgrad_mode > 1) return false;
-    if (p->tile != 0 && p->tile != TILE_DEFAULT) return false;
+    if (p->tile != 0 && p->tile != 16 && p->tile != 32) return false;
     if (p->list_cap < 0) return false;
     return true;
 }
@@ -99,7 +99,7 @@ static bool make_plan(const dressi_scene *sc, const dressi_view *views, int n_vi
     P.views.resize(n_views);
     long long vrec = 0, view_faces = 0;
     int tiles = 0;
-    const int T = TILE_DEFAULT;
+    const int T = p->tile ? p->tile : TILE_DEFAULT;
     for (int v = 0; v < n_views; ++v) {
         const dressi_view &dv = views[v];
         if (dv.mesh < 0 || dv.mesh >= sc->n_meshes) return false;
@@ -204,8 +204,8 @@ static Globals make_globals(const dressi_scene *sc, const dressi_params *p, cons
     g.K = p->K;
     g.edge_mode = p->edge_mode;
     g.shade_mode = p->shade_mode;
-    g.tile = TILE_DEFAULT;
-    g.tile_shift = 4;
+    g.tile = p->tile ? p->tile : TILE_DEFAULT;
+    g.tile_shift = g.tile == 32 ? 5 : 4;
     g.tex_f16 = sc->tex_dtype == DRESSI_TEX_F16;
     g.texgrad_mode = p->texgrad_mode;
     g.n_verts_total = sc->n_verts_total;

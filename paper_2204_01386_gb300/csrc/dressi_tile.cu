@@ -24,10 +24,10 @@
 
 namespace dressi {
 
-constexpr int TT = 16;                 // tile edge
-constexpr int NT = TT * TT;            // threads per CTA
+constexpr int NT = 256;                // threads per CTA
+constexpr int TT_MAX = 32;             // tile edges: 16 (one pixel per thread) or 32 (four)
 constexpr int RHO_MAX = 8;             // largest supported edge-mask radius
-constexpr int HS_MAX = TT + 2 * RHO_MAX;
+constexpr int HS_MAX = TT_MAX + 2 * RHO_MAX;
 constexpr float APPROX_EPS = 1e-3f;    // pixel slack of the tile-local (approximate) edge equations
 constexpr int CH = 256;                // faces staged per round (one per thread)
 constexpr int HASH = 2 * CH;           // face id -> staged slot, open addressing
@@ -114,7 +114,8 @@ __device__ __forceinline__ bool approx_candidate(const Pre &P, float lx, float l
     return true;
 }
 
-// position of halo pixel h in the ring of width rho around the tile (tile-local)
+// position of halo pixel h in the ring of width rho around a TT x TT tile (tile-local)
+template <int TT>
 __device__ __forceinline__ void halo_pos(int h, int rho, int &hx, int &hy)
 {
     const int hs = TT + 2 * rho;
@@ -548,15 +549,161 @@ __device__ __forceinline__ int search_start(const int *start, int n, int i)
     return lo;
 }
 
-// per-layer values of one pixel after the raster phase
-struct LayerVal {
-    float dist, l0, l1, l2;
-    bool hard;
-};
+// face of pair i = base + lane: one warp-uniform search for the warp's first pair,
+// then a short walk (a face holds tens of pairs, so a warp spans one or two faces)
+__device__ __forceinline__ int pair_face(const int *start, int n, int base, int i)
+{
+    int f = search_start(start, n, base);
+    while (f + 1 < n && start[f + 1] <= i) ++f;
+    return f;
+}
 
-template <int K, bool BWD>
+// (x, y) of pair q in a rect of width w: q / w by a float reciprocal (exact for q < 2^16)
+__device__ __forceinline__ void rect_xy(int q, int w, int &x, int &y)
+{
+    const int qy = __float2int_rz(((float)q + 0.5f) * __frcp_rn((float)w));
+    x = q - qy * w;
+    y = qy;
+}
+
+// S^H, edge mask, shading and blend (forward) or the adjoint (BWD) of one pixel
+// whose K layer ids are known; S.sh holds the tile's S^H with its ring.
+template <int K, bool BWD, int TT>
+__device__ __forceinline__ void finish_pixel(const Globals &g, const Smem &S, const ViewK &V, const MeshK &M,
+                                             const VRec *vr, int X0, int Y0, int lx, int ly, int rho,
+                                             const int (&ids)[K], bool single_chunk)
+{
+    const int X = X0 + lx, Y = Y0 + ly;
+    const float px = (float)X + 0.5f, py = (float)Y + 0.5f;
+    const int hs = TT + 2 * rho;
+    const long long pix = V.pix_off + (long long)Y * V.W + X;
+    int nl = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) nl += (ids[k] != 0x7fffffff) ? 1 : 0;
+    const bool SH = S.sh[(ly + rho) * hs + (lx + rho)] == 1;
+
+    // edge mask (Sec. 3.3.3): the window of radius rho sees both S^H = 0 and 1
+    bool E = g.edge_mode == 1;
+    if (g.edge_mode == 0) {
+        bool s0 = false, s1 = false;
+        for (int wy = 0; wy <= 2 * rho; ++wy)
+            for (int wx = 0; wx <= 2 * rho; ++wx) {
+                const unsigned char v = S.sh[(ly + wy) * hs + (lx + wx)];
+                s0 |= v == 0;
+                s1 |= v == 1;
+            }
+        E = s0 && s1;
+    }
+
+    if (!BWD) {
+        if (g.ids) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) g.ids[(long long)k * g.n_pix + pix] = (k < nl) ? ids[k] : -1;
+        }
+        float Cs[3] = {0.f, 0.f, 0.f}, C1[3] = {0.f, 0.f, 0.f};
+        float Ds = 0.f, prod = 1.f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            // outside the edge mask only the front layer is seen
+            if (!(k < nl && (E || k == 0))) continue;
+            // re-evaluate the layer at this pixel (from shared memory when the whole tile
+            // list was staged at once): distance and barycentrics
+            const int slot = single_chunk ? find_slot(S, ids[k]) : -1;
+            FaceRec Rg;
+            const FaceRec *R = nullptr;
+            if (slot >= 0) R = &S.F[slot];
+            else if (face_load(g, M, vr, ids[k], Rg)) R = &Rg;
+            Frag fr;
+            if (!R || !eval_face(*R, px, py, V.r_px, V.half_inv_S, fr)) continue;
+            Shade Sh;
+            frag_lambda(*R, fr, Sh.lam);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) { Sh.vi[i] = R->vi[i]; Sh.iw[i] = R->iw[i]; }
+            shade(g, V, M, fr.dist, Sh);
+            Cs[0] = fmaf(Sh.D, Sh.C[0], Cs[0]);
+            Cs[1] = fmaf(Sh.D, Sh.C[1], Cs[1]);
+            Cs[2] = fmaf(Sh.D, Sh.C[2], Cs[2]);
+            Ds += Sh.D;
+            prod *= 1.f - Sh.D;
+            if (k == 0) { C1[0] = Sh.C[0]; C1[1] = Sh.C[1]; C1[2] = Sh.C[2]; }
+        }
+        float4 o;
+        if (E) {
+            const float iD = Ds > 0.f ? 1.f / Ds : 0.f;
+            o = make_float4(Cs[0] * iD, Cs[1] * iD, Cs[2] * iD, 1.f - prod);
+        } else {
+            o = SH ? make_float4(C1[0], C1[1], C1[2], 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        reinterpret_cast<float4 *>(g.out)[pix] = o;
+    } else {
+        if (nl == 0) return;
+        const float4 gi4 = __ldg(reinterpret_cast<const float4 *>(g.gin) + pix);
+        const float gc[3] = {gi4.x, gi4.y, gi4.z};
+        if (gc[0] == 0.f && gc[1] == 0.f && gc[2] == 0.f && gi4.w == 0.f) return;
+        float gCk[K][3], gDk[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) { gDk[k] = 0.f; gCk[k][0] = gCk[k][1] = gCk[k][2] = 0.f; }
+        if (E) {
+            // pass 1: D_k and C_k of every layer
+            float Dk[K], Ck[K][3];
+#pragma unroll
+            for (int k = 0; k < K; ++k) { Dk[k] = 0.f; Ck[k][0] = Ck[k][1] = Ck[k][2] = 0.f; }
+            // rolled loop: one inlined copy of the layer code keeps the kernel small
+#pragma unroll 1
+            for (int k = 0; k < nl; ++k) {
+                Layer L;
+                if (layer_build(g, V, M, vr, ids[k], px, py, L)) {
+                    Dk[k] = L.S.D;
+                    Ck[k][0] = L.S.C[0]; Ck[k][1] = L.S.C[1]; Ck[k][2] = L.S.C[2];
+                }
+            }
+            float Ds = 0.f, Ie[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                Ds += Dk[k];
+                Ie[0] = fmaf(Dk[k], Ck[k][0], Ie[0]);
+                Ie[1] = fmaf(Dk[k], Ck[k][1], Ie[1]);
+                Ie[2] = fmaf(Dk[k], Ck[k][2], Ie[2]);
+            }
+            if (Ds > 0.f) {
+                const float iD = 1.f / Ds;
+                Ie[0] *= iD; Ie[1] *= iD; Ie[2] *= iD;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    gCk[k][0] = Dk[k] * iD * gc[0];
+                    gCk[k][1] = Dk[k] * iD * gc[1];
+                    gCk[k][2] = Dk[k] * iD * gc[2];
+                    gDk[k] = (gc[0] * (Ck[k][0] - Ie[0]) + gc[1] * (Ck[k][1] - Ie[1]) + gc[2] * (Ck[k][2] - Ie[2])) * iD;
+                }
+            }
+            // silhouette 1 - prod_k (1 - D_k)
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                float others = 1.f;
+#pragma unroll
+                for (int j = 0; j < K; ++j)
+                    if (j != k && j < nl) others *= 1.f - Dk[j];
+                if (k < nl) gDk[k] += gi4.w * others;
+            }
+        } else if (SH) {
+            gCk[0][0] = gc[0]; gCk[0][1] = gc[1]; gCk[0][2] = gc[2];
+        }
+        // pass 2: per-layer adjoint
+#pragma unroll 1
+        for (int k = 0; k < nl; ++k) {
+            const float gCl[3] = {gCk[k][0], gCk[k][1], gCk[k][2]};
+            const float gDl = gDk[k];
+            const bool any = gDl != 0.f || gCl[0] != 0.f || gCl[1] != 0.f || gCl[2] != 0.f;
+            Layer L;
+            if (any && layer_build(g, V, M, vr, ids[k], px, py, L)) layer_adjoint(g, V, M, L, px, py, gCl, gDl);
+        }
+    }
+}
+
+template <int K, bool BWD, int TT>
 __global__ void __launch_bounds__(NT, BWD ? 2 : 3) k_tile(Globals g)
 {
+    constexpr int PPT = TT * TT / NT;   // pixels per thread in the per-pixel phases
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
     unsigned long long *kbuf = reinterpret_cast<unsigned long long *>(smem_raw + sizeof(Smem));
@@ -570,24 +717,17 @@ __global__ void __launch_bounds__(NT, BWD ? 2 : 3) k_tile(Globals g)
     const int lt = t - V.tile_base;
     const int X0 = (lt % V.tiles_x) * TT, Y0 = (lt / V.tiles_x) * TT;
     const int tid = threadIdx.x;
-    const int lx = tid & (TT - 1), ly = tid >> 4;
-    const int X = X0 + lx, Y = Y0 + ly;
-    const bool inimg = X < V.W && Y < V.H;
-    const float px = (float)X + 0.5f, py = (float)Y + 0.5f;
     const int rho = (g.edge_mode == 0) ? min(V.rho, RHO_MAX) : 0;
     const int hs = TT + 2 * rho;
-    const long long pix = V.pix_off + (long long)Y * V.W + X;
     const int wlim = min(TT, V.W - X0), hlim = min(TT, V.H - Y0);   // tile part inside the image
 
     for (int i = tid; i < hs * hs; i += NT) {
         const int hx = X0 - rho + i % hs, hy = Y0 - rho + i / hs;
         S.sh[i] = (hx >= 0 && hy >= 0 && hx < V.W && hy < V.H) ? 0 : 2;
     }
-#pragma unroll
-    for (int k = 0; k < K; ++k) kbuf[tid * K + k] = EMPTY;
+    for (int i = tid; i < TT * TT * K; i += NT) kbuf[i] = EMPTY;
 
     const bool from_ids = BWD && g.ids_in != nullptr;
-    int ids[K];
     bool single_chunk = false;
     if (!from_ids) {
         const long long lb = g.tile_off[t], le = g.tile_off[t + 1];
@@ -667,12 +807,12 @@ __global__ void __launch_bounds__(NT, BWD ? 2 : 3) k_tile(Globals g)
             const int total = S.totals[0], htotal = S.totals[1];
             // (face, pixel) pairs of the tile
             for (int i = tid; i < total; i += NT) {
-                const int f = search_start(S.start, nch, i);
+                const int f = pair_face(S.start, nch, i - (tid & 31), i);
                 const int rc = S.rect[f];
-                const int w = (rc >> 16) & 0xff;
-                const int q = i - S.start[f];
-                const int qy = q / w;
-                const int x = (rc & 0xff) + (q - qy * w), y = ((rc >> 8) & 0xff) + qy;
+                int x, y;
+                rect_xy(i - S.start[f], (rc >> 16) & 0xff, x, y);
+                x += rc & 0xff;
+                y += (rc >> 8) & 0xff;
                 const Pre &P = S.P[f];
                 unsigned long long *slots = kbuf + (y * TT + x) * K;
                 float klb;
@@ -685,12 +825,12 @@ __global__ void __launch_bounds__(NT, BWD ? 2 : 3) k_tile(Globals g)
             }
             // (face, pixel) pairs of the ring: hard test only
             for (int i = tid; i < htotal; i += NT) {
-                const int f = search_start(S.hstart, nch, i);
+                const int f = pair_face(S.hstart, nch, i - (tid & 31), i);
                 const int rc = S.hrect[f];
-                const int w = (rc >> 16) & 0xff;
-                const int q = i - S.hstart[f];
-                const int qy = q / w;
-                const int x = (rc & 0xff) - 16 + (q - qy * w), y = ((rc >> 8) & 0xff) - 16 + qy;
+                int x, y;
+                rect_xy(i - S.hstart[f], (rc >> 16) & 0xff, x, y);
+                x += (rc & 0xff) - 16;
+                y += ((rc >> 8) & 0xff) - 16;
                 if (x >= 0 && x < TT && y >= 0 && y < TT) continue;   // interior: decided by the peel
                 const int si = (y + rho) * hs + (x + rho);
                 if (S.sh[si] != 0) continue;
@@ -705,208 +845,112 @@ __global__ void __launch_bounds__(NT, BWD ? 2 : 3) k_tile(Globals g)
             }
         }
         __syncthreads();
+        // S^H of the tile's own pixels from the front slot: hard keys are <= 1/2 and
+        // soft keys >= 1/2, so only a key of exactly 1/2 needs the face again
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const unsigned long long v = kbuf[tid * K + k];
-            ids[k] = (v == EMPTY) ? 0x7fffffff : (int)(unsigned int)(v & 0xffffffffu);
+        for (int j = 0; j < PPT; ++j) {
+            const int p = tid + j * NT;
+            const int lx = p % TT, ly = p / TT;
+            if (lx >= wlim || ly >= hlim) continue;
+            const unsigned long long v = kbuf[p * K];
+            bool sh = false;
+            if (v != EMPTY) {
+                const float key = __uint_as_float((unsigned int)(v >> 32));
+                sh = key < 0.5f;
+                if (key == 0.5f) {
+                    FaceRec R;
+                    Frag fr;
+                    sh = face_load(g, M, vr, (int)(unsigned int)(v & 0xffffffffu), R) &&
+                         eval_face(R, (float)(X0 + lx) + 0.5f, (float)(Y0 + ly) + 0.5f, V.r_px, V.half_inv_S, fr) &&
+                         fr.hard;
+                }
+            }
+            S.sh[(ly + rho) * hs + (lx + rho)] = sh ? 1 : 0;
         }
     } else {
-        // layers stored by the forward
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const int id = inimg ? __ldg(g.ids_in + (long long)k * g.n_pix + pix) : -1;
-            ids[k] = id >= 0 ? id : 0x7fffffff;
-        }
-        for (int h = tid; h < (rho > 0 ? hs * hs - NT : 0); h += NT) {
+        // layers stored by the forward: S^H of the tile and of its ring from the stored
+        // front layer of every pixel
+        const int ring = rho > 0 ? hs * hs - TT * TT : 0;
+        for (int h = tid; h < TT * TT + ring; h += NT) {
             int hx, hy;
-            halo_pos(h, rho, hx, hy);
+            if (h < TT * TT) { hx = h % TT; hy = h / TT; }
+            else halo_pos<TT>(h - TT * TT, rho, hx, hy);
             const int si = (hy + rho) * hs + (hx + rho);
-            if (S.sh[si] != 0) continue;
+            if (S.sh[si] == 2) continue;
             const long long hp = V.pix_off + (long long)(Y0 + hy) * V.W + (X0 + hx);
             const int id = __ldg(g.ids_in + hp);
-            if (id < 0) continue;
-            FaceRec R;
-            if (face_load(g, M, vr, id, R) && hard_test(R, (float)(X0 + hx) + 0.5f, (float)(Y0 + hy) + 0.5f))
-                S.sh[si] = 1;
-        }
-    }
-    int nl = 0;
-#pragma unroll
-    for (int k = 0; k < K; ++k) nl += (ids[k] != 0x7fffffff) ? 1 : 0;
-    if (!inimg) nl = 0;
-
-    // re-evaluate the kept layers at this pixel (from shared memory when the whole
-    // tile list was staged at once): hard flag, distance, barycentrics
-    LayerVal lv[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        lv[k].dist = 0.f; lv[k].l0 = lv[k].l1 = lv[k].l2 = 0.f; lv[k].hard = false;
-        if (k < nl && (!BWD || k == 0)) {
-            const int slot = single_chunk ? find_slot(S, ids[k]) : -1;
-            FaceRec Rg;
-            const FaceRec *R = nullptr;
-            if (slot >= 0) R = &S.F[slot];
-            else if (face_load(g, M, vr, ids[k], Rg)) R = &Rg;
-            Frag fr;
-            if (R && eval_face(*R, px, py, V.r_px, V.half_inv_S, fr)) {
-                float lam[3];
-                frag_lambda(*R, fr, lam);
-                lv[k].dist = fr.dist; lv[k].l0 = lam[0]; lv[k].l1 = lam[1]; lv[k].l2 = lam[2];
-                lv[k].hard = fr.hard;
+            bool sh = false;
+            if (id >= 0) {
+                FaceRec R;
+                sh = face_load(g, M, vr, id, R) && hard_test(R, (float)(X0 + hx) + 0.5f, (float)(Y0 + hy) + 0.5f);
             }
+            S.sh[si] = sh ? 1 : 0;
         }
     }
-    const bool SH = nl > 0 && lv[0].hard;
     __syncthreads();
-    if (inimg) S.sh[(ly + rho) * hs + (lx + rho)] = SH ? 1 : 0;
-    __syncthreads();
-    if (!inimg) return;
 
-    // edge mask (Sec. 3.3.3): the window of radius rho sees both S^H = 0 and 1
-    bool E = g.edge_mode == 1;
-    if (g.edge_mode == 0) {
-        bool s0 = false, s1 = false;
-        for (int wy = 0; wy <= 2 * rho; ++wy)
-            for (int wx = 0; wx <= 2 * rho; ++wx) {
-                const unsigned char v = S.sh[(ly + wy) * hs + (lx + wx)];
-                s0 |= v == 0;
-                s1 |= v == 1;
+    for (int j = 0; j < PPT; ++j) {
+        const int p = tid + j * NT;
+        const int lx = p % TT, ly = p / TT;
+        if (lx >= wlim || ly >= hlim) continue;
+        int ids[K];
+        if (!from_ids) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const unsigned long long v = kbuf[p * K + k];
+                ids[k] = (v == EMPTY) ? 0x7fffffff : (int)(unsigned int)(v & 0xffffffffu);
             }
-        E = s0 && s1;
-    }
-
-    if (!BWD) {
-        if (g.ids) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) g.ids[(long long)k * g.n_pix + pix] = (k < nl) ? ids[k] : -1;
-        }
-        float Cs[3] = {0.f, 0.f, 0.f}, C1[3] = {0.f, 0.f, 0.f};
-        float Ds = 0.f, prod = 1.f;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            // outside the edge mask only the front layer is seen
-            if (!(k < nl && (E || k == 0))) continue;
-            Shade Sh;
-            const int *fv = g.faces + 3 * (M.face_off + ids[k]);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                Sh.vi[i] = __ldg(fv + i);
-                Sh.iw[i] = __ldg(&vr[Sh.vi[i]].iw);
-            }
-            Sh.lam[0] = lv[k].l0; Sh.lam[1] = lv[k].l1; Sh.lam[2] = lv[k].l2;
-            shade(g, V, M, lv[k].dist, Sh);
-            Cs[0] = fmaf(Sh.D, Sh.C[0], Cs[0]);
-            Cs[1] = fmaf(Sh.D, Sh.C[1], Cs[1]);
-            Cs[2] = fmaf(Sh.D, Sh.C[2], Cs[2]);
-            Ds += Sh.D;
-            prod *= 1.f - Sh.D;
-            if (k == 0) { C1[0] = Sh.C[0]; C1[1] = Sh.C[1]; C1[2] = Sh.C[2]; }
-        }
-        float4 o;
-        if (E) {
-            const float iD = Ds > 0.f ? 1.f / Ds : 0.f;
-            o = make_float4(Cs[0] * iD, Cs[1] * iD, Cs[2] * iD, 1.f - prod);
         } else {
-            o = SH ? make_float4(C1[0], C1[1], C1[2], 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        reinterpret_cast<float4 *>(g.out)[pix] = o;
-    } else {
-        if (nl == 0) return;
-        const float4 gi4 = __ldg(reinterpret_cast<const float4 *>(g.gin) + pix);
-        const float gc[3] = {gi4.x, gi4.y, gi4.z};
-        if (gc[0] == 0.f && gc[1] == 0.f && gc[2] == 0.f && gi4.w == 0.f) return;
-        float gCk[K][3], gDk[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) { gDk[k] = 0.f; gCk[k][0] = gCk[k][1] = gCk[k][2] = 0.f; }
-        if (E) {
-            // pass 1: D_k and C_k of every layer
-            float Dk[K], Ck[K][3];
-#pragma unroll
-            for (int k = 0; k < K; ++k) { Dk[k] = 0.f; Ck[k][0] = Ck[k][1] = Ck[k][2] = 0.f; }
+            const long long pix = V.pix_off + (long long)(Y0 + ly) * V.W + (X0 + lx);
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                Layer L;
-                if (k < nl && layer_build(g, V, M, vr, ids[k], px, py, L)) {
-                    Dk[k] = L.S.D;
-                    Ck[k][0] = L.S.C[0]; Ck[k][1] = L.S.C[1]; Ck[k][2] = L.S.C[2];
-                }
+                const int id = __ldg(g.ids_in + (long long)k * g.n_pix + pix);
+                ids[k] = id >= 0 ? id : 0x7fffffff;
             }
-            float Ds = 0.f, Ie[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                Ds += Dk[k];
-                Ie[0] = fmaf(Dk[k], Ck[k][0], Ie[0]);
-                Ie[1] = fmaf(Dk[k], Ck[k][1], Ie[1]);
-                Ie[2] = fmaf(Dk[k], Ck[k][2], Ie[2]);
-            }
-            if (Ds > 0.f) {
-                const float iD = 1.f / Ds;
-                Ie[0] *= iD; Ie[1] *= iD; Ie[2] *= iD;
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    gCk[k][0] = Dk[k] * iD * gc[0];
-                    gCk[k][1] = Dk[k] * iD * gc[1];
-                    gCk[k][2] = Dk[k] * iD * gc[2];
-                    gDk[k] = (gc[0] * (Ck[k][0] - Ie[0]) + gc[1] * (Ck[k][1] - Ie[1]) + gc[2] * (Ck[k][2] - Ie[2])) * iD;
-                }
-            }
-            // silhouette 1 - prod_k (1 - D_k)
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                float others = 1.f;
-#pragma unroll
-                for (int j = 0; j < K; ++j)
-                    if (j != k && j < nl) others *= 1.f - Dk[j];
-                if (k < nl) gDk[k] += gi4.w * others;
-            }
-        } else if (SH) {
-            gCk[0][0] = gc[0]; gCk[0][1] = gc[1]; gCk[0][2] = gc[2];
         }
-        // pass 2: per-layer adjoint
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const bool any = gDk[k] != 0.f || gCk[k][0] != 0.f || gCk[k][1] != 0.f || gCk[k][2] != 0.f;
-            Layer L;
-            if (k < nl && any && layer_build(g, V, M, vr, ids[k], px, py, L))
-                layer_adjoint(g, V, M, L, px, py, gCk[k], gDk[k]);
-        }
+        finish_pixel<K, BWD, TT>(g, S, V, M, vr, X0, Y0, lx, ly, rho, ids, single_chunk);
     }
 }
 
-template <int K>
+template <int K, int TT>
 static size_t tile_smem_bytes()
 {
-    return sizeof(Smem) + sizeof(unsigned long long) * NT * K;
+    return sizeof(Smem) + sizeof(unsigned long long) * TT * TT * K;
 }
 
-template <int K, bool BWD>
+template <int K, bool BWD, int TT>
 static void launch_kk(const Globals &g, cudaStream_t s)
 {
     static bool configured = false;   // per process; the attribute is per function
-    const size_t smem = tile_smem_bytes<K>();
+    const size_t smem = tile_smem_bytes<K, TT>();
     if (!configured) {
-        cudaFuncSetAttribute(k_tile<K, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_tile<K, BWD, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured = true;
     }
-    k_tile<K, BWD><<<g.total_tiles, NT, smem, s>>>(g);
+    k_tile<K, BWD, TT><<<g.total_tiles, NT, smem, s>>>(g);
 }
 
-template <bool BWD>
+template <bool BWD, int TT>
 static void launch_k(const Globals &g, cudaStream_t s)
 {
     switch (g.K) {
-    case 1: launch_kk<1, BWD>(g, s); break;
-    case 2: launch_kk<2, BWD>(g, s); break;
-    case 3: launch_kk<3, BWD>(g, s); break;
-    case 4: launch_kk<4, BWD>(g, s); break;
-    default: launch_kk<5, BWD>(g, s); break;
+    case 1: launch_kk<1, BWD, TT>(g, s); break;
+    case 2: launch_kk<2, BWD, TT>(g, s); break;
+    case 3: launch_kk<3, BWD, TT>(g, s); break;
+    case 4: launch_kk<4, BWD, TT>(g, s); break;
+    default: launch_kk<5, BWD, TT>(g, s); break;
     }
 }
 
 void launch_tile(const Globals &g, bool backward, cudaStream_t s)
 {
-    if (backward) launch_k<true>(g, s);
-    else launch_k<false>(g, s);
+    if (g.tile == 32) {
+        if (backward) launch_k<true, 32>(g, s);
+        else launch_k<false, 32>(g, s);
+    } else {
+        if (backward) launch_k<true, 16>(g, s);
+        else launch_k<false, 16>(g, s);
+    }
     count_launch(1);
 }
 

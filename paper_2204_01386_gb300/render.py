@@ -100,20 +100,21 @@ def make_views(views: Sequence) -> "C.Array":
     return arr, off
 
 
-def make_params(p, list_cap: int = 0) -> B.DressiParams:
+def make_params(p, list_cap: int = 0, tile: int = 0) -> B.DressiParams:
     return B.DressiParams(int(p.K), float(p.r), float(p.sigma), float(p.delta), float(getattr(p, "gamma", 0.0)),
-                          int(p.edge_mode), int(p.shade_mode), int(getattr(p, "texgrad_mode", 0)), 0, int(list_cap))
+                          int(p.edge_mode), int(p.shade_mode), int(getattr(p, "texgrad_mode", 0)), int(tile),
+                          int(list_cap))
 
 
 class Renderer:
     """Owns the workspace and status word for one (scene, views, params) set."""
 
-    def __init__(self, scene: PackedScene, views: Sequence, params, list_cap: int = 0):
+    def __init__(self, scene: PackedScene, views: Sequence, params, list_cap: int = 0, tile: int = 0):
         self.lib = B.load()
         self.scene = scene
         self.views, self.n_pix = make_views(views)
         self.n_views = len(views)
-        self.params = make_params(params, list_cap)
+        self.params = make_params(params, list_cap, tile)
         self.K = int(params.K)
         sc = scene.c_struct()
         self.ws_bytes = int(self.lib.dressi_workspace_size(C.byref(sc), self.views, self.n_views, C.byref(self.params)))

@@ -48,10 +48,10 @@ def masks(o, params, view):
 
 
 class GpuRun:
-    def __init__(self, scene, device="cuda", list_cap=0):
+    def __init__(self, scene, device="cuda", list_cap=0, tile=0):
         self.scene = scene
         self.ps = PackedScene(scene.meshes, device)
-        self.r = Renderer(self.ps, scene.views, scene.params, list_cap=list_cap)
+        self.r = Renderer(self.ps, scene.views, scene.params, list_cap=list_cap, tile=tile)
 
     def forward(self, store_layers=True):
         # layer ids are always kept here so they can be compared; whether the
@@ -105,10 +105,10 @@ def window_of(view, win):
 
 
 def compare_scene(scene, windows=None, seed=0, grad_from_target=None, store_layers=True, list_cap=0,
-                  check_grads=True, report=None):
+                  check_grads=True, report=None, tile=0):
     """Runs both paths on every view (restricted to ``windows``) and asserts parity.
     Returns a dict of the measured errors."""
-    gpu = GpuRun(scene, list_cap=list_cap)
+    gpu = GpuRun(scene, list_cap=list_cap, tile=tile)
     gpu.forward(store_layers=store_layers)
     rng = np.random.default_rng(seed)
     stats = dict(ids_checked=0, ids_unstable=0, fwd_err=0.0, fwd_checked=0)

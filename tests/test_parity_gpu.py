@@ -19,19 +19,21 @@ def _target_images(scene, target, windows=None):
     return out
 
 
+@pytest.mark.parametrize("tile", [16, 32])
 @pytest.mark.parametrize("store_layers", [True, False])
-def test_config1_icosphere_vertex_colour(store_layers):
+def test_config1_icosphere_vertex_colour(store_layers, tile):
     s = synth.config1()
     t = synth.config1_target()
-    st = compare_scene(s, grad_from_target=_target_images(s, t), store_layers=store_layers)
+    st = compare_scene(s, grad_from_target=_target_images(s, t), store_layers=store_layers, tile=tile)
     assert st["ids_checked"] > 4000
 
 
+@pytest.mark.parametrize("tile", [16, 32])
 @pytest.mark.parametrize("store_layers", [True, False])
-def test_config2_textured_lambert(store_layers):
+def test_config2_textured_lambert(store_layers, tile):
     s = synth.config2()
     t = synth.perturbed(s, 99)
-    st = compare_scene(s, grad_from_target=_target_images(s, t), store_layers=store_layers)
+    st = compare_scene(s, grad_from_target=_target_images(s, t), store_layers=store_layers, tile=tile)
     assert st["ids_checked"] > 60000
 
 
@@ -40,7 +42,7 @@ def test_config2_textured_lambert(store_layers):
 def test_layers_and_edge_modes(K, edge_mode):
     s = synth.config1()
     s.params = synth.Params(K=K, r=3 / 64, sigma=3 / 64 / 7, delta=2 / 64, edge_mode=edge_mode, shade_mode=0)
-    compare_scene(s, seed=K * 10 + edge_mode)
+    compare_scene(s, seed=K * 10 + edge_mode, tile=32 if K % 2 else 16)
 
 
 @pytest.mark.parametrize("shade_mode", [1, 2])
@@ -64,7 +66,8 @@ def test_fp16_texture_storage():
     assert st["ids_checked"] > 10000
 
 
-def test_ragged_multi_mesh_multi_view():
+@pytest.mark.parametrize("tile", [16, 32])
+def test_ragged_multi_mesh_multi_view(tile):
     g = synth.rng(3)
     meshes, views = [], []
     for m, (sl, st_, res) in enumerate([(12, 7, 40), (30, 17, 96), (8, 5, 23)]):
@@ -79,18 +82,19 @@ def test_ragged_multi_mesh_multi_view():
         views.append(synth.View(synth.camera_mvp(2.8 * d, res, res), m, res, res))
     views.append(synth.View(synth.camera_mvp((0, 0, 3), 50, 31), 1, 50, 31))
     s = synth.Scene("ragged", meshes, views, synth.soft_params_px(64, shade_mode=2))
-    compare_scene(s)
+    compare_scene(s, tile=tile)
 
 
-def test_tile_list_overflow_falls_back_exactly():
+@pytest.mark.parametrize("tile", [16, 32])
+def test_tile_list_overflow_falls_back_exactly(tile):
     s = synth.config1()
-    full = GpuRun(s)
+    full = GpuRun(s, tile=tile)
     out_a, _ = full.forward()
-    tiny = GpuRun(s, list_cap=16)
+    tiny = GpuRun(s, list_cap=16, tile=tile)
     out_b, _ = tiny.forward()
     assert tiny.status() & 1
     assert torch.equal(out_a, out_b)
-    st = compare_scene(s, list_cap=16, check_grads=False)
+    st = compare_scene(s, list_cap=16, check_grads=False, tile=tile)
     assert st["status"] & 1
 
 
@@ -178,10 +182,11 @@ def test_config3_full_size_sampled(views):
     assert st["ids_checked"] > 2000
 
 
-def test_config5_full_size_crop():
+@pytest.mark.parametrize("tile", [16, 32])
+def test_config5_full_size_crop(tile):
     """1.31M tris, 4096^2 FP16 texture, 8 views at 2048^2, recompute backward;
     checked on a 64 x 64 crop of one view."""
     s = synth.config5()
     wins = [(992, 1000, 64, 64)] + [(0, 0, 0, 0)] * (len(s.views) - 1)
-    st = compare_scene(s, windows=wins, store_layers=False)
+    st = compare_scene(s, windows=wins, store_layers=False, tile=tile)
     assert st["ids_checked"] > 3000
