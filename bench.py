@@ -32,22 +32,42 @@ UNIT = "Mpixel*views/s"
 L2_FLUSH_BYTES = 512 << 20
 
 
-def workload_scene(rank=0, world=1, n_views=64, res=512):
-    """Batched multi-view workload; with several ranks every rank renders its own
-    64 views (Fibonacci directions strided over ranks): weak scaling."""
-    s = synth.config3(n_views=n_views * world, res=res)
+WORKLOADS = ("multiview", "textured", "ragged", "large")
+
+
+def workload_scene(rank=0, world=1, n_views=64, res=512, workload="multiview"):
+    """The benchmark workloads.  multiview (default): 64 views of 512^2 of a 20,480-tri
+    displaced UV sphere, 1024^2 FP32 texture, Lambert.  textured: one 256^2 view of a
+    5,120-tri sphere with a 512^2 texture.  ragged: 32 meshes of 1k..200k tris at mixed
+    resolutions and textures.  large: 1.31M-tri icosphere, 4096^2 FP16 texture, 8 views
+    of 2048^2, checkpointed backward.  With several ranks every rank renders its own
+    views (directions strided over ranks): weak scaling."""
+    if workload == "multiview":
+        s = synth.config3(n_views=n_views * world, res=res)
+    elif workload == "textured":
+        s = synth.config2()
+        s.views = s.views * world
+    elif workload == "ragged":
+        s = synth.config4()
+    else:
+        s = synth.config5(n_views=8 * world)
     s.views = s.views[rank::world]
     return s
 
 
-def workload_desc(s):
+def workload_desc(s, workload="multiview"):
     m = s.meshes[0]
-    return {"workload": "batched multi-view: %d views x %dx%d, %d-tri displaced UV sphere, %dx%d FP32 texture, "
-                        "Lambert, K=%d, r=2px" % (len(s.views), s.views[0].width, s.views[0].height,
-                                                   m.faces.shape[0], m.tex.shape[1], m.tex.shape[0], s.params.K),
-            "views": len(s.views), "resolution": s.views[0].width, "triangles": int(m.faces.shape[0]),
-            "texture": int(m.tex.shape[0]), "K": s.params.K, "store_layers": True,
-            "l2": "512 MiB buffer written between timed steps"}
+    tris = sorted({int(x.faces.shape[0]) for x in s.meshes})
+    d = {"views": len(s.views), "resolution": s.views[0].width, "triangles": tris[0] if len(tris) == 1 else tris,
+         "texture": int(m.tex.shape[0]), "K": s.params.K, "store_layers": bool(s.params.store_layers),
+         "l2": "512 MiB buffer written between timed steps"}
+    if workload == "multiview":
+        d["workload"] = ("batched multi-view: %d views x %dx%d, %d-tri displaced UV sphere, %dx%d FP32 texture, "
+                         "Lambert, K=%d, r=2px" % (len(s.views), s.views[0].width, s.views[0].height,
+                                                    m.faces.shape[0], m.tex.shape[1], m.tex.shape[0], s.params.K))
+    else:
+        d["workload"] = s.name
+    return d
 
 
 # ----------------------------------------------------------------------------
@@ -112,7 +132,7 @@ def time_oracle(scene, n_views, seed=0):
 def reference_arm(args, rank, world):
     if rank != 0:
         return
-    s = workload_scene(0, 1, n_views=args.views)
+    s = workload_scene(0, 1, n_views=args.views, workload=args.workload)
     views_per_step = 1
     for _ in range(args.warmup):
         time_oracle(s, views_per_step)
@@ -127,7 +147,7 @@ def reference_arm(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_desc(s),
+            "config": workload_desc(s, args.workload),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{views_per_step} view(s) of {s.views[0].width}^2 per step, FP64 C oracle "
                                        "(bbox pre-test), single thread"},
@@ -138,21 +158,23 @@ def reference_arm(args, rank, world):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
-def algorithmic_bytes(scene, K, backward):
-    """Bytes one launch of the per-tile kernel must move at minimum (store-layer mode):
-    forward: RGBA out 16 B + K layer ids 4 B per pixel; per view the vertex records
-    (32 B) and faces (12 B); the texture once (16 B/texel).
-    adjoint: dL/dI 16 B + K ids 4 B per pixel; per view vertex records, faces and the
-    screen-gradient accumulators (16 B read + 16 B written per vertex); texture read
-    once and the texel gradient read + written once (2 x 16 B/texel)."""
-    m = scene.meshes[0]
-    V, F = m.pos.shape[0], m.faces.shape[0]
-    texels = m.tex.shape[0] * m.tex.shape[1]
+def algorithmic_bytes(scene, K, backward, store_layers=True):
+    """Bytes one launch of the per-tile kernel must move at minimum:
+    forward: RGBA out 16 B (+ K layer ids 4 B when stored) per pixel; per view the vertex
+    records (32 B) and faces (12 B) of its mesh; every texture once (texel bytes).
+    adjoint: dL/dI 16 B (+ K ids 4 B when stored) per pixel; per view vertex records,
+    faces and the screen-gradient accumulators (16 B read + 16 B written per vertex);
+    textures read once and the FP32 texel gradient read + written once (2 x 16 B/texel)."""
     px = scene.pixels
-    per_view = len(scene.views) * (32 * V + 12 * F)
+    per_view = sum(32 * scene.meshes[v.mesh].pos.shape[0] + 12 * scene.meshes[v.mesh].faces.shape[0]
+                   for v in scene.views)
+    tex_bytes = sum(m.tex.shape[0] * m.tex.shape[1] * 4 * m.tex.itemsize for m in scene.meshes if m.tex is not None)
+    texels = sum(m.tex.shape[0] * m.tex.shape[1] for m in scene.meshes if m.tex is not None)
+    ids = 4 * K if store_layers else 0
     if not backward:
-        return px * (16 + 4 * K) + per_view + 16 * texels
-    return px * (16 + 4 * K) + per_view + len(scene.views) * 32 * V + 3 * 16 * texels
+        return px * (16 + ids) + per_view + tex_bytes
+    acc = sum(32 * scene.meshes[v.mesh].pos.shape[0] for v in scene.views)
+    return px * (16 + ids) + per_view + acc + tex_bytes + 2 * 16 * texels
 
 
 def ours(args, rank, world, local_rank):
@@ -168,28 +190,35 @@ def ours(args, rank, world, local_rank):
     dist = None
     if world > 1:
         import torch.distributed as dist
-    s = workload_scene(rank, world, n_views=args.views)
+    s = workload_scene(rank, world, n_views=args.views, workload=args.workload)
+    store = bool(s.params.store_layers)
     tgt_scene = synth.perturbed(s, 4321 + rank)
     ps = PackedScene(s.meshes, dev)
-    r = Renderer(ps, s.views, s.params, tile=args.tile)
+    r = Renderer(ps, s.views, s.params, tile=args.tile, schedule=args.schedule)
+    tuned = None
+    if args.tile == 0 and args.schedule == 0:
+        tuned = r.autotune(cache_path=os.path.join(tempfile.gettempdir(), "dressi_bench_autotune.json"))
+    tile = int(r.params.tile) or 16
+    schedule = int(r.params.schedule) or 1
     # target images (inputs of the loss), rendered once outside the timed region
     pt = PackedScene(tgt_scene.meshes, dev)
-    rt = Renderer(pt, tgt_scene.views, tgt_scene.params)
+    rt = Renderer(pt, tgt_scene.views, tgt_scene.params, tile=tile)
     target, _ = rt.forward(store_layers=False)
     torch.cuda.synchronize()
     del rt, pt
     lib = B.load()
     n_pix = r.n_pix
     out = torch.empty(n_pix, 4, device=dev)
-    ids = torch.empty(s.params.K, n_pix, dtype=torch.int32, device=dev)
+    ids = torch.empty(s.params.K, n_pix, dtype=torch.int32, device=dev) if store else None
     grad = torch.empty_like(out)
     loss = torch.zeros(1, device=dev)
     gp = torch.empty(3, ps.n_verts_total, device=dev)
     gt = torch.empty(ps.n_texels, 4, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+    stream = torch.cuda.current_stream(dev)
 
     def step():
-        r.forward(store_layers=True, out=out, ids=ids)
+        r.forward(store_layers=store, out=out, ids=ids)
         loss.zero_()
         r.l2_grad(out, target, grad, loss)
         r.backward(grad, ids=ids, grad_pos=gp, grad_tex=gt)
@@ -201,63 +230,115 @@ def ours(args, rank, world, local_rank):
         step()
     torch.cuda.synchronize()
     assert (r.device_status() & ~1) == 0, r.device_status()
+    c0 = lib.dressi_launch_count()
+    step()
+    torch.cuda.synchronize()
+    launches_per_step = lib.dressi_launch_count() - c0
 
-    stream = torch.cuda.current_stream(dev)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    # 1) the per-tile kernels timed live: CUDA events recorded by the library right
+    #    around them, on the stream they are launched on, in non-graph steps
+    n_prof = max(3, min(args.steps, 10))
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(n_prof)]
     for e in ev:
         for x in e:
             x.record(stream)
     torch.cuda.synchronize()
-    launches0 = lib.dressi_launch_count()
+    for k in range(n_prof):
+        flush.fill_(float(k))
+        e = ev[k]
+        lib.dressi_set_profile_events(C.c_void_p(e[0].cuda_event), C.c_void_p(e[1].cuda_event),
+                                      C.c_void_p(e[2].cuda_event), C.c_void_p(e[3].cuda_event))
+        step()
+    torch.cuda.synchronize()
+    lib.dressi_set_profile_events(None, None, None, None)
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    bwd_ms = [e[2].elapsed_time(e[3]) for e in ev]
+
+    # 2) the headline: whole steps, replayed from a CUDA graph (single rank)
+    use_graph = world == 1 and not args.no_graph
+    run = step
+    if use_graph:
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg):
+            step()
+        cg.replay()
+        torch.cuda.synchronize()
+        run = cg.replay
+    tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = Clocks(local_rank)
     clocks.start()
+    time.sleep(0.3)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     for k in range(args.steps):
         flush.fill_(float(k))
-        e = ev[k]
-        lib.dressi_set_profile_events(C.c_void_p(e[2].cuda_event), C.c_void_p(e[3].cuda_event),
-                                      C.c_void_p(e[4].cuda_event), C.c_void_p(e[5].cuda_event))
-        e[0].record(stream)
-        step()
-        e[1].record(stream)
+        tev[k][0].record(stream)
+        run()
+        tev[k][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clock_info = clocks.stop()
-    lib.dressi_set_profile_events(None, None, None, None)
-    launches = lib.dressi_launch_count() - launches0
-    step_ms = [e[0].elapsed_time(e[1]) for e in ev]
-    fwd_ms = [e[2].elapsed_time(e[3]) for e in ev]
-    bwd_ms = [e[4].elapsed_time(e[5]) for e in ev]
+    assert (r.device_status() & ~1) == 0, r.device_status()
+    step_ms = [a.elapsed_time(b) for a, b in tev]
     total_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    px_all = s.pixels * world * args.steps
-    value = px_all / (total_ms * 1e-3) / 1e6
+    value = s.pixels * world * args.steps / (total_ms * 1e-3) / 1e6
 
     # dominant kernel roofline (live CUDA-event durations of the per-tile kernels)
-    import json as _json
     peaks = {}
     try:
-        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     fwd_avg, bwd_avg = statistics.mean(fwd_ms), statistics.mean(bwd_ms)
     bwd_dom = bwd_avg >= fwd_avg
-    kb = algorithmic_bytes(s, s.params.K, bwd_dom)
+    kb = algorithmic_bytes(s, s.params.K, bwd_dom, store)
     dur = (bwd_avg if bwd_dom else fwd_avg) * 1e-3
     achieved = kb / dur / 1e9
-    roofline = {"kernel": "k_tile<3,%s>" % ("bwd" if bwd_dom else "fwd"), "bound": "hbm", "achieved": achieved,
-                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+    roofline = {"kernel": "k_tile<%d,%s,%d>" % (s.params.K, "bwd" if bwd_dom else "fwd", tile), "bound": "hbm",
+                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback",
                 "fwd_tile_ms": fwd_avg, "bwd_tile_ms": bwd_avg, "algorithmic_bytes": kb}
 
-    # end to end through the public API with host buffers
+    # 3) the same views as a plain per-view launch sequence (one call per view, one CTA
+    #    per tile), to compare with the batched form above
+    plain = None
+    if len(s.views) > 1 and not args.no_plain and world == 1:
+        rv = [Renderer(ps, [v], s.params, tile=tile, schedule=1) for v in s.views]
+        offs = [int(x.pix_off) for x in r.views]
+        idv = [torch.empty(s.params.K, v.width * v.height, dtype=torch.int32, device=dev) if store else None
+               for v in s.views]
+
+        def plain_step():
+            for i, (rr, v) in enumerate(zip(rv, s.views)):
+                sl = slice(offs[i], offs[i] + v.width * v.height)
+                rr.forward(store_layers=store, out=out[sl], ids=idv[i])
+                rr.l2_grad(out[sl], target[sl], grad[sl], loss)
+                rr.backward(grad[sl], ids=idv[i], grad_pos=gp, grad_tex=gt)
+
+        for _ in range(2):
+            plain_step()
+        torch.cuda.synchronize()
+        n_plain = max(3, args.steps // 2)
+        pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_plain)]
+        for k in range(n_plain):
+            flush.fill_(float(k))
+            pe[k][0].record(stream)
+            plain_step()
+            pe[k][1].record(stream)
+        torch.cuda.synchronize()
+        pms = sum(a.elapsed_time(b) for a, b in pe)
+        plain = {"value": s.pixels * n_plain / (pms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": pms / n_plain,
+                 "note": "one forward/loss/adjoint call per view, one CTA per tile, no graph"}
+        del rv
+
+    # 4) end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
         h_pos = ps.pos.cpu().pin_memory()
@@ -298,17 +379,19 @@ def ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        nv = args.cpu_views
+        nv = min(args.cpu_views, len(s.views))
         px, dt = time_oracle(s, nv)
         cpu = {"value": px / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{nv} of {len(s.views)} views ({s.views[0].width}^2), forward + adjoint, FP64 C oracle, "
-                         f"single thread, {dt:.1f} s"}
+               "sample": f"{nv} of {len(s.views)} views, forward + adjoint, FP64 C oracle, single thread, {dt:.1f} s"}
     if rank == 0:
+        cfg = workload_desc(s, args.workload)
+        cfg.update({"tile": tile, "schedule": "persistent longest-first" if schedule == 2 else "CTA per tile",
+                    "autotuned": tuned is not None, "list_cap": int(r.params.list_cap), "cuda_graph": use_graph})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": workload_desc(s), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(launches), "clocks": clock_info}
+                "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches_per_step * args.steps), "clocks": clock_info, "plain_per_view": plain}
         print(json.dumps(line), flush=True)
 
 
@@ -322,7 +405,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-views", type=int, default=12)
     ap.add_argument("--views", type=int, default=64, help="views per rank (64 = the benchmark workload)")
-    ap.add_argument("--tile", type=int, default=16, choices=[16, 32], help="screen tile edge in pixels")
+    ap.add_argument("--tile", type=int, default=0, choices=[0, 16, 32],
+                    help="screen tile edge in pixels (0: chosen by the autotuner)")
+    ap.add_argument("--schedule", type=int, default=0, choices=[0, 1, 2],
+                    help="per-tile kernel: 1 one CTA per tile, 2 persistent longest-first (0: autotuner)")
+    ap.add_argument("--workload", default="multiview", choices=WORKLOADS)
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))

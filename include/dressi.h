@@ -115,6 +115,8 @@ typedef struct {
     int32_t shade_mode; /* 0 vertex colour, 1 unlit texture, 2 texture * max(0, n.l) */
     int32_t texgrad_mode; /* 0 warp-aggregated atomics, 1 texel-space gather (deterministic) */
     int32_t tile;       /* tile edge in pixels: 16 or 32; 0 = 16 */
+    int32_t schedule;   /* per-tile kernel: 0 auto (= 1), 1 one CTA per tile, 2 persistent CTAs
+                           pulling (view, tile) items longest face list first */
     int64_t list_cap;   /* tile-list capacity in entries; 0 = library default (see header of
                            dressi_workspace_size) */
 } dressi_params;
@@ -175,6 +177,21 @@ DRESSI_API int dressi_backward(const dressi_scene *scene, const dressi_view *vie
 DRESSI_API int dressi_forward_static_scratch(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
                                              const dressi_params *params, float *out_rgba, int32_t *layer_ids,
                                              int64_t n_pix, int32_t *dev_status, void *stream);
+
+/* Autotuner (no counterpart in the paper): times one forward + adjoint pass for
+   every execution choice (tile edge 16 / 32, schedule 1 / 2) whose workspace fits in
+   ws_bytes, keeps the fastest in params->tile / params->schedule, and sets
+   params->list_cap to the tile-list entries this scene actually needs plus 25 %
+   headroom (so the workspace of later calls can shrink).  The method parameters
+   (K, r, sigma, delta, modes) are not changed.  out_rgba, grad_* and ws are scratch
+   that this call overwrites (same shapes as for dressi_forward / dressi_backward).
+   This call synchronises the host (it reads timings and the list size back), so it
+   must not be captured into a CUDA graph.  *best_ms receives the fastest pass time.
+   Returns DRESSI_ERR_WORKSPACE when no choice fits in ws_bytes. */
+DRESSI_API int dressi_autotune(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
+                               dressi_params *params, float *out_rgba, int64_t n_pix, float *grad_pos,
+                               float *grad_col, float *grad_tex, void *ws, size_t ws_bytes, int32_t *dev_status,
+                               void *stream, float *best_ms);
 
 /* L2 loss helper for training loops: grad[i] = 2 (out[i] - target[i]) over n floats and
    *loss_accum += sum (out - target)^2 (DEVICE float, accumulated atomically). */

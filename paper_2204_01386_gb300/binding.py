@@ -39,7 +39,8 @@ class DressiView(C.Structure):
 class DressiParams(C.Structure):
     _fields_ = [("K", C.c_int32), ("r", C.c_float), ("sigma", C.c_float), ("delta", C.c_float),
                 ("gamma", C.c_float), ("edge_mode", C.c_int32), ("shade_mode", C.c_int32),
-                ("texgrad_mode", C.c_int32), ("tile", C.c_int32), ("list_cap", C.c_int64)]
+                ("texgrad_mode", C.c_int32), ("tile", C.c_int32), ("schedule", C.c_int32),
+                ("list_cap", C.c_int64)]
 
 
 # every symbol declared in include/dressi.h, with its ctypes signature
@@ -54,6 +55,9 @@ SIGNATURES = {
     "dressi_forward_static_scratch": (C.c_int, [C.POINTER(DressiScene), C.POINTER(DressiView), C.c_int32,
                                                 C.POINTER(DressiParams), C.c_void_p, C.c_void_p, C.c_int64,
                                                 C.c_void_p, C.c_void_p]),
+    "dressi_autotune": (C.c_int, [C.POINTER(DressiScene), C.POINTER(DressiView), C.c_int32, C.POINTER(DressiParams),
+                                  C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                  C.c_void_p, C.c_void_p, C.POINTER(C.c_float)]),
     "dressi_l2_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dressi_status_string": (C.c_char_p, [C.c_int]),
     "dressi_dev_status_string": (C.c_char_p, [C.c_int]),

@@ -34,7 +34,8 @@ static void launch_tile_profiled(const Globals &g, bool bwd, cudaStream_t s)
 }
 
 struct Layout {
-    size_t views, meshes, vrec, tile_count, tile_off, tile_cursor, lists, nrm, nrm_sum, sgrad, ngrad, total;
+    size_t views, meshes, vrec, tile_count, tile_off, tile_cursor, lists, nrm, nrm_sum, sgrad, ngrad, queue,
+        tile_order, lpt_hist, total;
     long long n_vrec;
     int total_tiles;
     long long list_cap;
@@ -59,6 +60,7 @@ static bool check_params(const dressi_params *p)
     if (p->shade_mode < 0 || p->shade_mode > 2) return false;
     if (p->texgrad_mode < 0 || p->texgrad_mode > 1) return false;
     if (p->tile != 0 && p->tile != 16 && p->tile != 32) return false;
+    if (p->schedule < 0 || p->schedule > 2) return false;
     if (p->list_cap < 0) return false;
     return true;
 }
@@ -155,6 +157,9 @@ static bool make_plan(const dressi_scene *sc, const dressi_view *views, int n_vi
     L.nrm_sum = o; o = align_up(o + sizeof(float4) * nv);
     L.sgrad = o; o = align_up(o + sizeof(float4) * (size_t)std::max<long long>(vrec, 1));
     L.ngrad = o; o = align_up(o + sizeof(float4) * nv);
+    L.queue = o; o = align_up(o + sizeof(int) * 4);
+    L.tile_order = o; o = align_up(o + sizeof(int) * (size_t)std::max(tiles, 1));
+    L.lpt_hist = o; o = align_up(o + sizeof(int) * LPT_BINS);
     L.total = o;
     return true;
 }
@@ -227,6 +232,10 @@ static Globals make_globals(const dressi_scene *sc, const dressi_params *p, cons
     g.sgrad = reinterpret_cast<float4 *>(ws + L.sgrad);
     g.ngrad = reinterpret_cast<float4 *>(ws + L.ngrad);
     g.status = status;
+    g.persistent = p->schedule == 2;
+    g.queue = reinterpret_cast<int *>(ws + L.queue);
+    g.tile_order = nullptr;
+    g.lpt_hist = reinterpret_cast<int *>(ws + L.lpt_hist);
     return g;
 }
 
@@ -246,6 +255,21 @@ static void run_setup(const Globals &g, const Plan &P, char *ws, bool need_bins,
         cudaMemsetAsync(ws + L.tile_cursor, 0, sizeof(int) * (size_t)L.total_tiles, s);
         launch_bin(g, (int)P.views.size(), P.max_nf_view, s);
     }
+}
+
+// the per-tile kernel, persistent (longest face list first when the lists exist) or
+// one CTA per tile
+static void run_tiles(Globals &g, const Plan &P, char *ws, bool bins_built, bool bwd, cudaStream_t s)
+{
+    if (g.persistent) {
+        cudaMemsetAsync(ws + P.lay.queue, 0, sizeof(int) * 4, s);
+        if (bins_built) {
+            cudaMemsetAsync(ws + P.lay.lpt_hist, 0, sizeof(int) * LPT_BINS, s);
+            g.tile_order = reinterpret_cast<const int *>(ws + P.lay.tile_order);
+            launch_lpt_order(g, s);
+        }
+    }
+    launch_tile_profiled(g, bwd, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -338,7 +362,7 @@ int dressi_forward(const dressi_scene *scene, const dressi_view *views, int32_t 
     g.out = out_rgba;
     g.ids = layer_ids;
     run_setup(g, P, w, true, s);
-    launch_tile_profiled(g, false, s);
+    run_tiles(g, P, w, true, false, s);
     return cudaGetLastError() == cudaSuccess ? DRESSI_OK : DRESSI_ERR_LAUNCH;
 }
 
@@ -382,10 +406,73 @@ int dressi_backward(const dressi_scene *scene, const dressi_view *views, int32_t
     if (params->shade_mode == 2)
         cudaMemsetAsync(w + P.lay.ngrad, 0, sizeof(float4) * (size_t)std::max<long long>(nvt, 1), s);
     run_setup(g, P, w, layer_ids == nullptr, s);
-    launch_tile_profiled(g, true, s);
+    run_tiles(g, P, w, layer_ids == nullptr, true, s);
     launch_vertex_bwd(g, (int)P.views.size(), P.max_nv_view, (int)P.meshes.size(), P.max_nf,
                       params->shade_mode == 2, s);
     return cudaGetLastError() == cudaSuccess ? DRESSI_OK : DRESSI_ERR_LAUNCH;
+}
+
+int dressi_autotune(const dressi_scene *scene, const dressi_view *views, int32_t n_views, dressi_params *params,
+                    float *out_rgba, int64_t n_pix, float *grad_pos, float *grad_col, float *grad_tex, void *ws,
+                    size_t ws_bytes, int32_t *dev_status, void *stream, float *best_ms)
+{
+    if (!params || !out_rgba || !grad_pos || !dev_status || !ws) return DRESSI_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const dressi_params base = *params;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return DRESSI_ERR_LAUNCH;
+    float best = 3.0e38f;
+    dressi_params chosen = base;
+    int rc = DRESSI_ERR_WORKSPACE;
+    const int tiles[2] = {16, 32}, scheds[2] = {1, 2};
+    for (int ti = 0; ti < 2; ++ti) {
+        for (int si = 0; si < 2; ++si) {
+            dressi_params p = base;
+            p.tile = tiles[ti];
+            p.schedule = scheds[si];
+            p.list_cap = 0;
+            Plan P;
+            if (!make_plan(scene, views, n_views, &p, n_pix, P)) { rc = DRESSI_ERR_ARG; goto done; }
+            if (P.lay.total > ws_bytes) continue;
+            float ms = 0.f;
+            for (int rep = 0; rep < 3; ++rep) {   // first run warms up, the best of the others counts
+                cudaEventRecord(e0, s);
+                int r1 = dressi_forward(scene, views, n_views, &p, out_rgba, nullptr, n_pix, ws, ws_bytes,
+                                        dev_status, stream);
+                int r2 = r1 == DRESSI_OK ? dressi_backward(scene, views, n_views, &p, out_rgba, nullptr, n_pix,
+                                                           grad_pos, grad_col, grad_tex, ws, ws_bytes, dev_status,
+                                                           stream)
+                                         : r1;
+                cudaEventRecord(e1, s);
+                if (r2 != DRESSI_OK) { rc = r2; goto done; }
+                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = DRESSI_ERR_LAUNCH; goto done; }
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep == 1 || (rep > 1 && t < ms)) ms = t;
+            }
+            rc = DRESSI_OK;
+            if (ms < best) {
+                // keep this choice and size its tile lists from the entries it needed
+                // (the exclusive scan's last element, written by the last pass)
+                best = ms;
+                chosen = p;
+                int total = 0;
+                if (cudaMemcpy(&total, static_cast<char *>(ws) + P.lay.tile_off + sizeof(int) * P.lay.total_tiles,
+                               sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess)
+                    chosen.list_cap = (long long)total + total / 4 + 1024;
+            }
+        }
+    }
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == DRESSI_OK) {
+        params->tile = chosen.tile;
+        params->schedule = chosen.schedule;
+        params->list_cap = chosen.list_cap;
+        if (best_ms) *best_ms = best;
+    }
+    return rc;
 }
 
 int dressi_l2_loss_grad(const float *out, const float *target, int64_t n, float *grad, float *loss_accum,

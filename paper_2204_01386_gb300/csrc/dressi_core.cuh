@@ -23,6 +23,7 @@ namespace dressi {
 
 constexpr int MAXK = DRESSI_MAX_K;
 constexpr int CHUNK = 128;   // faces staged in shared memory per round
+constexpr int LPT_BINS = 1024;  // face-list lengths bucketed for the longest-first tile order
 constexpr int FLAG_LIVE = 1 << 7;
 constexpr int FLAG_RANGE = 1 << 8;
 
@@ -95,6 +96,12 @@ struct Globals {
     float4 *nrm;          // [n_verts_total] normalized vertex normals
     float4 *nrm_sum;      // [n_verts_total] unnormalized sums
     int *status;
+    // scheduling of the per-tile kernel
+    int persistent;       // 1: persistent CTAs pull tiles from *queue
+    int pad1;
+    int *queue;           // tile queue head (zeroed before each pass)
+    const int *tile_order;  // tiles by descending face-list length, or nullptr
+    int *lpt_hist;        // [LPT_BINS] scratch of the ordering sort
     // forward
     float *out;
     int *ids;             // [K][n_pix] or nullptr

@@ -9,6 +9,7 @@ void launch_vertex(const Globals &g, int n_views, int max_nv, cudaStream_t s);
 void launch_normals(const Globals &g, int n_meshes, int max_nf, cudaStream_t s);
 void launch_bin(const Globals &g, int n_views, int max_nf, cudaStream_t s);
 void launch_tile(const Globals &g, bool backward, cudaStream_t s);
+void launch_lpt_order(const Globals &g, cudaStream_t s);
 void launch_vertex_bwd(const Globals &g, int n_views, int max_nv, int n_meshes, int max_nf, bool normals,
                        cudaStream_t s);
 void launch_l2(const float *out, const float *tgt, long long n, float *grad, float *loss, cudaStream_t s);

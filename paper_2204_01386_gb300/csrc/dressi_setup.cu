@@ -173,6 +173,51 @@ __global__ void __launch_bounds__(1024) k_scan(Globals g)
 }
 
 // ---------------------------------------------------------------------------
+// longest-first tile order for the persistent tile kernel: a counting sort of the
+// tiles by descending face-list length (lengths bucketed, ties in any order)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int lpt_bin(int count) { return LPT_BINS - 1 - min(count, LPT_BINS - 1); }
+
+__global__ void k_lpt_hist(Globals g)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.total_tiles; t += gridDim.x * blockDim.x)
+        atomicAdd(g.lpt_hist + lpt_bin(g.tile_count[t]), 1);
+}
+
+__global__ void __launch_bounds__(LPT_BINS) k_lpt_scan(Globals g)
+{
+    __shared__ int warp_sums[LPT_BINS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int v = g.lpt_hist[tid];
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_sums[lane] = w;
+    }
+    __syncthreads();
+    g.lpt_hist[tid] = x - v + (warp > 0 ? warp_sums[warp - 1] : 0);   // exclusive offsets
+}
+
+__global__ void k_lpt_scatter(Globals g)
+{
+    int *order = const_cast<int *>(g.tile_order);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.total_tiles; t += gridDim.x * blockDim.x)
+        order[atomicAdd(g.lpt_hist + lpt_bin(g.tile_count[t]), 1)] = t;
+}
+
+// ---------------------------------------------------------------------------
 // adjoint, per (view, vertex): (dX, dY, d(1/w)) -> clip -> object space
 // ---------------------------------------------------------------------------
 __global__ void k_vertex_bwd(Globals g)
@@ -293,6 +338,15 @@ void launch_bin(const Globals &g, int n_views, int max_nf, cudaStream_t s)
     k_bin<0><<<grid, 256, 0, s>>>(g);
     k_scan<<<1, 1024, 0, s>>>(g);
     k_bin<1><<<grid, 256, 0, s>>>(g);
+    count_launch(3);
+}
+
+void launch_lpt_order(const Globals &g, cudaStream_t s)
+{
+    const int grid = grid_x(g.total_tiles, 256, 1024);
+    k_lpt_hist<<<grid, 256, 0, s>>>(g);
+    k_lpt_scan<<<1, LPT_BINS, 0, s>>>(g);
+    k_lpt_scatter<<<grid, 256, 0, s>>>(g);
     count_launch(3);
 }
 

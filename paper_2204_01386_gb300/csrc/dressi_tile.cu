@@ -22,6 +22,8 @@
 #include "dressi_core.cuh"
 #include "dressi_launch.h"
 
+#include <algorithm>
+
 namespace dressi {
 
 constexpr int NT = 256;                // threads per CTA
@@ -505,7 +507,7 @@ struct Smem {
     int hstart[CH];      // exclusive prefix of ring pairs
     int2 hash[HASH];     // (face id, slot) of the last staged chunk
     int wsum[2][NT / 32];
-    int view, totals[2];
+    int view, totals[2], next;
     unsigned char sh[HS_MAX * HS_MAX];
 };
 
@@ -700,15 +702,11 @@ __device__ __forceinline__ void finish_pixel(const Globals &g, const Smem &S, co
     }
 }
 
+// everything one CTA does for global tile t
 template <int K, bool BWD, int TT>
-__global__ void __launch_bounds__(NT, BWD ? 2 : 3) k_tile(Globals g)
+__device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned long long *kbuf, const int t)
 {
     constexpr int PPT = TT * TT / NT;   // pixels per thread in the per-pixel phases
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
-    unsigned long long *kbuf = reinterpret_cast<unsigned long long *>(smem_raw + sizeof(Smem));
-
-    const int t = blockIdx.x;
     if (threadIdx.x == 0) S.view = view_of_tile(g, t);
     __syncthreads();
     const ViewK &V = g.views[S.view];
@@ -912,6 +910,35 @@ __global__ void __launch_bounds__(NT, BWD ? 2 : 3) k_tile(Globals g)
     }
 }
 
+// one CTA per tile
+template <int K, bool BWD, int TT>
+__global__ void __launch_bounds__(NT, BWD ? 2 : 3) k_tile(Globals g)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    unsigned long long *kbuf = reinterpret_cast<unsigned long long *>(smem_raw + sizeof(Smem));
+    tile_body<K, BWD, TT>(g, S, kbuf, blockIdx.x);
+}
+
+// persistent: as many CTAs as fit on the GPU pull tiles from one queue, in the
+// order of g.tile_order (longest face list first) when it is given
+template <int K, bool BWD, int TT>
+__global__ void __launch_bounds__(NT, BWD ? 2 : 3) k_tile_persistent(Globals g)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    unsigned long long *kbuf = reinterpret_cast<unsigned long long *>(smem_raw + sizeof(Smem));
+    for (;;) {
+        if (threadIdx.x == 0) S.next = atomicAdd(g.queue, 1);
+        __syncthreads();
+        const int q = S.next;
+        if (q >= g.total_tiles) break;
+        const int t = g.tile_order ? g.tile_order[q] : q;
+        tile_body<K, BWD, TT>(g, S, kbuf, t);
+        __syncthreads();   // the tile's shared memory is free again
+    }
+}
+
 template <int K, int TT>
 static size_t tile_smem_bytes()
 {
@@ -921,13 +948,27 @@ static size_t tile_smem_bytes()
 template <int K, bool BWD, int TT>
 static void launch_kk(const Globals &g, cudaStream_t s)
 {
-    static bool configured = false;   // per process; the attribute is per function
+    // per process: the attributes are per function, the SM count per device
+    static bool configured = false;
+    static int per_sm = 1, sms = 1;
     const size_t smem = tile_smem_bytes<K, TT>();
     if (!configured) {
         cudaFuncSetAttribute(k_tile<K, BWD, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_tile_persistent<K, BWD, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_persistent<K, BWD, TT>, NT, smem);
+        if (per_sm < 1) per_sm = 1;
+        if (sms < 1) sms = 1;
         configured = true;
     }
-    k_tile<K, BWD, TT><<<g.total_tiles, NT, smem, s>>>(g);
+    if (g.persistent) {
+        const int grid = std::min(g.total_tiles, per_sm * sms);
+        k_tile_persistent<K, BWD, TT><<<grid, NT, smem, s>>>(g);
+    } else {
+        k_tile<K, BWD, TT><<<g.total_tiles, NT, smem, s>>>(g);
+    }
 }
 
 template <bool BWD, int TT>

@@ -11,6 +11,9 @@ Layouts (as the C ABI wants them):
 from __future__ import annotations
 
 import ctypes as C
+import hashlib
+import json
+import os
 from typing import List, Optional, Sequence
 
 import numpy as np
@@ -100,21 +103,22 @@ def make_views(views: Sequence) -> "C.Array":
     return arr, off
 
 
-def make_params(p, list_cap: int = 0, tile: int = 0) -> B.DressiParams:
+def make_params(p, list_cap: int = 0, tile: int = 0, schedule: int = 0) -> B.DressiParams:
     return B.DressiParams(int(p.K), float(p.r), float(p.sigma), float(p.delta), float(getattr(p, "gamma", 0.0)),
                           int(p.edge_mode), int(p.shade_mode), int(getattr(p, "texgrad_mode", 0)), int(tile),
-                          int(list_cap))
+                          int(schedule), int(list_cap))
 
 
 class Renderer:
     """Owns the workspace and status word for one (scene, views, params) set."""
 
-    def __init__(self, scene: PackedScene, views: Sequence, params, list_cap: int = 0, tile: int = 0):
+    def __init__(self, scene: PackedScene, views: Sequence, params, list_cap: int = 0, tile: int = 0,
+                 schedule: int = 0):
         self.lib = B.load()
         self.scene = scene
         self.views, self.n_pix = make_views(views)
         self.n_views = len(views)
-        self.params = make_params(params, list_cap, tile)
+        self.params = make_params(params, list_cap, tile, schedule)
         self.K = int(params.K)
         sc = scene.c_struct()
         self.ws_bytes = int(self.lib.dressi_workspace_size(C.byref(sc), self.views, self.n_views, C.byref(self.params)))
@@ -126,6 +130,69 @@ class Renderer:
 
     def _stream(self):
         return C.c_void_p(torch.cuda.current_stream(self.scene.device).cuda_stream)
+
+    def signature(self) -> str:
+        """Key of this workload for the autotune cache: GPU, views, meshes, parameters."""
+        p = self.params
+        parts = [torch.cuda.get_device_name(self.scene.device), str(self.n_views)]
+        parts += ["%d:%dx%d" % (v.mesh, v.width, v.height) for v in self.views]
+        parts += ["%d/%d/%dx%d" % (m.n_verts, m.n_faces, m.tex_w, m.tex_h) for m in self.scene.table]
+        parts += [str(x) for x in (p.K, p.r, p.sigma, p.delta, p.edge_mode, p.shade_mode, p.texgrad_mode)]
+        return hashlib.sha1("|".join(parts).encode()).hexdigest()[:20]
+
+    def autotune(self, cache_path: Optional[str] = None) -> dict:
+        """Chooses tile edge, schedule and tile-list capacity by timing (dressi_autotune),
+        remembering the choice per workload in a JSON file (``cache_path``, else
+        $DRESSI_AUTOTUNE_CACHE, else ~/.cache/dressi/autotune.json)."""
+        path = cache_path or os.environ.get("DRESSI_AUTOTUNE_CACHE") or os.path.join(
+            os.path.expanduser("~"), ".cache", "dressi", "autotune.json")
+        key = self.signature()
+        cache = {}
+        if os.path.exists(path):
+            try:
+                cache = json.load(open(path))
+            except (OSError, ValueError):
+                cache = {}
+        choice = cache.get(key)
+        if choice is None:
+            dev = self.scene.device
+            sc = self.scene.c_struct()
+            need = 0
+            for tile in (16, 32):
+                for sched in (1, 2):
+                    q = B.DressiParams.from_buffer_copy(self.params)
+                    q.tile, q.schedule, q.list_cap = tile, sched, 0
+                    need = max(need, int(self.lib.dressi_workspace_size(C.byref(sc), self.views, self.n_views,
+                                                                       C.byref(q))))
+            ws = torch.empty(need, dtype=torch.uint8, device=dev)
+            out = torch.empty(self.n_pix, 4, dtype=torch.float32, device=dev)
+            gp = torch.empty(3, self.scene.n_verts_total, dtype=torch.float32, device=dev)
+            gc = torch.empty_like(gp) if self.scene.col is not None and self.params.shade_mode == 0 else None
+            gt = (torch.empty(self.scene.n_texels, 4, dtype=torch.float32, device=dev)
+                  if self.scene.tex is not None and self.params.shade_mode != 0 else None)
+            q = B.DressiParams.from_buffer_copy(self.params)
+            best = C.c_float(0.0)
+            code = self.lib.dressi_autotune(C.byref(sc), self.views, self.n_views, C.byref(q), out.data_ptr(),
+                                            self.n_pix, gp.data_ptr(), gc.data_ptr() if gc is not None else None,
+                                            gt.data_ptr() if gt is not None else None, ws.data_ptr(), need,
+                                            self.status.data_ptr(), self._stream(), C.byref(best))
+            B.check(code, "dressi_autotune")
+            choice = {"tile": int(q.tile), "schedule": int(q.schedule), "list_cap": int(q.list_cap),
+                      "ms": float(best.value)}
+            cache[key] = choice
+            try:
+                os.makedirs(os.path.dirname(path), exist_ok=True)
+                tmp = path + ".%d.tmp" % os.getpid()
+                json.dump(cache, open(tmp, "w"), indent=1)
+                os.replace(tmp, path)
+            except OSError:
+                pass
+            del ws
+        self.params.tile, self.params.schedule, self.params.list_cap = choice["tile"], choice["schedule"], choice["list_cap"]
+        sc = self.scene.c_struct()
+        self.ws_bytes = int(self.lib.dressi_workspace_size(C.byref(sc), self.views, self.n_views, C.byref(self.params)))
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.scene.device)
+        return dict(choice)
 
     def forward(self, store_layers: bool = True, out: Optional[torch.Tensor] = None,
                 ids: Optional[torch.Tensor] = None, pos=None, col=None, tex=None):

@@ -43,14 +43,14 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_layout_matches_header(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "dressi.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(dressi_mesh), sizeof(dressi_scene),'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(dressi_mesh), sizeof(dressi_scene),'
                     ' sizeof(dressi_view), sizeof(dressi_params), offsetof(dressi_view, pix_off),'
-                    ' offsetof(dressi_params, list_cap));return 0;}\n')
+                    ' offsetof(dressi_params, list_cap), offsetof(dressi_params, schedule));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [C.sizeof(B.DressiMesh), C.sizeof(B.DressiScene), C.sizeof(B.DressiView), C.sizeof(B.DressiParams),
-            B.DressiView.pix_off.offset, B.DressiParams.list_cap.offset]
+            B.DressiView.pix_off.offset, B.DressiParams.list_cap.offset, B.DressiParams.schedule.offset]
     assert got == want
 
 
@@ -73,19 +73,19 @@ def _views(n=1, w=64, h=48):
 def test_workspace_size_host_only(lib):
     sc, keep = _scene()
     v = _views(2)
-    p = B.DressiParams(3, 0.01, 0.01 / 7, 0.01, 0.0, 0, 0, 0, 0, 0)
+    p = B.DressiParams(3, 0.01, 0.01 / 7, 0.01, 0.0, 0, 0, 0, 0, 0, 0)
     n = lib.dressi_workspace_size(C.byref(sc), v, 2, C.byref(p))
     assert n > 0 and n % 256 == 0
-    p2 = B.DressiParams(3, 0.01, 0.01 / 7, 0.01, 0.0, 0, 0, 0, 0, 10 ** 6)
+    p2 = B.DressiParams(3, 0.01, 0.01 / 7, 0.01, 0.0, 0, 0, 0, 0, 0, 10 ** 6)
     assert lib.dressi_workspace_size(C.byref(sc), v, 2, C.byref(p2)) > n
 
 
 @pytest.mark.parametrize("bad", ["K0", "K6", "sigma0", "edge3", "shade_tex_missing", "mesh_idx", "pix_off", "tile",
-                                 "rho_too_big", "nan_mvp"])
+                                 "rho_too_big", "nan_mvp", "schedule"])
 def test_invalid_arguments_rejected_on_host(lib, bad):
     sc, keep = _scene()
     v = _views(1)
-    p = B.DressiParams(3, 0.01, 0.01 / 7, 0.01, 0.0, 0, 0, 0, 0, 0)
+    p = B.DressiParams(3, 0.01, 0.01 / 7, 0.01, 0.0, 0, 0, 0, 0, 0, 0)
     n_pix = 64 * 48
     if bad == "K0":
         p.K = 0
@@ -107,6 +107,8 @@ def test_invalid_arguments_rejected_on_host(lib, bad):
         p.delta = 0.5
     elif bad == "nan_mvp":
         v[0].mvp[3] = float("nan")
+    elif bad == "schedule":
+        p.schedule = 3
     if bad != "pix_off":   # the image size is only known to the passes
         assert lib.dressi_workspace_size(C.byref(sc), v, 1, C.byref(p)) == 0
     # the entry points reject before touching the device
@@ -120,7 +122,7 @@ def test_invalid_arguments_rejected_on_host(lib, bad):
 def test_workspace_too_small_rejected(lib):
     sc, keep = _scene()
     v = _views(1)
-    p = B.DressiParams(3, 0.01, 0.01 / 7, 0.01, 0.0, 0, 0, 0, 0, 0)
+    p = B.DressiParams(3, 0.01, 0.01 / 7, 0.01, 0.0, 0, 0, 0, 0, 0, 0)
     n = lib.dressi_workspace_size(C.byref(sc), v, 1, C.byref(p))
     code = lib.dressi_forward(C.byref(sc), v, 1, C.byref(p), 0x1000, None, 64 * 48, 0x1000, n - 1, 0x1000, None)
     assert code == B.DRESSI_ERR_WORKSPACE

@@ -190,3 +190,23 @@ def test_config5_full_size_crop(tile):
     wins = [(992, 1000, 64, 64)] + [(0, 0, 0, 0)] * (len(s.views) - 1)
     st = compare_scene(s, windows=wins, store_layers=False, tile=tile)
     assert st["ids_checked"] > 3000
+
+
+def test_autotune_choice_gives_identical_images(tmp_path):
+    """The autotuner only changes execution choices: the layer ids after tuning are
+    bit-identical to the default choice's and the image agrees within the parity
+    tolerance (vertex normals are summed with float atomics, so Lambert images of two
+    runs may differ in the last bits); the choice is cached."""
+    s = synth.config2()
+    ref = GpuRun(s)
+    out_a, ids_a = ref.forward()
+    tuned = GpuRun(s)
+    cache = str(tmp_path / "tune.json")
+    ch = tuned.r.autotune(cache_path=cache)
+    assert ch["tile"] in (16, 32) and ch["schedule"] in (1, 2) and ch["list_cap"] > 0 and ch["ms"] > 0
+    out_b, ids_b = tuned.forward()
+    assert tuned.status() == 0
+    assert torch.equal(ids_a, ids_b)
+    assert (out_a - out_b).abs().max().item() <= 1e-5
+    again = GpuRun(s)
+    assert again.r.autotune(cache_path=cache) == ch   # served from the cache
