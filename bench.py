@@ -191,6 +191,7 @@ def ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
     s = workload_scene(rank, world, n_views=args.views, workload=args.workload)
+    s.params.texgrad_mode = args.texgrad
     store = bool(s.params.store_layers)
     tgt_scene = synth.perturbed(s, 4321 + rank)
     ps = PackedScene(s.meshes, dev)
@@ -385,7 +386,7 @@ def ours(args, rank, world, local_rank):
                "sample": f"{nv} of {len(s.views)} views, forward + adjoint, FP64 C oracle, single thread, {dt:.1f} s"}
     if rank == 0:
         cfg = workload_desc(s, args.workload)
-        cfg.update({"tile": tile, "schedule": "persistent longest-first" if schedule == 2 else "CTA per tile",
+        cfg.update({"texgrad": "texel-space gather" if args.texgrad else "atomics", "tile": tile, "schedule": "persistent longest-first" if schedule == 2 else "CTA per tile",
                     "autotuned": tuned is not None, "list_cap": int(r.params.list_cap), "cuda_graph": use_graph})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -411,6 +412,8 @@ def main():
                     help="per-tile kernel: 1 one CTA per tile, 2 persistent longest-first (0: autotuner)")
     ap.add_argument("--workload", default="multiview", choices=WORKLOADS)
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--texgrad", type=int, default=0, choices=[0, 1],
+                    help="texel gradients: 0 vector red.global atomics, 1 deterministic sort + texel-space gather")
     ap.add_argument("--no-plain", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

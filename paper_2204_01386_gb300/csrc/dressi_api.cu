@@ -34,8 +34,10 @@ static void launch_tile_profiled(const Globals &g, bool bwd, cudaStream_t s)
 }
 
 struct Layout {
-    size_t views, meshes, vrec, tile_count, tile_off, tile_cursor, lists, nrm, nrm_sum, sgrad, ngrad, queue,
-        tile_order, lpt_hist, total;
+    size_t views, meshes, vrec, tile_count, tile_off, tile_cursor, lists, nrm, adj_off, adj_cur, adj, scan_partial,
+        sgrad, ngrad, queue,
+        tile_order, lpt_hist, tg_keys, tg_pay0, tg_pay1, tg_scratch, total;
+    long long tg_slots;   // texel-gather record slots (0 unless texgrad_mode 1 with a texture)
     long long n_vrec;
     int total_tiles;
     long long list_cap;
@@ -45,8 +47,8 @@ struct Plan {
     std::vector<ViewK> views;
     std::vector<MeshK> meshes;
     Layout lay;
-    int max_nv = 0, max_nf = 0, max_nv_view = 0, max_nf_view = 0;
-    long long n_texels = 0;
+    int max_nv = 0, max_nf = 0, max_nv_view = 0, max_nf_view = 0, max_texels = 0;
+    long long n_texels = 0, n_faces = 0;
 };
 
 static bool check_params(const dressi_params *p)
@@ -90,16 +92,18 @@ static bool make_plan(const dressi_scene *sc, const dressi_view *views, int n_vi
         if (textured) {
             if (dm.tex_w <= 0 || dm.tex_h <= 0 || dm.tex_off < 0) return false;
             P.n_texels = std::max(P.n_texels, (long long)dm.tex_off + (long long)dm.tex_w * dm.tex_h);
+            P.max_texels = std::max(P.max_texels, dm.tex_w * dm.tex_h);
         }
         P.max_nv = std::max(P.max_nv, dm.n_verts);
         P.max_nf = std::max(P.max_nf, dm.n_faces);
+        P.n_faces += dm.n_faces;
     }
     if (!sc->pos || !sc->faces) return false;
     if (p->shade_mode == 0 && !sc->col) return false;
     if (textured && (!sc->uv || !sc->tex)) return false;
 
     P.views.resize(n_views);
-    long long vrec = 0, view_faces = 0;
+    long long vrec = 0, view_faces = 0, view_pixels = 0;
     int tiles = 0;
     const int T = p->tile ? p->tile : TILE_DEFAULT;
     for (int v = 0; v < n_views; ++v) {
@@ -130,6 +134,8 @@ static bool make_plan(const dressi_scene *sc, const dressi_view *views, int n_vi
         k.pad = 0;
         k.pix_off = dv.pix_off;
         k.vrec_off = vrec;
+        k.slot_base = view_pixels;
+        view_pixels += (long long)dv.width * dv.height;
         const MeshK &mk = P.meshes[dv.mesh];
         vrec += mk.nV;
         view_faces += mk.nF;
@@ -154,12 +160,21 @@ static bool make_plan(const dressi_scene *sc, const dressi_view *views, int n_vi
     L.lists = o; o = align_up(o + sizeof(int) * (size_t)L.list_cap);
     const size_t nv = (size_t)std::max<long long>(sc->n_verts_total, 1);
     L.nrm = o; o = align_up(o + sizeof(float4) * nv);
-    L.nrm_sum = o; o = align_up(o + sizeof(float4) * nv);
+    L.adj_off = o; o = align_up(o + sizeof(int) * (nv + 1));
+    L.adj_cur = o; o = align_up(o + sizeof(int) * nv);
+    L.adj = o; o = align_up(o + sizeof(int) * 3 * (size_t)std::max<long long>(P.n_faces, 1));
+    L.scan_partial = o; o = align_up(o + sizeof(int) * (size_t)scan_partials_needed((long long)nv + 1));
     L.sgrad = o; o = align_up(o + sizeof(float4) * (size_t)std::max<long long>(vrec, 1));
     L.ngrad = o; o = align_up(o + sizeof(float4) * nv);
     L.queue = o; o = align_up(o + sizeof(int) * 4);
     L.tile_order = o; o = align_up(o + sizeof(int) * (size_t)std::max(tiles, 1));
     L.lpt_hist = o; o = align_up(o + sizeof(int) * LPT_BINS);
+    L.tg_slots = (p->texgrad_mode == 1 && textured) ? view_pixels * p->K : 0;
+    const size_t ts = (size_t)std::max<long long>(L.tg_slots, 1);
+    L.tg_keys = o; o = align_up(o + sizeof(unsigned) * ts);
+    L.tg_pay0 = o; o = align_up(o + sizeof(float4) * ts);
+    L.tg_pay1 = o; o = align_up(o + sizeof(float) * ts);
+    L.tg_scratch = o; o = align_up(o + (L.tg_slots ? texgather_scratch_bytes(L.tg_slots, P.n_texels, ALIGN) : 0));
     L.total = o;
     return true;
 }
@@ -228,7 +243,10 @@ static Globals make_globals(const dressi_scene *sc, const dressi_params *p, cons
     g.tile_cursor = reinterpret_cast<int *>(ws + L.tile_cursor);
     g.lists = reinterpret_cast<int *>(ws + L.lists);
     g.nrm = reinterpret_cast<float4 *>(ws + L.nrm);
-    g.nrm_sum = reinterpret_cast<float4 *>(ws + L.nrm_sum);
+    g.adj_off = reinterpret_cast<int *>(ws + L.adj_off);
+    g.adj_cur = reinterpret_cast<int *>(ws + L.adj_cur);
+    g.adj = reinterpret_cast<int *>(ws + L.adj);
+    g.scan_partial = reinterpret_cast<int *>(ws + L.scan_partial);
     g.sgrad = reinterpret_cast<float4 *>(ws + L.sgrad);
     g.ngrad = reinterpret_cast<float4 *>(ws + L.ngrad);
     g.status = status;
@@ -236,6 +254,10 @@ static Globals make_globals(const dressi_scene *sc, const dressi_params *p, cons
     g.queue = reinterpret_cast<int *>(ws + L.queue);
     g.tile_order = nullptr;
     g.lpt_hist = reinterpret_cast<int *>(ws + L.lpt_hist);
+    g.tg_keys = reinterpret_cast<unsigned *>(ws + L.tg_keys);
+    g.tg_pay0 = reinterpret_cast<float4 *>(ws + L.tg_pay0);
+    g.tg_pay1 = reinterpret_cast<float *>(ws + L.tg_pay1);
+    g.n_texels_max_key = P.n_texels;
     return g;
 }
 
@@ -247,8 +269,10 @@ static void run_setup(const Globals &g, const Plan &P, char *ws, bool need_bins,
     upload(P.meshes.data(), sizeof(MeshK) * P.meshes.size(), ws + L.meshes, s);
     launch_vertex(g, (int)P.views.size(), P.max_nv_view, s);
     if (g.shade_mode == 2) {
-        cudaMemsetAsync(ws + L.nrm_sum, 0, sizeof(float4) * (size_t)std::max<long long>(g.n_verts_total, 1), s);
-        launch_normals(g, (int)P.meshes.size(), P.max_nf, s);
+        const size_t nv = (size_t)std::max<long long>(g.n_verts_total, 1);
+        cudaMemsetAsync(ws + L.adj_off, 0, sizeof(int) * (nv + 1), s);
+        cudaMemsetAsync(ws + L.adj_cur, 0, sizeof(int) * nv, s);
+        launch_normals(g, (int)P.meshes.size(), P.max_nf, P.max_nv, s);
     }
     if (need_bins) {
         cudaMemsetAsync(ws + L.tile_count, 0, sizeof(int) * (size_t)L.total_tiles, s);
@@ -405,8 +429,14 @@ int dressi_backward(const dressi_scene *scene, const dressi_view *views, int32_t
     cudaMemsetAsync(w + P.lay.sgrad, 0, sizeof(float4) * (size_t)std::max<long long>(P.lay.n_vrec, 1), s);
     if (params->shade_mode == 2)
         cudaMemsetAsync(w + P.lay.ngrad, 0, sizeof(float4) * (size_t)std::max<long long>(nvt, 1), s);
+    const bool gather = g.gtex && P.lay.tg_slots > 0;
+    if (!gather) g.texgrad_mode = 0;
+    if (gather) cudaMemsetAsync(w + P.lay.tg_keys, 0xff, sizeof(unsigned) * (size_t)P.lay.tg_slots, s);
     run_setup(g, P, w, layer_ids == nullptr, s);
     run_tiles(g, P, w, layer_ids == nullptr, true, s);
+    if (gather)
+        launch_tex_gather(g, P.lay.tg_slots, P.n_texels, (int)P.meshes.size(), P.max_texels, w + P.lay.tg_scratch,
+                          ALIGN, s);
     launch_vertex_bwd(g, (int)P.views.size(), P.max_nv_view, (int)P.meshes.size(), P.max_nf,
                       params->shade_mode == 2, s);
     return cudaGetLastError() == cudaSuccess ? DRESSI_OK : DRESSI_ERR_LAUNCH;

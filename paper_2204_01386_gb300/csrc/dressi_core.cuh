@@ -23,7 +23,8 @@ namespace dressi {
 
 constexpr int MAXK = DRESSI_MAX_K;
 constexpr int CHUNK = 128;   // faces staged in shared memory per round
-constexpr int LPT_BINS = 1024;  // face-list lengths bucketed for the longest-first tile order
+constexpr int LPT_BINS = 1024;
+constexpr unsigned TG_NONE = 0xffffffffu;  // texel-gather record slot without a texture gradient  // face-list lengths bucketed for the longest-first tile order
 constexpr int FLAG_LIVE = 1 << 7;
 constexpr int FLAG_RANGE = 1 << 8;
 
@@ -44,6 +45,7 @@ struct ViewK {
     int pad;
     long long pix_off;
     long long vrec_off;     // first record of this view in the per-view vertex buffer
+    long long slot_base;    // first pixel of this view in the texel-gather record slots
 };
 
 struct MeshK {
@@ -93,8 +95,11 @@ struct Globals {
     const void *tex;
     VRec *vrec;
     int *tile_count, *tile_off, *tile_cursor, *lists;
-    float4 *nrm;          // [n_verts_total] normalized vertex normals
-    float4 *nrm_sum;      // [n_verts_total] unnormalized sums
+    float4 *nrm;          // [n_verts_total] normalized vertex normals, w = |sum|
+    int *adj_off;         // [n_verts_total + 1] vertex -> incident faces (CSR offsets)
+    int *adj_cur;         // [n_verts_total] fill cursors
+    int *adj;             // [3 * faces] incident face ids (mesh-local)
+    int *scan_partial;    // scratch of the device-wide scan
     int *status;
     // scheduling of the per-tile kernel
     int persistent;       // 1: persistent CTAs pull tiles from *queue
@@ -111,6 +116,12 @@ struct Globals {
     float4 *sgrad;        // per (view, vertex): dX, dY, d(1/w)
     float4 *ngrad;        // [n_verts_total] gradient of the normalized vertex normals
     float *gpos, *gcol, *gtex;
+    // texel-space gather of the texture gradient (texgrad_mode 1): one record per
+    // (pixel, layer) at slot (slot_base + pixel) * K + layer
+    unsigned *tg_keys;
+    float4 *tg_pay0;      // dL/dA (RGB), fx
+    float *tg_pay1;       // fy
+    long long n_texels_max_key;
 };
 
 // ---------------------------------------------------------------------------

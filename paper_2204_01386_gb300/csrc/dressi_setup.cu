@@ -51,38 +51,68 @@ __global__ void k_vertex(Globals g)
 
 // ---------------------------------------------------------------------------
 // area-weighted vertex normals (listing BuildNormalCompute): m_v = sum of
-// (P1 - P0) x (P2 - P0) over the faces holding v, n_v = m_v / |m_v|
+// (P1 - P0) x (P2 - P0) over the faces holding v, n_v = m_v / |m_v|.
+// The sum runs over a vertex -> face adjacency in increasing face order, so the
+// normals (and everything shaded with them) are bitwise reproducible.
 // ---------------------------------------------------------------------------
-__global__ void k_normal_accum(Globals g)
+__device__ __forceinline__ bool face_vertices(const Globals &g, const MeshK &M, int f, int v[3])
+{
+    const int *fv = g.faces + 3 * (M.face_off + f);
+    v[0] = __ldg(fv); v[1] = __ldg(fv + 1); v[2] = __ldg(fv + 2);
+    return (unsigned)v[0] < (unsigned)M.nV && (unsigned)v[1] < (unsigned)M.nV && (unsigned)v[2] < (unsigned)M.nV;
+}
+
+template <int PASS>
+__global__ void k_adjacency(Globals g)
 {
     const MeshK &M = g.meshes[blockIdx.y];
-    const long long nvt = g.n_verts_total;
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < M.nF; f += gridDim.x * blockDim.x) {
-        const int *fv = g.faces + 3 * (M.face_off + f);
-        int v[3] = {__ldg(fv), __ldg(fv + 1), __ldg(fv + 2)};
-        if ((unsigned)v[0] >= (unsigned)M.nV || (unsigned)v[1] >= (unsigned)M.nV || (unsigned)v[2] >= (unsigned)M.nV)
-            continue;
-        float P[3][3];
+        int v[3];
+        if (!face_vertices(g, M, f, v)) continue;
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) P[j][c] = __ldg(g.pos + c * nvt + M.vert_off + v[j]);
-        float u[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
-        float w[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
-        float4 a = make_float4(u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0], 0.f);
-#pragma unroll
-        for (int j = 0; j < 3; ++j) atomicAdd(g.nrm_sum + M.vert_off + v[j], a);
+        for (int j = 0; j < 3; ++j) {
+            const long long gv = M.vert_off + v[j];
+            if (PASS == 0) atomicAdd(g.adj_off + gv, 1);
+            else g.adj[g.adj_off[gv] + atomicAdd(g.adj_cur + gv, 1)] = f;
+        }
     }
 }
 
-__global__ void k_normal_finish(Globals g)
+__global__ void k_normal_csr(Globals g)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.n_verts_total;
-         i += (long long)gridDim.x * blockDim.x) {
-        float4 m = g.nrm_sum[i];
-        float l = sqrtf(m.x * m.x + m.y * m.y + m.z * m.z);
-        float s = l > 0.f ? 1.f / l : 0.f;
-        g.nrm[i] = make_float4(m.x * s, m.y * s, m.z * s, l);
+    const MeshK &M = g.meshes[blockIdx.y];
+    const long long nvt = g.n_verts_total;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M.nV; i += gridDim.x * blockDim.x) {
+        const long long gv = M.vert_off + i;
+        const int b = g.adj_off[gv], e = g.adj_off[gv + 1];
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+        // incident faces in increasing id order (the lists are short: pick the next
+        // larger id each round)
+        int last = -1;
+        for (int round = b; round < e; ++round) {
+            int f = 0x7fffffff;
+            for (int q = b; q < e; ++q) {
+                const int c = g.adj[q];
+                if (c > last && c < f) f = c;
+            }
+            if (f == 0x7fffffff) break;
+            last = f;
+            int v[3];
+            face_vertices(g, M, f, v);
+            float P[3][3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) P[j][c] = __ldg(g.pos + c * nvt + M.vert_off + v[j]);
+            const float u[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+            const float w[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+            m0 += u[1] * w[2] - u[2] * w[1];
+            m1 += u[2] * w[0] - u[0] * w[2];
+            m2 += u[0] * w[1] - u[1] * w[0];
+        }
+        const float l = sqrtf(m0 * m0 + m1 * m1 + m2 * m2);
+        const float s = l > 0.f ? 1.f / l : 0.f;
+        g.nrm[gv] = make_float4(m0 * s, m1 * s, m2 * s, l);
     }
 }
 
@@ -324,12 +354,15 @@ void launch_vertex(const Globals &g, int n_views, int max_nv, cudaStream_t s)
     count_launch(1);
 }
 
-void launch_normals(const Globals &g, int n_meshes, int max_nf, cudaStream_t s)
+void launch_normals(const Globals &g, int n_meshes, int max_nf, int max_nv, cudaStream_t s)
 {
-    dim3 grid(grid_x(max_nf, 256, 2048), n_meshes);
-    k_normal_accum<<<grid, 256, 0, s>>>(g);
-    k_normal_finish<<<grid_x(g.n_verts_total, 256, 4096), 256, 0, s>>>(g);
-    count_launch(2);
+    // adj_off and adj_cur are zeroed by the caller
+    dim3 gf(grid_x(max_nf, 256, 2048), n_meshes), gv(grid_x(max_nv, 256, 2048), n_meshes);
+    k_adjacency<0><<<gf, 256, 0, s>>>(g);
+    launch_scan_inplace(g.adj_off, (int)(g.n_verts_total + 1), g.scan_partial, s);
+    k_adjacency<1><<<gf, 256, 0, s>>>(g);
+    k_normal_csr<<<gv, 256, 0, s>>>(g);
+    count_launch(3);
 }
 
 void launch_bin(const Globals &g, int n_views, int max_nf, cudaStream_t s)

@@ -1,0 +1,300 @@
+// dressi_texgather.cu -- deterministic texel gradients: the texel-space gather
+// alternative to red.global atomics (Sec. 3.2.2: the gradients of the four texels a
+// bilinear sample reads "should be summed up").
+//
+// The adjoint writes one record per (pixel, layer) into a slot fixed by the pixel:
+// key = the global index of the sample's base texel (ix0, iy0), payload = dL/dA
+// (RGB) and the bilinear fractions (fx, fy); slots without a texture gradient keep
+// the key TG_NONE.  Then:
+//   1. a stable LSD radix sort (8-bit digits) orders the (key, slot) pairs by base
+//      texel; the first pass drops TG_NONE keys; equal keys keep slot order;
+//   2. one thread per texel sums, in a fixed order, the records of the four bases
+//      whose bilinear footprint holds the texel (itself, its left, upper and
+//      upper-left neighbours, with REPEAT wrap) with the matching weights.
+// No floating-point atomics: the result is bitwise reproducible.
+#include "dressi_core.cuh"
+#include "dressi_launch.h"
+
+namespace dressi {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 16;                      // items per thread per block
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;    // items per block
+constexpr int RS_BINS = 256;
+
+// --- device-wide exclusive scan of n ints (in place), three kernels -------------
+constexpr int SC_THREADS = 1024;
+constexpr int SC_ITEMS = 4;
+constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
+
+__device__ __forceinline__ int block_excl_scan(int v, int *warp_tot, int &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) warp_tot[lane] = w;
+    }
+    __syncthreads();
+    total = warp_tot[nw - 1];
+    const int r = x - v + (warp > 0 ? warp_tot[warp - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const int *a, int n, int *partial)
+{
+    __shared__ int wt[32];
+    const int base = blockIdx.x * SC_TILE + threadIdx.x * SC_ITEMS;
+    int s = 0;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) s += (base + j < n) ? a[base + j] : 0;
+    int total;
+    block_excl_scan(s, wt, total);
+    if (threadIdx.x == 0) partial[blockIdx.x] = total;
+}
+
+// exclusive scan of the partials in one block (nparts <= SC_TILE); partial[nparts] = total
+__global__ void __launch_bounds__(SC_THREADS) k_scan_partials(int *partial, int nparts)
+{
+    __shared__ int wt[32];
+    const int base = threadIdx.x * SC_ITEMS;
+    int v[SC_ITEMS], s = 0;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) { v[j] = (base + j < nparts) ? partial[base + j] : 0; s += v[j]; }
+    int total;
+    int run = block_excl_scan(s, wt, total);
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        if (base + j < nparts) partial[base + j] = run;
+        run += v[j];
+    }
+    if (threadIdx.x == 0) partial[nparts] = total;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_down(int *a, int n, const int *partial)
+{
+    __shared__ int wt[32];
+    const int base = blockIdx.x * SC_TILE + threadIdx.x * SC_ITEMS;
+    int v[SC_ITEMS], s = 0;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) { v[j] = (base + j < n) ? a[base + j] : 0; s += v[j]; }
+    int total;
+    int run = block_excl_scan(s, wt, total) + partial[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        if (base + j < n) a[base + j] = run;
+        run += v[j];
+    }
+}
+
+// --- stable LSD radix sort pass ---------------------------------------------------
+// Items [0, n) of keys_in/vals_in (n read from *count when count != nullptr);
+// vals_in == nullptr means val = item index.  hist is [RS_BINS][nblocks].
+__device__ __forceinline__ int rs_count(const int *count, long long cap)
+{
+    return count ? *count : (int)cap;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const unsigned *keys, const int *count, long long cap,
+                                                        int shift, int *hist, int nblocks)
+{
+    __shared__ int h[RS_BINS];
+    const int n = rs_count(count, cap);
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * RS_TILE;
+    for (int j = 0; j < RS_ITEMS; ++j) {
+        const long long i = base + j * RS_THREADS + threadIdx.x;
+        if (i < n) {
+            const unsigned k = keys[i];
+            if (k != TG_NONE) atomicAdd(&h[(k >> shift) & 0xff], 1);
+        }
+    }
+    __syncthreads();
+    hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const unsigned *keys_in, const int *vals_in,
+                                                           const int *count, long long cap, int shift,
+                                                           const int *offs, int nblocks, unsigned *keys_out,
+                                                           int *vals_out)
+{
+    __shared__ int run[RS_BINS];                     // next free position of each digit
+    __shared__ int wcnt[RS_THREADS / 32][RS_BINS];   // per-warp digit counts of a round
+    const int n = rs_count(count, cap);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    run[tid] = offs[tid * nblocks + blockIdx.x];
+    const long long base = (long long)blockIdx.x * RS_TILE;
+    for (int j = 0; j < RS_ITEMS; ++j) {
+        for (int w = 0; w < RS_THREADS / 32; ++w) wcnt[w][tid] = 0;
+        __syncthreads();
+        const long long i = base + j * RS_THREADS + tid;
+        unsigned k = TG_NONE;
+        if (i < n) k = keys_in[i];
+        const bool valid = k != TG_NONE;
+        const int d = valid ? (int)((k >> shift) & 0xff) : RS_BINS;   // RS_BINS: dropped
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        // turn the per-warp counts of digit `tid` into exclusive offsets within the round
+        {
+            int acc = 0;
+            for (int w = 0; w < RS_THREADS / 32; ++w) {
+                const int c = wcnt[w][tid];
+                wcnt[w][tid] = acc;
+                acc += c;
+            }
+            __syncthreads();
+            if (valid) {
+                const int pos = run[d] + wcnt[warp][d] + rank;
+                keys_out[pos] = k;
+                vals_out[pos] = vals_in ? vals_in[i] : (int)i;
+            }
+            __syncthreads();
+            run[tid] += acc;
+        }
+        __syncthreads();
+    }
+}
+
+// --- gather ------------------------------------------------------------------------
+// first sorted position with key >= k
+__device__ __forceinline__ int lower_bound_u(const unsigned *keys, int n, unsigned k)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (keys[mid] < k) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_tex_gather(Globals g, const unsigned *keys, const int *vals, const int *count)
+{
+    const MeshK &M = g.meshes[blockIdx.y];
+    const long long n_tex = (long long)M.tex_w * M.tex_h;
+    const int n = *count;
+    const float4 *p0 = g.tg_pay0;
+    const float *p1 = g.tg_pay1;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n_tex;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(q % M.tex_w), y = (int)(q / M.tex_w);
+        const int xl = x == 0 ? M.tex_w - 1 : x - 1, yu = y == 0 ? M.tex_h - 1 : y - 1;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+        // bases whose bilinear footprint holds (x, y): (x, y) as corner 00, (x-1, y) as 10,
+        // (x, y-1) as 01, (x-1, y-1) as 11 (REPEAT wrap)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int bx = (c & 1) ? xl : x, by = (c & 2) ? yu : y;
+            // a texture of width or height 1 wraps a texel onto itself: the same base
+            // then owns several corners of the footprint, all handled by its records
+            const unsigned key = (unsigned)(M.tex_off + (long long)by * M.tex_w + bx);
+            int i = lower_bound_u(keys, n, key);
+            for (; i < n && keys[i] == key; ++i) {
+                const int slot = vals[i];
+                const float4 r = p0[slot];
+                const float fx = r.w, fy = p1[slot];
+                const float wx = (c & 1) ? fx : 1.f - fx, wy = (c & 2) ? fy : 1.f - fy;
+                const float w = wx * wy;
+                a0 = fmaf(w, r.x, a0);
+                a1 = fmaf(w, r.y, a1);
+                a2 = fmaf(w, r.z, a2);
+            }
+        }
+        reinterpret_cast<float4 *>(g.gtex)[M.tex_off + q] = make_float4(a0, a1, a2, 0.f);
+    }
+}
+
+// --- driver -------------------------------------------------------------------------
+static int grid_of(long long n, int block, int cap)
+{
+    long long b = (n + block - 1) / block;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+void launch_scan_inplace(int *a, int n, int *partial, cudaStream_t s)
+{
+    const int nparts = (n + SC_TILE - 1) / SC_TILE;
+    k_scan_reduce<<<nparts, SC_THREADS, 0, s>>>(a, n, partial);
+    k_scan_partials<<<1, SC_THREADS, 0, s>>>(partial, nparts);
+    k_scan_down<<<nparts, SC_THREADS, 0, s>>>(a, n, partial);
+    count_launch(3);
+}
+
+int scan_partials_needed(long long n) { return (int)((n + SC_TILE - 1) / SC_TILE) + 1; }
+
+size_t texgather_scratch_bytes(long long slots, long long n_texels, size_t align)
+{
+    const long long nblocks = (slots + RS_TILE - 1) / RS_TILE;
+    const long long hist = (long long)RS_BINS * nblocks;
+    const long long parts = (hist + SC_TILE - 1) / SC_TILE + 1;
+    auto up = [align](size_t x) { return (x + align - 1) / align * align; };
+    (void)n_texels;
+    return up(sizeof(unsigned) * slots) * 2 + up(sizeof(int) * slots) * 2 + up(sizeof(int) * hist) +
+           up(sizeof(int) * parts) + up(sizeof(int) * 4);
+}
+
+void launch_tex_gather(const Globals &g, long long slots, long long n_texels, int n_meshes, int max_texels,
+                       char *scratch, size_t align, cudaStream_t s)
+{
+    (void)n_texels;
+    auto up = [align](size_t x) { return (x + align - 1) / align * align; };
+    const long long nblocks = (slots + RS_TILE - 1) / RS_TILE;
+    const long long hist_n = (long long)RS_BINS * nblocks;
+    char *p = scratch;
+    unsigned *kA = reinterpret_cast<unsigned *>(p); p += up(sizeof(unsigned) * slots);
+    unsigned *kB = reinterpret_cast<unsigned *>(p); p += up(sizeof(unsigned) * slots);
+    int *vA = reinterpret_cast<int *>(p); p += up(sizeof(int) * slots);
+    int *vB = reinterpret_cast<int *>(p); p += up(sizeof(int) * slots);
+    int *hist = reinterpret_cast<int *>(p); p += up(sizeof(int) * hist_n);
+    int *partial = reinterpret_cast<int *>(p); p += up(sizeof(int) * ((hist_n + SC_TILE - 1) / SC_TILE + 1));
+    int *count = reinterpret_cast<int *>(p);
+    const int nparts = (int)((hist_n + SC_TILE - 1) / SC_TILE);
+
+    // digits needed for the largest key
+    int passes = 1;
+    while (passes < 4 && (1ull << (8 * passes)) <= (unsigned long long)g.n_texels_max_key) ++passes;
+
+    const unsigned *kin = g.tg_keys;
+    const int *vin = nullptr;
+    const int *cnt = nullptr;
+    unsigned *kout = kA;
+    int *vout = vA;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        k_rs_hist<<<(int)nblocks, RS_THREADS, 0, s>>>(kin, cnt, slots, shift, hist, (int)nblocks);
+        launch_scan_inplace(hist, (int)hist_n, partial, s);
+        if (pass == 0) {
+            // the number of kept (valid) records is the scan's total
+            cudaMemcpyAsync(count, partial + nparts, sizeof(int), cudaMemcpyDeviceToDevice, s);
+        }
+        k_rs_scatter<<<(int)nblocks, RS_THREADS, 0, s>>>(kin, vin, cnt, slots, shift, hist, (int)nblocks, kout, vout);
+        count_launch(2);
+        cnt = count;
+        kin = kout;
+        vin = vout;
+        kout = (kout == kA) ? kB : kA;
+        vout = (vout == vA) ? vB : vA;
+    }
+    dim3 grid(grid_of(max_texels, 256, 4096), n_meshes);
+    k_tex_gather<<<grid, 256, 0, s>>>(g, kin, vin, count);
+    count_launch(1);
+}
+
+}  // namespace dressi

@@ -317,7 +317,7 @@ __device__ __forceinline__ bool layer_build(const Globals &g, const ViewK &V, co
 // adjoint of one layer: gC = dL/dC_k, gD = dL/dD_k
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, const MeshK &M, const Layer &L,
-                                              float px, float py, const float gC[3], float gD)
+                                              float px, float py, const float gC[3], float gD, long long slot)
 {
     const long long nvt = g.n_verts_total;
     const FaceRec &R = L.R;
@@ -406,7 +406,12 @@ __device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, 
             const long long i11 = tb + (long long)S.iy[1] * M.tex_w + S.ix[1];
             const float w00 = (1.f - S.fx) * (1.f - S.fy), w10 = S.fx * (1.f - S.fy), w01 = (1.f - S.fx) * S.fy,
                         w11 = S.fx * S.fy;
-            if (g.gtex) {
+            if (g.gtex && g.texgrad_mode == 1) {
+                // deterministic mode: one record at this (pixel, layer)'s own slot
+                g.tg_keys[slot] = (unsigned)i00;
+                g.tg_pay0[slot] = make_float4(gA[0], gA[1], gA[2], S.fx);
+                g.tg_pay1[slot] = S.fy;
+            } else if (g.gtex) {
                 float4 *gt = reinterpret_cast<float4 *>(g.gtex);
                 atomicAdd(gt + i00, make_float4(w00 * gA[0], w00 * gA[1], w00 * gA[2], 0.f));
                 atomicAdd(gt + i10, make_float4(w10 * gA[0], w10 * gA[1], w10 * gA[2], 0.f));
@@ -576,6 +581,7 @@ __device__ __forceinline__ void finish_pixel(const Globals &g, const Smem &S, co
                                              const int (&ids)[K], bool single_chunk)
 {
     const int X = X0 + lx, Y = Y0 + ly;
+    const int lx_g = X, ly_g = Y;   // view-local pixel coordinates
     const float px = (float)X + 0.5f, py = (float)Y + 0.5f;
     const int hs = TT + 2 * rho;
     const long long pix = V.pix_off + (long long)Y * V.W + X;
@@ -697,7 +703,9 @@ __device__ __forceinline__ void finish_pixel(const Globals &g, const Smem &S, co
             const float gDl = gDk[k];
             const bool any = gDl != 0.f || gCl[0] != 0.f || gCl[1] != 0.f || gCl[2] != 0.f;
             Layer L;
-            if (any && layer_build(g, V, M, vr, ids[k], px, py, L)) layer_adjoint(g, V, M, L, px, py, gCl, gDl);
+            const long long slot = (V.slot_base + (long long)ly_g * V.W + lx_g) * K + k;
+            if (any && layer_build(g, V, M, vr, ids[k], px, py, L))
+                layer_adjoint(g, V, M, L, px, py, gCl, gDl, slot);
         }
     }
 }

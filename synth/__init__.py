@@ -149,8 +149,6 @@ def uv_sphere(slices: int, stacks: int):
                 faces.append((v00, v01, v11))
                 faces.append((v00, v11, v10))
     faces = np.asarray(faces, dtype=np.int64)
-    # orientation is decided on a slightly inflated copy so that pole
-    # vertices (which sit on the axis) do not make the test ambiguous
     return pos, _orient_outward(pos, faces).astype(np.int32), uv
 
 
@@ -366,13 +364,13 @@ def config4(seed: int = 1238, n_meshes: int = 32) -> Scene:
 
 
 def config5(seed: int = 1239, subdiv: int = 8, n_views: int = 8, res: int = 2048,
-            tex_side: int = 4096) -> Scene:
+            tex_side: int = 4096, tex_dtype=np.float16) -> Scene:
     """Large: icosphere 8x displaced (1.31M tris), 4096^2 FP16 texture, 8 views at 2048^2."""
     g = rng(seed)
     pos, faces = icosphere(subdiv)
     pos = displace(pos, 0.1, seed)
     pos, faces, uv = icosphere_uv(pos, faces)
-    mesh = Mesh(_f32(pos), faces, uv=_f32(uv), tex=_tex(g, tex_side, np.float16))
+    mesh = Mesh(_f32(pos), faces, uv=_f32(uv), tex=_tex(g, tex_side, tex_dtype))
     views = [View(camera_mvp(3.0 * d, res, res), 0, res, res) for d in fibonacci_dirs(n_views)]
     p = soft_params_px(res, shade_mode=2, store_layers=0)
     return Scene(f"icosphere{subdiv}_{n_views}x{res}px_tex{tex_side}h", [mesh], views, p)

@@ -66,6 +66,26 @@ def test_fp16_texture_storage():
     assert st["ids_checked"] > 10000
 
 
+def test_fp16_texture_error_against_fp32_oracle():
+    """FP16 storage with FP32 arithmetic: against the FP64 oracle fed the FP32 texture,
+    the image error is bounded by the storage rounding of the texels (half an FP16 ulp,
+    2^-12 for texels in [0, 1)), because bilinear weights, Lambert factors and the blend
+    weights are convex combinations or factors <= 1."""
+    s32 = synth.config5(subdiv=4, n_views=2, res=128, tex_side=256, tex_dtype=np.float32)
+    s16 = synth.config5(subdiv=4, n_views=2, res=128, tex_side=256, tex_dtype=np.float16)
+    np.testing.assert_array_equal(s16.meshes[0].tex, s32.meshes[0].tex.astype(np.float16))
+    gpu = GpuRun(s16)
+    gpu.forward()
+    worst = 0.0
+    for i, v in enumerate(s32.views):
+        o = oracle.render(s32.meshes[0], v, s32.params)
+        _, sv = masks(o, s32.params, v)
+        err = np.abs(gpu.view_rgba(i) - o["rgba"])[sv]
+        worst = max(worst, float(err.max()))
+    assert worst <= 2.0 ** -12 + 1e-5, worst
+    assert worst > 1e-6   # the storage rounding is visible: the comparison is not vacuous
+
+
 @pytest.mark.parametrize("tile", [16, 32])
 def test_ragged_multi_mesh_multi_view(tile):
     g = synth.rng(3)
@@ -210,3 +230,42 @@ def test_autotune_choice_gives_identical_images(tmp_path):
     assert (out_a - out_b).abs().max().item() <= 1e-5
     again = GpuRun(s)
     assert again.r.autotune(cache_path=cache) == ch   # served from the cache
+
+
+@pytest.mark.parametrize("store_layers", [True, False])
+def test_texel_gather_mode_matches_oracle(store_layers):
+    """texgrad_mode 1 (sort + texel-space gather, no float atomics) against the oracle."""
+    s = synth.config2(texgrad_mode=1)
+    t = synth.perturbed(s, 99)
+    compare_scene(s, grad_from_target=_target_images(s, t), store_layers=store_layers)
+
+
+def test_texel_gather_is_bitwise_reproducible_and_agrees_with_atomics():
+    s = synth.config2(texgrad_mode=1)
+    g = [np.random.default_rng(4).normal(size=(256, 256, 4))]
+    a = GpuRun(s)
+    a.forward()
+    t1 = a.backward(g)[0][2]
+    t2 = a.backward(g)[0][2]
+    np.testing.assert_array_equal(t1, t2)            # no atomics: identical bits every run
+    s0 = synth.config2(texgrad_mode=0)
+    b = GpuRun(s0)
+    b.forward()
+    t0 = b.backward(g)[0][2]
+    assert rel_l2(t1, t0) < 1e-6
+    assert np.abs(t1).max() > 0
+
+
+def test_texel_gather_ragged_multi_texture():
+    """Several meshes with textures of different sizes share one sorted record list."""
+    g = synth.rng(8)
+    meshes, views = [], []
+    for m, (sl, st_, side) in enumerate([(16, 9, 32), (24, 13, 64), (10, 7, 16)]):
+        pos, faces, uv = synth.uv_sphere(sl, st_)
+        tex = np.zeros((side, side, 4), np.float32)
+        tex[..., :3] = g.random((side, side, 3))
+        meshes.append(synth.Mesh(pos.astype(np.float32), faces, uv=uv.astype(np.float32), tex=tex))
+        d = g.normal(size=3)
+        views.append(synth.View(synth.camera_mvp(2.8 * d / np.linalg.norm(d), 48, 48), m, 48, 48))
+    s = synth.Scene("ragged_gather", meshes, views, synth.soft_params_px(48, shade_mode=1, texgrad_mode=1))
+    compare_scene(s)
