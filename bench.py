@@ -28,6 +28,14 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 METRIC = "fwd+bwd Mpixel*views/s"
+# FP32 arithmetic (an FMA counts 2) the method needs per unit of work, counted from
+# the operations written in the kernels: one exact SignedDist + Shift evaluation of a
+# candidate face at a pixel; one layer's barycentrics, texture sample, Lambert
+# shading and blend; one layer's adjoint with the forward values it recomputes.
+FLOP_CANDIDATE = 50
+FLOP_SHADE_LAYER = 110
+FLOP_ADJOINT_LAYER = 340
+SMS, FP32_LANES_PER_SM = 152, 128
 UNIT = "Mpixel*views/s"
 L2_FLUSH_BYTES = 512 << 20
 
@@ -177,6 +185,26 @@ def algorithmic_bytes(scene, K, backward, store_layers=True):
     return px * (16 + ids) + per_view + acc + tex_bytes + 2 * 16 * texels
 
 
+def recorded_traffic(kernel, pixels):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled to
+    `pixels`, or None when the kernel sources changed since the capture."""
+    import hashlib
+    try:
+        rec = dict(line.split(": ", 1) for line in open(os.path.join(ROOT, "profiles", "k_tile_traffic.txt"))
+                   .read().splitlines() if line and not line.startswith("#"))
+    except OSError:
+        return None
+    csrc = os.path.join(ROOT, "paper_2204_01386_gb300", "csrc")
+    h = hashlib.sha1(open(os.path.join(csrc, "dressi_tile.cu"), "rb").read() +
+                     open(os.path.join(csrc, "dressi_core.cuh"), "rb").read()).hexdigest()[:16]
+    if rec.get("source_hash") != h:
+        return None
+    for d in ("fwd", "bwd"):
+        if rec.get(d + "_kernel") == kernel:
+            return int(rec[d + "_bytes"]) * pixels / int(rec["pixels_captured"])
+    return None
+
+
 def ours(args, rank, world, local_rank):
     import ctypes as C
 
@@ -198,7 +226,8 @@ def ours(args, rank, world, local_rank):
     r = Renderer(ps, s.views, s.params, tile=args.tile, schedule=args.schedule)
     tuned = None
     if args.tile == 0 and args.schedule == 0:
-        tuned = r.autotune(cache_path=os.path.join(tempfile.gettempdir(), "dressi_bench_autotune.json"))
+        tuned = r.autotune(cache_path=os.path.join(tempfile.gettempdir(), "dressi_bench_autotune.json"),
+                           store_layers=store)
     tile = int(r.params.tile) or 16
     schedule = int(r.params.schedule) or 1
     # target images (inputs of the loss), rendered once outside the timed region
@@ -255,6 +284,18 @@ def ours(args, rank, world, local_rank):
     fwd_ms = [e[0].elapsed_time(e[1]) for e in ev]
     bwd_ms = [e[2].elapsed_time(e[3]) for e in ev]
 
+    # work counters of one forward and one adjoint launch (untimed pass)
+    counters = torch.zeros(4, dtype=torch.int64, device=dev)
+    lib.dressi_set_stats_buffer(C.c_void_p(counters.data_ptr()))
+    r.forward(store_layers=store, out=out, ids=ids)
+    torch.cuda.synchronize()
+    st_fwd = [int(x) for x in counters.tolist()]
+    counters.zero_()
+    r.backward(grad, ids=ids, grad_pos=gp, grad_tex=gt)
+    torch.cuda.synchronize()
+    st_bwd = [int(x) for x in counters.tolist()]
+    lib.dressi_set_stats_buffer(None)
+
     # 2) the headline: whole steps, replayed from a CUDA graph (single rank)
     use_graph = world == 1 and not args.no_graph
     run = step
@@ -301,11 +342,22 @@ def ours(args, rank, world, local_rank):
     bwd_dom = bwd_avg >= fwd_avg
     kb = algorithmic_bytes(s, s.params.K, bwd_dom, store)
     dur = (bwd_avg if bwd_dom else fwd_avg) * 1e-3
-    achieved = kb / dur / 1e9
-    roofline = {"kernel": "k_tile<%d,%s,%d>" % (s.params.K, "bwd" if bwd_dom else "fwd", tile), "bound": "hbm",
-                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback",
-                "fwd_tile_ms": fwd_avg, "bwd_tile_ms": bwd_avg, "algorithmic_bytes": kb}
+    st = st_bwd if bwd_dom else st_fwd
+    flops = st[2] * FLOP_CANDIDATE + st[3] * (FLOP_ADJOINT_LAYER if bwd_dom else FLOP_SHADE_LAYER)
+    sm_mhz = clock_info.get("sm_mhz") or 2070.0
+    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flops / dur / 1e12
+    kname = "k_tile<%d,%s,%d>" % (s.params.K, "bwd" if bwd_dom else "fwd", tile)
+    roofline = {"kernel": kname, "bound": "alu",
+                "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                "traffic": recorded_traffic(kname, s.pixels) if args.workload == "multiview" else None,
+                "peak_source": "FP32: %d SMs x %d lanes x 2 FLOP x %.0f MHz (sampled SM clock)" % (
+                    SMS, FP32_LANES_PER_SM, sm_mhz),
+                "algorithmic_flop": flops, "fwd_tile_ms": fwd_avg, "bwd_tile_ms": bwd_avg,
+                "work_fwd": dict(zip(("pairs", "exact_evals", "candidates", "layers"), st_fwd)),
+                "work_bwd": dict(zip(("pairs", "exact_evals", "candidates", "layers"), st_bwd)),
+                "hbm_algorithmic_bytes": kb, "hbm_achieved_gbs": kb / dur / 1e9,
+                "hbm_frac": kb / dur / 1e9 / hbm_peak}
 
     # 3) the same views as a plain per-view launch sequence (one call per view, one CTA
     #    per tile), to compare with the batched form above

@@ -183,13 +183,16 @@ DRESSI_API int dressi_forward_static_scratch(const dressi_scene *scene, const dr
    ws_bytes, keeps the fastest in params->tile / params->schedule, and sets
    params->list_cap to the tile-list entries this scene actually needs plus 25 %
    headroom (so the workspace of later calls can shrink).  The method parameters
-   (K, r, sigma, delta, modes) are not changed.  out_rgba, grad_* and ws are scratch
-   that this call overwrites (same shapes as for dressi_forward / dressi_backward).
+   (K, r, sigma, delta, modes) are not changed.  out_rgba, layer_ids, grad_* and ws
+   are scratch that this call overwrites (same shapes as for dressi_forward /
+   dressi_backward); pass layer_ids (or NULL) as the calls being tuned will, since
+   keeping the layer ids or re-rasterizing in the adjoint changes which choice wins.
    This call synchronises the host (it reads timings and the list size back), so it
    must not be captured into a CUDA graph.  *best_ms receives the fastest pass time.
    Returns DRESSI_ERR_WORKSPACE when no choice fits in ws_bytes. */
 DRESSI_API int dressi_autotune(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
-                               dressi_params *params, float *out_rgba, int64_t n_pix, float *grad_pos,
+                               dressi_params *params, float *out_rgba, int32_t *layer_ids, int64_t n_pix,
+                               float *grad_pos,
                                float *grad_col, float *grad_tex, void *ws, size_t ws_bytes, int32_t *dev_status,
                                void *stream, float *best_ms);
 
@@ -210,6 +213,14 @@ DRESSI_API const char *dressi_dev_status_string(int bit);
    cudaEventElapsedTime.  fwd_* are used by dressi_forward, bwd_* by
    dressi_backward; NULL disables.  Process-wide setting, not thread safe. */
 DRESSI_API int dressi_set_profile_events(void *fwd_begin, void *fwd_end, void *bwd_begin, void *bwd_end);
+
+/* Statistics hook (no counterpart in the paper): when dev_counters (DEVICE array of
+   4 unsigned 64-bit integers, caller-owned and caller-zeroed) is set, every per-tile
+   kernel adds to it: [0] (face, pixel) pairs enumerated, [1] exact SignedDist
+   evaluations, [2] of those, candidates (dist >= -r) merged into a K-list, [3] layers
+   shaded (forward) or back-propagated (adjoint).  NULL disables.  Process-wide
+   setting, not thread safe; the counting costs one atomic per warp and tile. */
+DRESSI_API int dressi_set_stats_buffer(void *dev_counters);
 
 /* Number of kernels this library has launched since it was loaded (process-wide). */
 DRESSI_API unsigned long long dressi_launch_count(void);

@@ -56,14 +56,15 @@ SIGNATURES = {
                                                 C.POINTER(DressiParams), C.c_void_p, C.c_void_p, C.c_int64,
                                                 C.c_void_p, C.c_void_p]),
     "dressi_autotune": (C.c_int, [C.POINTER(DressiScene), C.POINTER(DressiView), C.c_int32, C.POINTER(DressiParams),
-                                  C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
-                                  C.c_void_p, C.c_void_p, C.POINTER(C.c_float)]),
+                                  C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_size_t, C.c_void_p, C.c_void_p, C.POINTER(C.c_float)]),
     "dressi_l2_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dressi_status_string": (C.c_char_p, [C.c_int]),
     "dressi_dev_status_string": (C.c_char_p, [C.c_int]),
     "dressi_abi_version": (C.c_int, []),
     "dressi_set_profile_events": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dressi_launch_count": (C.c_ulonglong, []),
+    "dressi_set_stats_buffer": (C.c_int, [C.c_void_p]),
 }
 
 _lock = threading.Lock()

@@ -24,6 +24,8 @@ void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memo
 
 // optional events recorded around the per-tile kernel (profiling hook)
 static cudaEvent_t g_prof[4] = {nullptr, nullptr, nullptr, nullptr};
+// optional device work counters of the per-tile kernel (statistics hook)
+static unsigned long long *g_stats = nullptr;
 
 static void launch_tile_profiled(const Globals &g, bool bwd, cudaStream_t s)
 {
@@ -254,6 +256,7 @@ static Globals make_globals(const dressi_scene *sc, const dressi_params *p, cons
     g.queue = reinterpret_cast<int *>(ws + L.queue);
     g.tile_order = nullptr;
     g.lpt_hist = reinterpret_cast<int *>(ws + L.lpt_hist);
+    g.stats = g_stats;
     g.tg_keys = reinterpret_cast<unsigned *>(ws + L.tg_keys);
     g.tg_pay0 = reinterpret_cast<float4 *>(ws + L.tg_pay0);
     g.tg_pay1 = reinterpret_cast<float *>(ws + L.tg_pay1);
@@ -340,6 +343,12 @@ int dressi_set_profile_events(void *fwd_begin, void *fwd_end, void *bwd_begin, v
 }
 
 unsigned long long dressi_launch_count(void) { return g_launches.load(); }
+
+int dressi_set_stats_buffer(void *dev_counters)
+{
+    g_stats = static_cast<unsigned long long *>(dev_counters);
+    return DRESSI_OK;
+}
 
 const char *dressi_status_string(int code)
 {
@@ -443,8 +452,8 @@ int dressi_backward(const dressi_scene *scene, const dressi_view *views, int32_t
 }
 
 int dressi_autotune(const dressi_scene *scene, const dressi_view *views, int32_t n_views, dressi_params *params,
-                    float *out_rgba, int64_t n_pix, float *grad_pos, float *grad_col, float *grad_tex, void *ws,
-                    size_t ws_bytes, int32_t *dev_status, void *stream, float *best_ms)
+                    float *out_rgba, int32_t *layer_ids, int64_t n_pix, float *grad_pos, float *grad_col,
+                    float *grad_tex, void *ws, size_t ws_bytes, int32_t *dev_status, void *stream, float *best_ms)
 {
     if (!params || !out_rgba || !grad_pos || !dev_status || !ws) return DRESSI_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -465,11 +474,11 @@ int dressi_autotune(const dressi_scene *scene, const dressi_view *views, int32_t
             if (!make_plan(scene, views, n_views, &p, n_pix, P)) { rc = DRESSI_ERR_ARG; goto done; }
             if (P.lay.total > ws_bytes) continue;
             float ms = 0.f;
-            for (int rep = 0; rep < 3; ++rep) {   // first run warms up, the best of the others counts
+            for (int rep = 0; rep < 5; ++rep) {   // two runs warm up, the best of the others counts
                 cudaEventRecord(e0, s);
-                int r1 = dressi_forward(scene, views, n_views, &p, out_rgba, nullptr, n_pix, ws, ws_bytes,
+                int r1 = dressi_forward(scene, views, n_views, &p, out_rgba, layer_ids, n_pix, ws, ws_bytes,
                                         dev_status, stream);
-                int r2 = r1 == DRESSI_OK ? dressi_backward(scene, views, n_views, &p, out_rgba, nullptr, n_pix,
+                int r2 = r1 == DRESSI_OK ? dressi_backward(scene, views, n_views, &p, out_rgba, layer_ids, n_pix,
                                                            grad_pos, grad_col, grad_tex, ws, ws_bytes, dev_status,
                                                            stream)
                                          : r1;
@@ -478,7 +487,7 @@ int dressi_autotune(const dressi_scene *scene, const dressi_view *views, int32_t
                 if (cudaEventSynchronize(e1) != cudaSuccess) { rc = DRESSI_ERR_LAUNCH; goto done; }
                 float t = 0.f;
                 cudaEventElapsedTime(&t, e0, e1);
-                if (rep == 1 || (rep > 1 && t < ms)) ms = t;
+                if (rep == 2 || (rep > 2 && t < ms)) ms = t;
             }
             rc = DRESSI_OK;
             if (ms < best) {

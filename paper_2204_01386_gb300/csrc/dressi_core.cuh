@@ -118,6 +118,7 @@ struct Globals {
     float *gpos, *gcol, *gtex;
     // texel-space gather of the texture gradient (texgrad_mode 1): one record per
     // (pixel, layer) at slot (slot_base + pixel) * K + layer
+    unsigned long long *stats;  // optional work counters (see dressi_set_stats_buffer) or nullptr
     unsigned *tg_keys;
     float4 *tg_pay0;      // dL/dA (RGB), fx
     float *tg_pay1;       // fy

@@ -576,7 +576,7 @@ __device__ __forceinline__ void rect_xy(int q, int w, int &x, int &y)
 // S^H, edge mask, shading and blend (forward) or the adjoint (BWD) of one pixel
 // whose K layer ids are known; S.sh holds the tile's S^H with its ring.
 template <int K, bool BWD, int TT>
-__device__ __forceinline__ void finish_pixel(const Globals &g, const Smem &S, const ViewK &V, const MeshK &M,
+__device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S, const ViewK &V, const MeshK &M,
                                              const VRec *vr, int X0, int Y0, int lx, int ly, int rho,
                                              const int (&ids)[K], bool single_chunk)
 {
@@ -603,6 +603,7 @@ __device__ __forceinline__ void finish_pixel(const Globals &g, const Smem &S, co
         E = s0 && s1;
     }
 
+    unsigned layers = 0;
     if (!BWD) {
         if (g.ids) {
 #pragma unroll
@@ -624,6 +625,7 @@ __device__ __forceinline__ void finish_pixel(const Globals &g, const Smem &S, co
             Frag fr;
             if (!R || !eval_face(*R, px, py, V.r_px, V.half_inv_S, fr)) continue;
             Shade Sh;
+            ++layers;
             frag_lambda(*R, fr, Sh.lam);
 #pragma unroll
             for (int i = 0; i < 3; ++i) { Sh.vi[i] = R->vi[i]; Sh.iw[i] = R->iw[i]; }
@@ -644,10 +646,10 @@ __device__ __forceinline__ void finish_pixel(const Globals &g, const Smem &S, co
         }
         reinterpret_cast<float4 *>(g.out)[pix] = o;
     } else {
-        if (nl == 0) return;
+        if (nl == 0) return 0;
         const float4 gi4 = __ldg(reinterpret_cast<const float4 *>(g.gin) + pix);
         const float gc[3] = {gi4.x, gi4.y, gi4.z};
-        if (gc[0] == 0.f && gc[1] == 0.f && gc[2] == 0.f && gi4.w == 0.f) return;
+        if (gc[0] == 0.f && gc[1] == 0.f && gc[2] == 0.f && gi4.w == 0.f) return 0;
         float gCk[K][3], gDk[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) { gDk[k] = 0.f; gCk[k][0] = gCk[k][1] = gCk[k][2] = 0.f; }
@@ -704,10 +706,13 @@ __device__ __forceinline__ void finish_pixel(const Globals &g, const Smem &S, co
             const bool any = gDl != 0.f || gCl[0] != 0.f || gCl[1] != 0.f || gCl[2] != 0.f;
             Layer L;
             const long long slot = (V.slot_base + (long long)ly_g * V.W + lx_g) * K + k;
-            if (any && layer_build(g, V, M, vr, ids[k], px, py, L))
+            if (any && layer_build(g, V, M, vr, ids[k], px, py, L)) {
+                ++layers;
                 layer_adjoint(g, V, M, L, px, py, gCl, gDl, slot);
+            }
         }
     }
+    return layers;
 }
 
 // everything one CTA does for global tile t
@@ -735,6 +740,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
 
     const bool from_ids = BWD && g.ids_in != nullptr;
     bool single_chunk = false;
+    unsigned n_pairs = 0, n_exact = 0, n_cand = 0, n_layers = 0;
     if (!from_ids) {
         const long long lb = g.tile_off[t], le = g.tile_off[t + 1];
         const bool fallback = le > g.list_cap;
@@ -812,6 +818,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
             __syncthreads();
             const int total = S.totals[0], htotal = S.totals[1];
             // (face, pixel) pairs of the tile
+            if (g.stats) n_pairs += (total > tid) ? (total - tid + NT - 1) / NT : 0;
             for (int i = tid; i < total; i += NT) {
                 const int f = pair_face(S.start, nch, i - (tid & 31), i);
                 const int rc = S.rect[f];
@@ -826,8 +833,11 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                 const unsigned long long last = *reinterpret_cast<volatile unsigned long long *>(slots + K - 1);
                 if (klb > __uint_as_float((unsigned int)(last >> 32))) continue;
                 Frag fr;
-                if (eval_face(S.F[f], (float)(X0 + x) + 0.5f, (float)(Y0 + y) + 0.5f, V.r_px, V.half_inv_S, fr))
+                ++n_exact;
+                if (eval_face(S.F[f], (float)(X0 + x) + 0.5f, (float)(Y0 + y) + 0.5f, V.r_px, V.half_inv_S, fr)) {
+                    ++n_cand;
                     kbuf_insert<K>(slots, pack_frag(fr.key, S.F[f].id));
+                }
             }
             // (face, pixel) pairs of the ring: hard test only
             for (int i = tid; i < htotal; i += NT) {
@@ -914,7 +924,17 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                 ids[k] = id >= 0 ? id : 0x7fffffff;
             }
         }
-        finish_pixel<K, BWD, TT>(g, S, V, M, vr, X0, Y0, lx, ly, rho, ids, single_chunk);
+        n_layers += finish_pixel<K, BWD, TT>(g, S, V, M, vr, X0, Y0, lx, ly, rho, ids, single_chunk);
+    }
+    if (g.stats) {
+        // work counters: pairs enumerated, exact evaluations, candidates kept, layers shaded
+        unsigned long long c[4] = {n_pairs, n_exact, n_cand, n_layers};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c[q] += __shfl_xor_sync(0xffffffffu, c[q], o);
+            if ((threadIdx.x & 31) == 0) atomicAdd(g.stats + q, c[q]);
+        }
     }
 }
 

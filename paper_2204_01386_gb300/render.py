@@ -140,13 +140,15 @@ class Renderer:
         parts += [str(x) for x in (p.K, p.r, p.sigma, p.delta, p.edge_mode, p.shade_mode, p.texgrad_mode)]
         return hashlib.sha1("|".join(parts).encode()).hexdigest()[:20]
 
-    def autotune(self, cache_path: Optional[str] = None) -> dict:
-        """Chooses tile edge, schedule and tile-list capacity by timing (dressi_autotune),
-        remembering the choice per workload in a JSON file (``cache_path``, else
-        $DRESSI_AUTOTUNE_CACHE, else ~/.cache/dressi/autotune.json)."""
+    def autotune(self, cache_path: Optional[str] = None, store_layers: bool = True) -> dict:
+        """Chooses tile edge, schedule and tile-list capacity by timing (dressi_autotune)
+        forward + adjoint passes that keep the layer ids (``store_layers``) or
+        re-rasterize, as the training loop will, remembering the choice per workload in
+        a JSON file (``cache_path``, else $DRESSI_AUTOTUNE_CACHE, else
+        ~/.cache/dressi/autotune.json)."""
         path = cache_path or os.environ.get("DRESSI_AUTOTUNE_CACHE") or os.path.join(
             os.path.expanduser("~"), ".cache", "dressi", "autotune.json")
-        key = self.signature()
+        key = self.signature() + ("s" if store_layers else "r")
         cache = {}
         if os.path.exists(path):
             try:
@@ -172,7 +174,9 @@ class Renderer:
                   if self.scene.tex is not None and self.params.shade_mode != 0 else None)
             q = B.DressiParams.from_buffer_copy(self.params)
             best = C.c_float(0.0)
+            ids = torch.empty(self.K, self.n_pix, dtype=torch.int32, device=dev) if store_layers else None
             code = self.lib.dressi_autotune(C.byref(sc), self.views, self.n_views, C.byref(q), out.data_ptr(),
+                                            ids.data_ptr() if ids is not None else None,
                                             self.n_pix, gp.data_ptr(), gc.data_ptr() if gc is not None else None,
                                             gt.data_ptr() if gt is not None else None, ws.data_ptr(), need,
                                             self.status.data_ptr(), self._stream(), C.byref(best))
