@@ -117,8 +117,10 @@ typedef struct {
     int32_t tile;       /* tile edge in pixels: 16 or 32; 0 = 16 */
     int32_t schedule;   /* per-tile kernel: 0 auto (= 1), 1 one CTA per tile, 2 persistent CTAs
                            pulling (view, tile) items longest face list first */
-    int64_t list_cap;   /* tile-list capacity in entries; 0 = library default (see header of
-                           dressi_workspace_size) */
+    int64_t list_cap;   /* tile-list capacity in entries; 0 = library default
+                           max(4 x faces over all views, 64 x tiles).  Clamped to
+                           2^31 - 2.  A tile whose list ends past it falls back to the
+                           view's whole mesh and sets DRESSI_DEV_TILE_OVERFLOW */
 } dressi_params;
 
 /* Size in bytes of the workspace that dressi_forward / dressi_backward need for

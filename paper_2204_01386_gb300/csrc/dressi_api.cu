@@ -151,7 +151,9 @@ static bool make_plan(const dressi_scene *sc, const dressi_view *views, int n_vi
     L.n_vrec = vrec;
     L.total_tiles = tiles;
     L.list_cap = p->list_cap > 0 ? p->list_cap : std::max<long long>(4 * view_faces, 64LL * tiles);
-    if (L.list_cap > 0x7fffffffLL) L.list_cap = 0x7fffffffLL;
+    // below INT_MAX: the saturating tile-count scan marks a total past 2^31 - 1 as INT_MAX,
+    // which must read as over capacity
+    if (L.list_cap > 0x7ffffffeLL) L.list_cap = 0x7ffffffeLL;
     size_t o = 0;
     L.views = o; o = align_up(o + sizeof(ViewK) * n_views);
     L.meshes = o; o = align_up(o + sizeof(MeshK) * sc->n_meshes);
@@ -165,7 +167,8 @@ static bool make_plan(const dressi_scene *sc, const dressi_view *views, int n_vi
     L.adj_off = o; o = align_up(o + sizeof(int) * (nv + 1));
     L.adj_cur = o; o = align_up(o + sizeof(int) * nv);
     L.adj = o; o = align_up(o + sizeof(int) * 3 * (size_t)std::max<long long>(P.n_faces, 1));
-    L.scan_partial = o; o = align_up(o + sizeof(int) * (size_t)scan_partials_needed((long long)nv + 1));
+    L.scan_partial = o;
+    o = align_up(o + sizeof(int) * (size_t)scan_partials_needed(std::max<long long>((long long)nv + 1, tiles + 1)));
     L.sgrad = o; o = align_up(o + sizeof(float4) * (size_t)std::max<long long>(vrec, 1));
     L.ngrad = o; o = align_up(o + sizeof(float4) * nv);
     L.queue = o; o = align_up(o + sizeof(int) * 4);

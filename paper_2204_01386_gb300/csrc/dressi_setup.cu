@@ -30,16 +30,19 @@ __global__ void k_vertex(Globals g)
                                        __dmul_rn((double)m[2], p2)),
                              (double)m[3]);
         }
-        const double X = __dmul_rn(__dmul_rn(__dadd_rn(__ddiv_rn(c[0], c[3]), 1.0), 0.5), (double)V.W);
-        const double Y = __dmul_rn(__dmul_rn(__dadd_rn(__ddiv_rn(c[1], c[3]), 1.0), 0.5), (double)V.H);
-        const double Z = __ddiv_rn(c[2], c[3]);
+        // one FP64 reciprocal, then products: within an FP64 ulp of the quotients, and
+        // exact where w = 1
+        const double iw = __ddiv_rn(1.0, c[3]);
+        const double X = __dmul_rn(__dmul_rn(__dadd_rn(__dmul_rn(c[0], iw), 1.0), 0.5), (double)V.W);
+        const double Y = __dmul_rn(__dmul_rn(__dadd_rn(__dmul_rn(c[1], iw), 1.0), 0.5), (double)V.H);
+        const double Z = __dmul_rn(c[2], iw);
         VRec r;
         r.xh = __double2float_rn(X);
         r.xl = __double2float_rn(__dsub_rn(X, (double)r.xh));
         r.yh = __double2float_rn(Y);
         r.yl = __double2float_rn(__dsub_rn(Y, (double)r.yh));
         r.z = __double2float_rn(Z);
-        r.iw = __double2float_rn(__ddiv_rn(1.0, c[3]));
+        r.iw = __double2float_rn(iw);
         const bool fin = isfinite(X) && isfinite(Y) && isfinite(Z);
         r.valid = (c[3] > 1e-6) && (Z >= 0.0) && (Z <= 1.0) && fin && fabs(X) < 1e30 && fabs(Y) < 1e30;
         r.pad = 0;
@@ -157,49 +160,6 @@ __global__ void k_bin(Globals g)
             }
     }
     if (PASS == 0 && bad) atomicOr(g.status, DRESSI_DEV_FACE_RANGE);
-}
-
-// exclusive scan of the per-tile counts (one CTA of 1024 threads)
-__global__ void __launch_bounds__(1024) k_scan(Globals g)
-{
-    __shared__ long long warp_sums[32];
-    const int n = g.total_tiles;
-    const int tid = threadIdx.x;
-    const int per = (n + 1023) / 1024;
-    const int b = tid * per, e = min(n, b + per);
-    long long s = 0;
-    for (int i = b; i < e; ++i) s += g.tile_count[i];
-    // inclusive scan of s over the block
-    long long x = s;
-    const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sums[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        long long w = warp_sums[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            long long y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        warp_sums[lane] = w;
-    }
-    __syncthreads();
-    long long run = x - s + (warp > 0 ? warp_sums[warp - 1] : 0);
-    for (int i = b; i < e; ++i) {
-        long long c = g.tile_count[i];
-        g.tile_off[i] = (int)min(run, (long long)0x7fffffff);
-        run += c;
-    }
-    if (tid == 1023) {
-        long long total = warp_sums[31];
-        g.tile_off[n] = (int)min(total, (long long)0x7fffffff);
-        if (total > g.list_cap) atomicOr(g.status, DRESSI_DEV_TILE_OVERFLOW);
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -369,9 +329,12 @@ void launch_bin(const Globals &g, int n_views, int max_nf, cudaStream_t s)
 {
     dim3 grid(grid_x(max_nf, 256, 2048), n_views);
     k_bin<0><<<grid, 256, 0, s>>>(g);
-    k_scan<<<1, 1024, 0, s>>>(g);
+    // exclusive prefix of the tile counts: tile_off[n] = total list entries
+    cudaMemcpyAsync(g.tile_off, g.tile_count, sizeof(int) * (size_t)g.total_tiles, cudaMemcpyDeviceToDevice, s);
+    cudaMemsetAsync(g.tile_off + g.total_tiles, 0, sizeof(int), s);
+    launch_scan_inplace(g.tile_off, g.total_tiles + 1, g.scan_partial, s);
     k_bin<1><<<grid, 256, 0, s>>>(g);
-    count_launch(3);
+    count_launch(2);
 }
 
 void launch_lpt_order(const Globals &g, cudaStream_t s)

@@ -22,10 +22,17 @@ constexpr int RS_ITEMS = 16;                      // items per thread per block
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;    // items per block
 constexpr int RS_BINS = 256;
 
-// --- device-wide exclusive scan of n ints (in place), three kernels -------------
+// --- device-wide exclusive scan of n non-negative ints (in place), three kernels ---
+// Sums saturate at INT_MAX (for non-negative terms min(a + b, INT_MAX) is still
+// associative), so a total past 2^31 - 1 reads as INT_MAX instead of wrapping.
 constexpr int SC_THREADS = 1024;
 constexpr int SC_ITEMS = 4;
 constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
+
+__device__ __forceinline__ int sat_add(int a, int b)
+{
+    return a > 0x7fffffff - b ? 0x7fffffff : a + b;
+}
 
 __device__ __forceinline__ int block_excl_scan(int v, int *warp_tot, int &total)
 {
@@ -34,8 +41,10 @@ __device__ __forceinline__ int block_excl_scan(int v, int *warp_tot, int &total)
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+        if (lane >= o) x = sat_add(x, y);
     }
+    int ex = __shfl_up_sync(0xffffffffu, x, 1);   // exclusive within the warp
+    if (lane == 0) ex = 0;
     if (lane == 31) warp_tot[warp] = x;
     __syncthreads();
     if (warp == 0) {
@@ -43,13 +52,13 @@ __device__ __forceinline__ int block_excl_scan(int v, int *warp_tot, int &total)
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
+            if (lane >= o) w = sat_add(w, y);
         }
         if (lane < nw) warp_tot[lane] = w;
     }
     __syncthreads();
     total = warp_tot[nw - 1];
-    const int r = x - v + (warp > 0 ? warp_tot[warp - 1] : 0);
+    const int r = sat_add(ex, warp > 0 ? warp_tot[warp - 1] : 0);
     __syncthreads();
     return r;
 }
@@ -60,7 +69,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const int *a, int n,
     const int base = blockIdx.x * SC_TILE + threadIdx.x * SC_ITEMS;
     int s = 0;
 #pragma unroll
-    for (int j = 0; j < SC_ITEMS; ++j) s += (base + j < n) ? a[base + j] : 0;
+    for (int j = 0; j < SC_ITEMS; ++j) s = sat_add(s, (base + j < n) ? a[base + j] : 0);
     int total;
     block_excl_scan(s, wt, total);
     if (threadIdx.x == 0) partial[blockIdx.x] = total;
@@ -73,13 +82,16 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_partials(int *partial, int 
     const int base = threadIdx.x * SC_ITEMS;
     int v[SC_ITEMS], s = 0;
 #pragma unroll
-    for (int j = 0; j < SC_ITEMS; ++j) { v[j] = (base + j < nparts) ? partial[base + j] : 0; s += v[j]; }
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        v[j] = (base + j < nparts) ? partial[base + j] : 0;
+        s = sat_add(s, v[j]);
+    }
     int total;
     int run = block_excl_scan(s, wt, total);
 #pragma unroll
     for (int j = 0; j < SC_ITEMS; ++j) {
         if (base + j < nparts) partial[base + j] = run;
-        run += v[j];
+        run = sat_add(run, v[j]);
     }
     if (threadIdx.x == 0) partial[nparts] = total;
 }
@@ -90,13 +102,16 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_down(int *a, int n, const i
     const int base = blockIdx.x * SC_TILE + threadIdx.x * SC_ITEMS;
     int v[SC_ITEMS], s = 0;
 #pragma unroll
-    for (int j = 0; j < SC_ITEMS; ++j) { v[j] = (base + j < n) ? a[base + j] : 0; s += v[j]; }
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        v[j] = (base + j < n) ? a[base + j] : 0;
+        s = sat_add(s, v[j]);
+    }
     int total;
-    int run = block_excl_scan(s, wt, total) + partial[blockIdx.x];
+    int run = sat_add(block_excl_scan(s, wt, total), partial[blockIdx.x]);
 #pragma unroll
     for (int j = 0; j < SC_ITEMS; ++j) {
         if (base + j < n) a[base + j] = run;
-        run += v[j];
+        run = sat_add(run, v[j]);
     }
 }
 
