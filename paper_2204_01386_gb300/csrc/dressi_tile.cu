@@ -34,6 +34,8 @@ constexpr float APPROX_EPS = 1e-3f;    // pixel slack of the tile-local (approxi
 constexpr int CH = 256;                // faces staged per round (one per thread)
 constexpr int HASH = 2 * CH;           // face id -> staged slot, open addressing
 constexpr unsigned long long EMPTY = ~0ULL;
+constexpr int QN = 4 * NT;             // queued candidate pairs per batch
+constexpr int NBLK = 2048;             // pair blocks of 32 with a table entry (65,536 pairs)
 
 // conservative tile-local data of a staged face: edge equations and bbox in pixels
 // relative to the tile origin (FP32, a few 1e-6 px of error), and the smallest depth
@@ -513,6 +515,8 @@ struct Smem {
     int2 hash[HASH];     // (face id, slot) of the last staged chunk
     int wsum[2][NT / 32];
     int view, totals[2], next;
+    int qn[2];           // queue fill of the current batch, by batch parity
+    unsigned long long m0[HS_MAX], m1[HS_MAX];   // per halo row: columns with S^H = 0 / 1
     unsigned char sh[HS_MAX * HS_MAX];
 };
 
@@ -556,13 +560,22 @@ __device__ __forceinline__ int search_start(const int *start, int n, int i)
     return lo;
 }
 
-// face of pair i = base + lane: one warp-uniform search for the warp's first pair,
-// then a short walk (a face holds tens of pairs, so a warp spans one or two faces)
-__device__ __forceinline__ int pair_face(const int *start, int n, int base, int i)
+// face of pair i = base + lane (base a multiple of 32): the face holding the block's
+// first pair from the block table (a search past the table), then a short walk (a face
+// holds tens of pairs, so a warp spans one or two faces)
+__device__ __forceinline__ int pair_face(const int *start, const unsigned char *blk, int n, int base, int i)
 {
-    int f = search_start(start, n, base);
+    int f = (base >> 5) < NBLK ? (int)blk[base >> 5] : search_start(start, n, base);
     while (f + 1 < n && start[f + 1] <= i) ++f;
     return f;
+}
+
+// block table of a pair prefix: blk[b] = the face holding pair 32 b
+__device__ __forceinline__ void fill_blocks(unsigned char *blk, int f, int start, int cnt)
+{
+    if (cnt <= 0) return;
+    const int be = min((start + cnt - 1) >> 5, NBLK - 1);
+    for (int b = (start + 31) >> 5; b <= be; ++b) blk[b] = (unsigned char)f;
 }
 
 // (x, y) of pair q in a rect of width w: q / w by a float reciprocal (exact for q < 2^16)
@@ -593,14 +606,10 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
     // edge mask (Sec. 3.3.3): the window of radius rho sees both S^H = 0 and 1
     bool E = g.edge_mode == 1;
     if (g.edge_mode == 0) {
-        bool s0 = false, s1 = false;
-        for (int wy = 0; wy <= 2 * rho; ++wy)
-            for (int wx = 0; wx <= 2 * rho; ++wx) {
-                const unsigned char v = S.sh[(ly + wy) * hs + (lx + wx)];
-                s0 |= v == 0;
-                s1 |= v == 1;
-            }
-        E = s0 && s1;
+        unsigned long long a0 = 0ull, a1 = 0ull;
+        for (int wy = 0; wy <= 2 * rho; ++wy) { a0 |= S.m0[ly + wy]; a1 |= S.m1[ly + wy]; }
+        const unsigned long long wm = (2ull << (2 * rho)) - 1ull;   // columns lx .. lx + 2 rho
+        E = ((a0 >> lx) & wm) && ((a1 >> lx) & wm);
     }
 
     unsigned layers = 0;
@@ -720,7 +729,15 @@ template <int K, bool BWD, int TT>
 __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned long long *kbuf, const int t)
 {
     constexpr int PPT = TT * TT / NT;   // pixels per thread in the per-pixel phases
-    if (threadIdx.x == 0) S.view = view_of_tile(g, t);
+    // after the K-lists: the candidate queue and the two pair-block tables
+    unsigned *qbuf = reinterpret_cast<unsigned *>(kbuf + TT * TT * K);
+    unsigned char *blk = reinterpret_cast<unsigned char *>(qbuf + QN);
+    unsigned char *hblk = blk + NBLK;
+    if (threadIdx.x == 0) {
+        S.view = view_of_tile(g, t);
+        S.qn[0] = 0;
+        S.qn[1] = 0;
+    }
     __syncthreads();
     const ViewK &V = g.views[S.view];
     const MeshK &M = g.meshes[V.mesh];
@@ -741,6 +758,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
     const bool from_ids = BWD && g.ids_in != nullptr;
     bool single_chunk = false;
     unsigned n_pairs = 0, n_exact = 0, n_cand = 0, n_layers = 0;
+    int batch = 0;   // candidate-queue batches so far (selects the queue counter)
     if (!from_ids) {
         const long long lb = g.tile_off[t], le = g.tile_off[t + 1];
         const bool fallback = le > g.list_cap;
@@ -812,36 +830,76 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                     if (w < wp) { oa += va; ob += vb; }
                     ta += va; tb += vb;
                 }
-                if (tid < CH) { S.start[tid] = oa + a - cnt; S.hstart[tid] = ob + b - hcnt; }
+                if (tid < CH) {
+                    S.start[tid] = oa + a - cnt;
+                    S.hstart[tid] = ob + b - hcnt;
+                    fill_blocks(blk, tid, oa + a - cnt, cnt);
+                    fill_blocks(hblk, tid, ob + b - hcnt, hcnt);
+                }
                 if (tid == 0) { S.totals[0] = ta; S.totals[1] = tb; }
             }
             __syncthreads();
             const int total = S.totals[0], htotal = S.totals[1];
-            // (face, pixel) pairs of the tile
+            // (face, pixel) pairs of the tile, in batches of QN: (1) every pair takes the
+            // approximate test and the survivors are queued, (2) the queue takes the exact
+            // evaluation with full warps.  A queue entry is x | y << 5 | face << 10 with the
+            // top 14 bits of the key lower bound above (truncated: still a lower bound).
             if (g.stats) n_pairs += (total > tid) ? (total - tid + NT - 1) / NT : 0;
-            for (int i = tid; i < total; i += NT) {
-                const int f = pair_face(S.start, nch, i - (tid & 31), i);
-                const int rc = S.rect[f];
-                int x, y;
-                rect_xy(i - S.start[f], (rc >> 16) & 0xff, x, y);
-                x += rc & 0xff;
-                y += (rc >> 8) & 0xff;
-                const Pre &P = S.P[f];
-                unsigned long long *slots = kbuf + (y * TT + x) * K;
-                float klb;
-                if (!approx_candidate(P, (float)x + 0.5f, (float)y + 0.5f, V.r_px, V.half_inv_S, klb)) continue;
-                const unsigned long long last = *reinterpret_cast<volatile unsigned long long *>(slots + K - 1);
-                if (klb > __uint_as_float((unsigned int)(last >> 32))) continue;
-                Frag fr;
-                ++n_exact;
-                if (eval_face(S.F[f], (float)(X0 + x) + 0.5f, (float)(Y0 + y) + 0.5f, V.r_px, V.half_inv_S, fr)) {
-                    ++n_cand;
-                    kbuf_insert<K>(slots, pack_frag(fr.key, S.F[f].id));
+            const int lane = tid & 31;
+            for (int b0 = 0; b0 < total; b0 += QN) {
+                int *qn = &S.qn[batch & 1];
+                const int rounds = min(QN / NT, (total - b0 + NT - 1) / NT);
+                for (int r = 0; r < rounds; ++r) {
+                    const int i = b0 + r * NT + tid;
+                    bool pass = false;
+                    unsigned ent = 0u;
+                    if (i < total) {
+                        const int f = pair_face(S.start, blk, nch, i - lane, i);
+                        const int rc = S.rect[f];
+                        int x, y;
+                        rect_xy(i - S.start[f], (rc >> 16) & 0xff, x, y);
+                        x += rc & 0xff;
+                        y += (rc >> 8) & 0xff;
+                        float klb;
+                        if (approx_candidate(S.P[f], (float)x + 0.5f, (float)y + 0.5f, V.r_px, V.half_inv_S, klb)) {
+                            const unsigned long long last = kbuf[(y * TT + x) * K + K - 1];
+                            if (!(klb > __uint_as_float((unsigned int)(last >> 32)))) {
+                                pass = true;
+                                ent = (__float_as_uint(klb) & 0xfffc0000u) | ((unsigned)f << 10) |
+                                      ((unsigned)y << 5) | (unsigned)x;
+                            }
+                        }
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, pass);
+                    if (m) {
+                        int qb = 0;
+                        if (lane == 0) qb = atomicAdd(qn, __popc(m));
+                        qb = __shfl_sync(0xffffffffu, qb, 0);
+                        if (pass) qbuf[qb + __popc(m & ((1u << lane) - 1u))] = ent;
+                    }
                 }
+                __syncthreads();   // queue complete
+                const int nq = *qn;
+                if (tid == 0) S.qn[(batch & 1) ^ 1] = 0;   // the next batch's counter
+                for (int j = tid; j < nq; j += NT) {
+                    const unsigned ent = qbuf[j];
+                    const int x = ent & 31, y = (ent >> 5) & 31, f = (ent >> 10) & 0xff;
+                    unsigned long long *slots = kbuf + (y * TT + x) * K;
+                    const unsigned long long last = *reinterpret_cast<volatile unsigned long long *>(slots + K - 1);
+                    if (__uint_as_float(ent & 0xfffc0000u) > __uint_as_float((unsigned int)(last >> 32))) continue;
+                    Frag fr;
+                    ++n_exact;
+                    if (eval_face(S.F[f], (float)(X0 + x) + 0.5f, (float)(Y0 + y) + 0.5f, V.r_px, V.half_inv_S, fr)) {
+                        ++n_cand;
+                        kbuf_insert<K>(slots, pack_frag(fr.key, S.F[f].id));
+                    }
+                }
+                __syncthreads();   // queue consumed
+                ++batch;
             }
             // (face, pixel) pairs of the ring: hard test only
             for (int i = tid; i < htotal; i += NT) {
-                const int f = pair_face(S.hstart, nch, i - (tid & 31), i);
+                const int f = pair_face(S.hstart, hblk, nch, i - (tid & 31), i);
                 const int rc = S.hrect[f];
                 int x, y;
                 rect_xy(i - S.hstart[f], (rc >> 16) & 0xff, x, y);
@@ -904,6 +962,22 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
         }
     }
     __syncthreads();
+    if (g.edge_mode == 0) {
+        // per halo row, the columns holding S^H = 0 and S^H = 1 (hs <= 48 fits 64 bits)
+        const int lane = tid & 31;
+        for (int row = tid >> 5; row < hs; row += NT / 32) {
+            unsigned long long b0 = 0ull, b1 = 0ull;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int col = half * 32 + lane;
+                const unsigned char v = col < hs ? S.sh[row * hs + col] : (unsigned char)2;
+                b0 |= (unsigned long long)__ballot_sync(0xffffffffu, v == 0) << (32 * half);
+                b1 |= (unsigned long long)__ballot_sync(0xffffffffu, v == 1) << (32 * half);
+            }
+            if (lane == 0) { S.m0[row] = b0; S.m1[row] = b1; }
+        }
+        __syncthreads();
+    }
 
     for (int j = 0; j < PPT; ++j) {
         const int p = tid + j * NT;
@@ -970,7 +1044,8 @@ __global__ void __launch_bounds__(NT, BWD ? 2 : 3) k_tile_persistent(Globals g)
 template <int K, int TT>
 static size_t tile_smem_bytes()
 {
-    return sizeof(Smem) + sizeof(unsigned long long) * TT * TT * K;
+    // Smem, the K-lists, the candidate queue, the two pair-block tables
+    return sizeof(Smem) + sizeof(unsigned long long) * TT * TT * K + sizeof(unsigned) * QN + 2 * NBLK;
 }
 
 template <int K, bool BWD, int TT>
