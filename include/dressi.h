@@ -132,8 +132,10 @@ DRESSI_API size_t dressi_workspace_size(const dressi_scene *scene, const dressi_
 /* Forward pass (Alg. 2 and the blend equations of Sec. 3.3.3).
      out_rgba   DEVICE [n_pix][4] float: colour I_c in rgb, silhouette I_s in alpha,
                 at the views' pixel offsets.  Pixels of no view are left untouched.
-     layer_ids  DEVICE [K][n_pix] int32 or NULL: face index (local to the view's mesh) of
-                each peel layer, -1 where a layer is empty.  Pass it to dressi_backward
+     layer_ids  DEVICE [K][n_pix] int32 or NULL: per peel layer, the face index (local to
+                the view's mesh), with bit 31 set when the fragment is soft (the pixel lies
+                outside the hard face, within r of it), and -1 where a layer is empty.
+                Decode: face = v & 0x7fffffff, hard = v >= 0.  Pass it to dressi_backward
                 to skip re-rasterization; NULL keeps nothing between the passes.
      n_pix      total pixels of the packed image buffers (>= every pix_off + W*H).
      ws         DEVICE workspace of ws_bytes >= dressi_workspace_size(...).

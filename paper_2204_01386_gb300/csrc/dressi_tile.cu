@@ -586,12 +586,25 @@ __device__ __forceinline__ void rect_xy(int q, int w, int &x, int &y)
     y = qy;
 }
 
+// hard or soft, from the key a fragment was kept with: hard keys are 0.5 z <= 1/2 and
+// soft keys 0.5 + 0.5 |d| / S >= 1/2, so only a key of exactly 1/2 needs the face again
+__device__ __forceinline__ bool kept_hard(const Globals &g, const ViewK &V, const MeshK &M, const VRec *vr,
+                                          unsigned long long v, float px, float py)
+{
+    const float key = __uint_as_float((unsigned int)(v >> 32));
+    if (key != 0.5f) return key < 0.5f;
+    FaceRec R;
+    Frag fr;
+    return face_load(g, M, vr, (int)(unsigned int)(v & 0xffffffffu), R) &&
+           eval_face(R, px, py, V.r_px, V.half_inv_S, fr) && fr.hard;
+}
+
 // S^H, edge mask, shading and blend (forward) or the adjoint (BWD) of one pixel
 // whose K layer ids are known; S.sh holds the tile's S^H with its ring.
 template <int K, bool BWD, int TT>
 __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S, const ViewK &V, const MeshK &M,
                                              const VRec *vr, int X0, int Y0, int lx, int ly, int rho,
-                                             const int (&ids)[K], bool single_chunk)
+                                             const int (&ids)[K], unsigned hardbits, bool single_chunk)
 {
     const int X = X0 + lx, Y = Y0 + ly;
     const int lx_g = X, ly_g = Y;   // view-local pixel coordinates
@@ -616,7 +629,11 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
     if (!BWD) {
         if (g.ids) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) g.ids[(long long)k * g.n_pix + pix] = (k < nl) ? ids[k] : -1;
+            for (int k = 0; k < K; ++k) {
+                // stored layer: the face index, with bit 31 set for a soft fragment
+                const unsigned soft = ((hardbits >> k) & 1u) ? 0u : 0x80000000u;
+                g.ids[(long long)k * g.n_pix + pix] = (k < nl) ? (int)((unsigned)ids[k] | soft) : -1;
+            }
         }
         float Cs[3] = {0.f, 0.f, 0.f}, C1[3] = {0.f, 0.f, 0.f};
         float Ds = 0.f, prod = 1.f;
@@ -919,46 +936,23 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
             }
         }
         __syncthreads();
-        // S^H of the tile's own pixels from the front slot: hard keys are <= 1/2 and
-        // soft keys >= 1/2, so only a key of exactly 1/2 needs the face again
+        // S^H of the tile's own pixels from the front slot
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
             const int p = tid + j * NT;
             const int lx = p % TT, ly = p / TT;
             if (lx >= wlim || ly >= hlim) continue;
             const unsigned long long v = kbuf[p * K];
-            bool sh = false;
-            if (v != EMPTY) {
-                const float key = __uint_as_float((unsigned int)(v >> 32));
-                sh = key < 0.5f;
-                if (key == 0.5f) {
-                    FaceRec R;
-                    Frag fr;
-                    sh = face_load(g, M, vr, (int)(unsigned int)(v & 0xffffffffu), R) &&
-                         eval_face(R, (float)(X0 + lx) + 0.5f, (float)(Y0 + ly) + 0.5f, V.r_px, V.half_inv_S, fr) &&
-                         fr.hard;
-                }
-            }
+            const bool sh = v != EMPTY && kept_hard(g, V, M, vr, v, (float)(X0 + lx) + 0.5f, (float)(Y0 + ly) + 0.5f);
             S.sh[(ly + rho) * hs + (lx + rho)] = sh ? 1 : 0;
         }
     } else {
-        // layers stored by the forward: S^H of the tile and of its ring from the stored
-        // front layer of every pixel
-        const int ring = rho > 0 ? hs * hs - TT * TT : 0;
-        for (int h = tid; h < TT * TT + ring; h += NT) {
-            int hx, hy;
-            if (h < TT * TT) { hx = h % TT; hy = h / TT; }
-            else halo_pos<TT>(h - TT * TT, rho, hx, hy);
-            const int si = (hy + rho) * hs + (hx + rho);
-            if (S.sh[si] == 2) continue;
-            const long long hp = V.pix_off + (long long)(Y0 + hy) * V.W + (X0 + hx);
-            const int id = __ldg(g.ids_in + hp);
-            bool sh = false;
-            if (id >= 0) {
-                FaceRec R;
-                sh = face_load(g, M, vr, id, R) && hard_test(R, (float)(X0 + hx) + 0.5f, (float)(Y0 + hy) + 0.5f);
-            }
-            S.sh[si] = sh ? 1 : 0;
+        // layers stored by the forward: S^H of the tile and of its ring is the hard flag
+        // of every pixel's stored front layer (a non-negative id: hard; bit 31: soft)
+        for (int i = tid; i < hs * hs; i += NT) {
+            if (S.sh[i] == 2) continue;
+            const long long hp = V.pix_off + (long long)(Y0 - rho + i / hs) * V.W + (X0 - rho + i % hs);
+            S.sh[i] = __ldg(g.ids_in + hp) >= 0 ? 1 : 0;
         }
     }
     __syncthreads();
@@ -984,21 +978,32 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
         const int lx = p % TT, ly = p / TT;
         if (lx >= wlim || ly >= hlim) continue;
         int ids[K];
+        unsigned hardbits = 0u;
         if (!from_ids) {
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const unsigned long long v = kbuf[p * K + k];
                 ids[k] = (v == EMPTY) ? 0x7fffffff : (int)(unsigned int)(v & 0xffffffffu);
             }
+            if (!BWD && g.ids) {
+                // hard flags of the stored layers; the front one is S^H itself
+                hardbits = S.sh[(ly + rho) * hs + (lx + rho)] == 1 ? 1u : 0u;
+#pragma unroll
+                for (int k = 1; k < K; ++k) {
+                    const unsigned long long v = kbuf[p * K + k];
+                    if (v != EMPTY && kept_hard(g, V, M, vr, v, (float)(X0 + lx) + 0.5f, (float)(Y0 + ly) + 0.5f))
+                        hardbits |= 1u << k;
+                }
+            }
         } else {
             const long long pix = V.pix_off + (long long)(Y0 + ly) * V.W + (X0 + lx);
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const int id = __ldg(g.ids_in + (long long)k * g.n_pix + pix);
-                ids[k] = id >= 0 ? id : 0x7fffffff;
+                ids[k] = id == -1 ? 0x7fffffff : (id & 0x7fffffff);
             }
         }
-        n_layers += finish_pixel<K, BWD, TT>(g, S, V, M, vr, X0, Y0, lx, ly, rho, ids, single_chunk);
+        n_layers += finish_pixel<K, BWD, TT>(g, S, V, M, vr, X0, Y0, lx, ly, rho, ids, hardbits, single_chunk);
     }
     if (g.stats) {
         // work counters: pairs enumerated, exact evaluations, candidates kept, layers shaded

@@ -251,6 +251,21 @@ class Renderer:
         return img[v.pix_off: v.pix_off + v.width * v.height].view(v.height, v.width, -1)
 
 
+def decode_layer_ids(ids):
+    """Split stored layer ids into (face index, hard flag): -1 / False where a layer
+    is empty; a soft fragment is stored with bit 31 set.  Works on torch tensors and
+    numpy arrays of int32."""
+    if isinstance(ids, torch.Tensor):
+        empty = ids == -1
+        face = torch.where(empty, torch.full_like(ids, -1), ids & 0x7FFFFFFF)
+        return face, ids >= 0
+    import numpy as np
+    ids = np.asarray(ids, dtype=np.int32)
+    empty = ids == -1
+    face = np.where(empty, np.int32(-1), ids & np.int32(0x7FFFFFFF))
+    return face, ids >= 0
+
+
 class DressiFn(torch.autograd.Function):
     """out = HardSoftRas(pos, col, tex) for a fixed renderer (faces, UVs, views, params).
 

@@ -16,7 +16,7 @@ import torch
 from scipy import ndimage
 
 import oracle
-from paper_2204_01386_gb300 import PackedScene, Renderer
+from paper_2204_01386_gb300 import PackedScene, Renderer, decode_layer_ids
 
 TAU_PX = 1e-4
 TAU_KEY = 1e-6
@@ -64,9 +64,17 @@ class GpuRun:
     def view_rgba(self, i):
         return self.r.view_image(self.out, i).cpu().numpy().astype(np.float64)
 
-    def view_ids(self, i):
+    def view_raw_ids(self, i):
         v = self.r.views[i]
         return self.ids[:, v.pix_off: v.pix_off + v.width * v.height].view(-1, v.height, v.width).cpu().numpy()
+
+    def view_ids(self, i):
+        """Face index of each layer, -1 where empty."""
+        return decode_layer_ids(self.view_raw_ids(i))[0]
+
+    def view_hard(self, i):
+        """Hard flag of each layer (False where empty)."""
+        return decode_layer_ids(self.view_raw_ids(i))[1]
 
     def backward(self, grads_per_view, use_ids=True):
         g = torch.zeros(self.r.n_pix, 4, dtype=torch.float32, device=self.ps.device)
@@ -119,7 +127,10 @@ def compare_scene(scene, windows=None, seed=0, grad_from_target=None, store_laye
         o = oracle.render(scene.meshes[v.mesh], v, scene.params, window=win)
         s_ids, s_val = masks(o, scene.params, v)
         gi = gpu.view_ids(i)[:, y0:y0 + h, x0:x0 + w]
-        gi = np.where(gi < 0, -1, gi)
+        gh = gpu.view_hard(i)[:, y0:y0 + h, x0:x0 + w]
+        # the stored ids carry each layer's hard / soft flag as well
+        bad_hard = ((gh != (o["hard"] != 0)) & (o["ids"] >= 0)).any(0) & s_ids
+        assert not bad_hard.any(), f"view {i}: {bad_hard.sum()} stable pixels with different hard flags"
         bad = (gi != o["ids"]).any(0) & s_ids
         stats["ids_checked"] += int(s_ids.sum())
         stats["ids_unstable"] += int((~s_ids).sum())

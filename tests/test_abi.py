@@ -153,3 +153,16 @@ def test_product_does_not_import_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "hardsoftras_oracle" not in txt, f
+
+
+def test_decode_layer_ids():
+    """Stored layer ids: face index, bit 31 set for a soft fragment, -1 for an empty layer."""
+    import numpy as np
+    import torch
+    from paper_2204_01386_gb300 import decode_layer_ids
+    raw = np.array([5, 5 | -0x80000000, -1, 0, -0x80000000, 0x7FFFFFFE, 0x7FFFFFFE | -0x80000000], np.int64).astype(np.int32)
+    face, hard = decode_layer_ids(raw)
+    assert face.tolist() == [5, 5, -1, 0, 0, 0x7FFFFFFE, 0x7FFFFFFE]
+    assert hard.tolist() == [True, False, False, True, False, True, False]
+    tf, th = decode_layer_ids(torch.as_tensor(raw))
+    assert tf.tolist() == face.tolist() and th.tolist() == hard.tolist()
