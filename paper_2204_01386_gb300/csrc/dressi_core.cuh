@@ -46,6 +46,7 @@ struct ViewK {
     long long pix_off;
     long long vrec_off;     // first record of this view in the per-view vertex buffer
     long long slot_base;    // first pixel of this view in the texel-gather record slots
+    long long frec_off;     // first record of this view in the per-view face table
 };
 
 struct MeshK {
@@ -62,7 +63,8 @@ struct __align__(16) VRec {
 };
 
 // per-face record used by every pixel evaluation
-struct FaceRec {
+// 32 words (128 bytes, one cache line): word 22 holds the flags
+struct __align__(16) FaceRec {
     float xh[3], xl[3], yh[3], yl[3];
     float L[3];      // length of edge i (canonical)
     float invL[3];   // 1 / L
@@ -73,7 +75,9 @@ struct FaceRec {
     int id;          // face index local to the mesh
     int vi[3];       // vertex indices local to the mesh
     float iw[3];     // 1 / w of the corners
+    int pad[2];
 };
+static_assert(sizeof(FaceRec) == 128, "FaceRec is one 128-byte line");
 
 struct Globals {
     const ViewK *views;
@@ -94,6 +98,7 @@ struct Globals {
     const int *faces;
     const void *tex;
     VRec *vrec;
+    FaceRec *frec;        // per (view, face): the face's record, written by the setup
     int *tile_count, *tile_off, *tile_cursor, *lists;
     float4 *nrm;          // [n_verts_total] normalized vertex normals, w = |sum|
     int *adj_off;         // [n_verts_total + 1] vertex -> incident faces (CSR offsets)
@@ -203,6 +208,54 @@ __device__ __forceinline__ bool face_load(const Globals &g, const MeshK &m, cons
     if (live) flags |= FLAG_LIVE;
     R.flags = flags;
     return live;
+}
+
+// the (view, face) record of the face table (face_load's result, written once per call
+// by the setup); false for a face out of range or culled, as face_load
+__device__ __forceinline__ bool face_get(const Globals &g, const ViewK &V, const MeshK &m, int f, FaceRec &R)
+{
+    if ((unsigned)f >= (unsigned)m.nF) {
+        R.id = f;
+        R.flags = FLAG_RANGE;
+        return false;
+    }
+    const float4 *src = reinterpret_cast<const float4 *>(g.frec + V.frec_off + f);
+    float w[32];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float4 q = __ldg(src + i);
+        w[4 * i] = q.x; w[4 * i + 1] = q.y; w[4 * i + 2] = q.z; w[4 * i + 3] = q.w;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        R.xh[i] = w[i]; R.xl[i] = w[3 + i]; R.yh[i] = w[6 + i]; R.yl[i] = w[9 + i];
+        R.L[i] = w[12 + i]; R.invL[i] = w[15 + i]; R.z[i] = w[18 + i];
+        R.vi[i] = __float_as_int(w[24 + i]); R.iw[i] = w[27 + i];
+    }
+    R.invA = w[21];
+    R.flags = __float_as_int(w[22]);
+    R.id = __float_as_int(w[23]);
+    return (R.flags & FLAG_LIVE) != 0;
+}
+
+// face_get into shared memory: eight 16-byte copies
+__device__ __forceinline__ bool face_stage(const Globals &g, const ViewK &V, const MeshK &m, int f, FaceRec &dst)
+{
+    if ((unsigned)f >= (unsigned)m.nF) {
+        dst.id = f;
+        dst.flags = FLAG_RANGE;
+        return false;
+    }
+    const float4 *src = reinterpret_cast<const float4 *>(g.frec + V.frec_off + f);
+    float4 *d = reinterpret_cast<float4 *>(&dst);
+    int flags = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float4 q = __ldg(src + i);
+        d[i] = q;
+        if (i == 5) flags = __float_as_int(q.z);   // word 22
+    }
+    return (flags & FLAG_LIVE) != 0;
 }
 
 // Result of evaluating one face at one pixel centre.

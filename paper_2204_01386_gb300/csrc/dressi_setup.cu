@@ -120,6 +120,36 @@ __global__ void k_normal_csr(Globals g)
 }
 
 // ---------------------------------------------------------------------------
+// face table: the record of every (view, face) -- screen corners, canonical edges,
+// lengths, area, flags -- built once per call and read by binning, staging,
+// shading and the adjoint (one 128-byte line each)
+// ---------------------------------------------------------------------------
+__global__ void k_face(Globals g)
+{
+    const ViewK &V = g.views[blockIdx.y];
+    const MeshK &M = g.meshes[V.mesh];
+    const VRec *vr = g.vrec + V.vrec_off;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < M.nF; f += gridDim.x * blockDim.x) {
+        FaceRec R;
+        face_load(g, M, vr, f, R);
+        if (R.flags & FLAG_RANGE) {
+            // out of range: nothing else of the record is meaningful
+#pragma unroll
+            for (int i = 0; i < 3; ++i) { R.vi[i] = 0; R.xh[i] = R.xl[i] = R.yh[i] = R.yl[i] = 0.f; }
+        }
+        float4 *dst = reinterpret_cast<float4 *>(g.frec + V.frec_off + f);
+        dst[0] = make_float4(R.xh[0], R.xh[1], R.xh[2], R.xl[0]);
+        dst[1] = make_float4(R.xl[1], R.xl[2], R.yh[0], R.yh[1]);
+        dst[2] = make_float4(R.yh[2], R.yl[0], R.yl[1], R.yl[2]);
+        dst[3] = make_float4(R.L[0], R.L[1], R.L[2], R.invL[0]);
+        dst[4] = make_float4(R.invL[1], R.invL[2], R.z[0], R.z[1]);
+        dst[5] = make_float4(R.z[2], R.invA, __int_as_float(R.flags), __int_as_float(R.id));
+        dst[6] = make_float4(__int_as_float(R.vi[0]), __int_as_float(R.vi[1]), __int_as_float(R.vi[2]), R.iw[0]);
+        dst[7] = make_float4(R.iw[1], R.iw[2], 0.f, 0.f);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // tile binning: every live face goes into the list of each tile that its
 // bounding box, grown by bin_R pixels (r plus the edge-mask halo plus a guard),
 // touches.  pass 0 counts, pass 1 fills.  Order inside a list is irrelevant:
@@ -130,13 +160,12 @@ __global__ void k_bin(Globals g)
 {
     const ViewK &V = g.views[blockIdx.y];
     const MeshK &M = g.meshes[V.mesh];
-    const VRec *vr = g.vrec + V.vrec_off;
     const int T = g.tile;
     const float Tinv = 1.f / (float)T;
     bool bad = false;
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < M.nF; f += gridDim.x * blockDim.x) {
         FaceRec R;
-        if (!face_load(g, M, vr, f, R)) {
+        if (!face_get(g, V, M, f, R)) {
             if (R.flags & FLAG_RANGE) bad = true;
             continue;
         }
@@ -323,6 +352,13 @@ void launch_normals(const Globals &g, int n_meshes, int max_nf, int max_nv, cuda
     k_adjacency<1><<<gf, 256, 0, s>>>(g);
     k_normal_csr<<<gv, 256, 0, s>>>(g);
     count_launch(3);
+}
+
+void launch_face(const Globals &g, int n_views, int max_nf, cudaStream_t s)
+{
+    dim3 grid(grid_x(max_nf, 256, 2048), n_views);
+    k_face<<<grid, 256, 0, s>>>(g);
+    count_launch(1);
 }
 
 void launch_bin(const Globals &g, int n_views, int max_nf, cudaStream_t s)

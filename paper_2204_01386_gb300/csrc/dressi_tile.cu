@@ -67,8 +67,9 @@ __device__ __forceinline__ void make_pre(const FaceRec &R, bool live, float tx0,
         const int ib = (i + 1) % 3;
         const float ex = vx[ib] - vx[i], ey = vy[ib] - vy[i];
         float nx = orient ? -ey : ey, ny = orient ? ex : -ex;
-        const float l = sqrtf(nx * nx + ny * ny);
-        const float s = l > 0.f ? 1.f / l : 0.f;
+        // 1 / |edge| of the record (same edge, accurate corners): within a few ulp of
+        // this edge's own length, far inside the pretest's slack
+        const float s = isfinite(R.invL[i]) ? R.invL[i] : 0.f;
         nx *= s; ny *= s;
         P.nx[i] = nx; P.ny[i] = ny;
         P.c[i] = -(nx * vx[i] + ny * vy[i]);
@@ -303,10 +304,10 @@ struct Layer {
     Shade S;
 };
 
-__device__ __forceinline__ bool layer_build(const Globals &g, const ViewK &V, const MeshK &M, const VRec *vr, int id,
+__device__ __forceinline__ bool layer_build(const Globals &g, const ViewK &V, const MeshK &M, int id,
                                             float px, float py, Layer &L)
 {
-    if (!face_load(g, M, vr, id, L.R)) return false;
+    if (!face_get(g, V, M, id, L.R)) return false;
     if (!eval_face(L.R, px, py, V.r_px, V.half_inv_S, L.fr)) return false;
     frag_lambda(L.R, L.fr, L.S.lam);
 #pragma unroll
@@ -588,14 +589,14 @@ __device__ __forceinline__ void rect_xy(int q, int w, int &x, int &y)
 
 // hard or soft, from the key a fragment was kept with: hard keys are 0.5 z <= 1/2 and
 // soft keys 0.5 + 0.5 |d| / S >= 1/2, so only a key of exactly 1/2 needs the face again
-__device__ __forceinline__ bool kept_hard(const Globals &g, const ViewK &V, const MeshK &M, const VRec *vr,
+__device__ __forceinline__ bool kept_hard(const Globals &g, const ViewK &V, const MeshK &M,
                                           unsigned long long v, float px, float py)
 {
     const float key = __uint_as_float((unsigned int)(v >> 32));
     if (key != 0.5f) return key < 0.5f;
     FaceRec R;
     Frag fr;
-    return face_load(g, M, vr, (int)(unsigned int)(v & 0xffffffffu), R) &&
+    return face_get(g, V, M, (int)(unsigned int)(v & 0xffffffffu), R) &&
            eval_face(R, px, py, V.r_px, V.half_inv_S, fr) && fr.hard;
 }
 
@@ -603,7 +604,7 @@ __device__ __forceinline__ bool kept_hard(const Globals &g, const ViewK &V, cons
 // whose K layer ids are known; S.sh holds the tile's S^H with its ring.
 template <int K, bool BWD, int TT>
 __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S, const ViewK &V, const MeshK &M,
-                                             const VRec *vr, int X0, int Y0, int lx, int ly, int rho,
+                                             int X0, int Y0, int lx, int ly, int rho,
                                              const int (&ids)[K], unsigned hardbits, bool single_chunk)
 {
     const int X = X0 + lx, Y = Y0 + ly;
@@ -644,17 +645,21 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
             // re-evaluate the layer at this pixel (from shared memory when the whole tile
             // list was staged at once): distance and barycentrics
             const int slot = single_chunk ? find_slot(S, ids[k]) : -1;
-            FaceRec Rg;
-            const FaceRec *R = nullptr;
-            if (slot >= 0) R = &S.F[slot];
-            else if (face_load(g, M, vr, ids[k], Rg)) R = &Rg;
+            FaceRec R;
+            bool live;
+            if (slot >= 0) {
+                R = S.F[slot];
+                live = (R.flags & FLAG_LIVE) != 0;
+            } else {
+                live = face_get(g, V, M, ids[k], R);
+            }
             Frag fr;
-            if (!R || !eval_face(*R, px, py, V.r_px, V.half_inv_S, fr)) continue;
+            if (!live || !eval_face(R, px, py, V.r_px, V.half_inv_S, fr)) continue;
             Shade Sh;
             ++layers;
-            frag_lambda(*R, fr, Sh.lam);
+            frag_lambda(R, fr, Sh.lam);
 #pragma unroll
-            for (int i = 0; i < 3; ++i) { Sh.vi[i] = R->vi[i]; Sh.iw[i] = R->iw[i]; }
+            for (int i = 0; i < 3; ++i) { Sh.vi[i] = R.vi[i]; Sh.iw[i] = R.iw[i]; }
             shade(g, V, M, fr.dist, Sh);
             Cs[0] = fmaf(Sh.D, Sh.C[0], Cs[0]);
             Cs[1] = fmaf(Sh.D, Sh.C[1], Cs[1]);
@@ -688,7 +693,7 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
 #pragma unroll 1
             for (int k = 0; k < nl; ++k) {
                 Layer L;
-                if (layer_build(g, V, M, vr, ids[k], px, py, L)) {
+                if (layer_build(g, V, M, ids[k], px, py, L)) {
                     Dk[k] = L.S.D;
                     Ck[k][0] = L.S.C[0]; Ck[k][1] = L.S.C[1]; Ck[k][2] = L.S.C[2];
                 }
@@ -732,7 +737,7 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
             const bool any = gDl != 0.f || gCl[0] != 0.f || gCl[1] != 0.f || gCl[2] != 0.f;
             Layer L;
             const long long slot = (V.slot_base + (long long)ly_g * V.W + lx_g) * K + k;
-            if (any && layer_build(g, V, M, vr, ids[k], px, py, L)) {
+            if (any && layer_build(g, V, M, ids[k], px, py, L)) {
                 ++layers;
                 layer_adjoint(g, V, M, L, px, py, gCl, gDl, slot);
             }
@@ -758,7 +763,6 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
     __syncthreads();
     const ViewK &V = g.views[S.view];
     const MeshK &M = g.meshes[V.mesh];
-    const VRec *vr = g.vrec + V.vrec_off;
     const int lt = t - V.tile_base;
     const int X0 = (lt % V.tiles_x) * TT, Y0 = (lt / V.tiles_x) * TT;
     const int tid = threadIdx.x;
@@ -791,7 +795,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
             if (tid < nch) {
                 const int f = fallback ? c0 + tid : g.lists[lb + c0 + tid];
                 FaceRec &R = S.F[tid];
-                const bool live = face_load(g, M, vr, f, R);
+                const bool live = face_stage(g, V, M, f, R);
                 Pre &P = S.P[tid];
                 make_pre(R, live, (float)X0, (float)Y0, V.r_px, P);
                 if (live) {
@@ -943,7 +947,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
             const int lx = p % TT, ly = p / TT;
             if (lx >= wlim || ly >= hlim) continue;
             const unsigned long long v = kbuf[p * K];
-            const bool sh = v != EMPTY && kept_hard(g, V, M, vr, v, (float)(X0 + lx) + 0.5f, (float)(Y0 + ly) + 0.5f);
+            const bool sh = v != EMPTY && kept_hard(g, V, M, v, (float)(X0 + lx) + 0.5f, (float)(Y0 + ly) + 0.5f);
             S.sh[(ly + rho) * hs + (lx + rho)] = sh ? 1 : 0;
         }
     } else {
@@ -991,7 +995,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
 #pragma unroll
                 for (int k = 1; k < K; ++k) {
                     const unsigned long long v = kbuf[p * K + k];
-                    if (v != EMPTY && kept_hard(g, V, M, vr, v, (float)(X0 + lx) + 0.5f, (float)(Y0 + ly) + 0.5f))
+                    if (v != EMPTY && kept_hard(g, V, M, v, (float)(X0 + lx) + 0.5f, (float)(Y0 + ly) + 0.5f))
                         hardbits |= 1u << k;
                 }
             }
@@ -1003,7 +1007,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                 ids[k] = id == -1 ? 0x7fffffff : (id & 0x7fffffff);
             }
         }
-        n_layers += finish_pixel<K, BWD, TT>(g, S, V, M, vr, X0, Y0, lx, ly, rho, ids, hardbits, single_chunk);
+        n_layers += finish_pixel<K, BWD, TT>(g, S, V, M, X0, Y0, lx, ly, rho, ids, hardbits, single_chunk);
     }
     if (g.stats) {
         // work counters: pairs enumerated, exact evaluations, candidates kept, layers shaded
@@ -1047,11 +1051,14 @@ __global__ void __launch_bounds__(NT, BWD ? 2 : 3) k_tile_persistent(Globals g)
 }
 
 template <int K, int TT>
-static size_t tile_smem_bytes()
+constexpr size_t tile_smem_bytes()
 {
     // Smem, the K-lists, the candidate queue, the two pair-block tables
     return sizeof(Smem) + sizeof(unsigned long long) * TT * TT * K + sizeof(unsigned) * QN + 2 * NBLK;
 }
+// three CTAs of the default configuration (K = 3, 16 px tiles) per SM: 228 KB of shared
+// memory per SM, 1 KB of it reserved per CTA
+static_assert(3 * (tile_smem_bytes<3, 16>() + 1024) <= 228 * 1024, "K = 3 tiles no longer fit three CTAs per SM");
 
 template <int K, bool BWD, int TT>
 static void launch_kk(const Globals &g, cudaStream_t s)
