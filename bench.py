@@ -195,7 +195,7 @@ def recorded_traffic(kernel, pixels):
     except OSError:
         return None
     csrc = os.path.join(ROOT, "paper_2204_01386_gb300", "csrc")
-    h = hashlib.sha1(open(os.path.join(csrc, "dressi_tile.cu"), "rb").read() +
+    h = hashlib.sha1(open(os.path.join(csrc, "dressi_tile.cuh"), "rb").read() +
                      open(os.path.join(csrc, "dressi_core.cuh"), "rb").read()).hexdigest()[:16]
     if rec.get("source_hash") != h:
         return None

@@ -273,6 +273,9 @@ struct Frag {
 // (farther than r_px outside).  Pure function of (R, px, py, r_px, half_inv_S).
 // Every array index below is a compile-time constant (canonical endpoints are
 // chosen by selects), so nothing spills to local memory.
+// With LAMBDA false the closest point's parameter o.t is left at 0: the peel needs the
+// key alone, shading and the adjoint re-evaluate the kept layers with LAMBDA.
+template <bool LAMBDA = true>
 __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, float r_px, float half_inv_S,
                                           Frag &o)
 {
@@ -354,7 +357,7 @@ __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, 
             if (feat == 1) { cw = c[1]; Lw = R.L[1]; }
             if (feat == 2) { cw = c[2]; Lw = R.L[2]; }
             best = __fdiv_rn(fabsf(cw), Lw);
-            bt = __fdiv_rn(btn, btd);
+            if (LAMBDA) bt = __fdiv_rn(btn, btd);
         }
         dist = -best;
     }

@@ -1,24 +1,26 @@
-// dressi_tile.cu -- the per-tile hot kernel of HardSoftRas, forward and adjoint.
+// dressi_tile.cuh -- the per-tile hot kernel of HardSoftRas, forward and adjoint
+// (included by one translation unit per mode: dressi_tile_fwd.cu, _bwd.cu, _ids.cu).
 //
-// One CTA owns one 16 x 16 pixel tile of one view (256 threads, one pixel each;
-// warp w owns the 16 x 2 block of rows 2w, 2w + 1).  Per CTA:
-//   1. the tile's face list is staged in shared memory, CHUNK faces at a time;
-//   2. each warp culls the staged faces against its pixel block with one
-//      conservative test per (face, warp) and a ballot, then every lane
-//      evaluates the surviving faces at its own pixel centre (SignedDist,
-//      hard test, Shift) and keeps the K smallest (key, id) pairs in registers
-//      (depth peeling of Alg. 2 done as a per-pixel K-selection);
-//   3. the hard stencil S^H of a ring of rho pixels around the tile is built
-//      from the same staged faces (hard test only), so the edge mask E of
-//      every tile pixel is known without a second pass over the image;
-//   4. forward: each layer is re-evaluated from its face id, shaded
-//      (perspective-correct interpolation, bilinear texture, Lambert) and
-//      blended (D_k = sigmoid(dist/sigma), colour and silhouette equations of
-//      Sec. 3.3.3); adjoint: the same values are rebuilt and dL/dI is pushed
-//      back to the screen-space corners, vertex colours, vertex normals and
-//      texels with red.global atomics.
-// With layer ids stored by the forward, the adjoint skips steps 1-3 and reads
-// them (S^H of the ring from the neighbours' stored front layer).
+// One CTA owns one TT x TT pixel tile of one view (TT = 16 or 32; 256 threads).  Per CTA:
+//   1. the tile's face list is staged in shared memory, CH faces at a time, from the
+//      per-(view, face) record table, with tile-local edge equations for a cheap
+//      conservative pretest;
+//   2. every (face, pixel) pair of the faces' r-grown bounding boxes is enumerated
+//      (pair -> face through a per-32-pair table); pairs passing the pretest and the
+//      key lower bound are queued, and the queue gets the exact SignedDist, hard test
+//      and Shift key with full warps; each pixel keeps its K smallest (key, id) pairs
+//      in shared memory (depth peeling of Alg. 2 as a per-pixel K-selection);
+//   3. the hard stencil S^H of a ring of rho pixels around the tile is built from the
+//      same staged faces (hard test only), so the edge mask E of every tile pixel is
+//      known without a second pass over the image;
+//   4. forward: each layer is re-evaluated, shaded (perspective-correct
+//      interpolation, bilinear texture, Lambert) and blended (D_k = sigmoid(dist/sigma),
+//      colour and silhouette equations of Sec. 3.3.3); adjoint: the same values are
+//      rebuilt and dL/dI is pushed back to the screen-space corners, vertex colours,
+//      vertex normals and texels.
+// With layer ids stored by the forward (mode 2), the adjoint skips steps 1-3: S^H of
+// the tile and its ring is the stored front layer's hard flag.
+#pragma once
 #include "dressi_core.cuh"
 #include "dressi_launch.h"
 
@@ -597,7 +599,7 @@ __device__ __forceinline__ bool kept_hard(const Globals &g, const ViewK &V, cons
     FaceRec R;
     Frag fr;
     return face_get(g, V, M, (int)(unsigned int)(v & 0xffffffffu), R) &&
-           eval_face(R, px, py, V.r_px, V.half_inv_S, fr) && fr.hard;
+           eval_face<false>(R, px, py, V.r_px, V.half_inv_S, fr) && fr.hard;
 }
 
 // S^H, edge mask, shading and blend (forward) or the adjoint (BWD) of one pixel
@@ -746,8 +748,9 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
     return layers;
 }
 
-// everything one CTA does for global tile t
-template <int K, bool BWD, int TT>
+// everything one CTA does for global tile t.  MODE: 0 forward, 1 adjoint that
+// re-rasterizes, 2 adjoint from stored layer ids
+template <int K, int MODE, int TT>
 __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned long long *kbuf, const int t)
 {
     constexpr int PPT = TT * TT / NT;   // pixels per thread in the per-pixel phases
@@ -776,7 +779,8 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
     }
     for (int i = tid; i < TT * TT * K; i += NT) kbuf[i] = EMPTY;
 
-    const bool from_ids = BWD && g.ids_in != nullptr;
+    constexpr bool BWD = MODE != 0;
+    constexpr bool from_ids = MODE == 2;
     bool single_chunk = false;
     unsigned n_pairs = 0, n_exact = 0, n_cand = 0, n_layers = 0;
     int batch = 0;   // candidate-queue batches so far (selects the queue counter)
@@ -910,7 +914,8 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                     if (__uint_as_float(ent & 0xfffc0000u) > __uint_as_float((unsigned int)(last >> 32))) continue;
                     Frag fr;
                     ++n_exact;
-                    if (eval_face(S.F[f], (float)(X0 + x) + 0.5f, (float)(Y0 + y) + 0.5f, V.r_px, V.half_inv_S, fr)) {
+                    if (eval_face<false>(S.F[f], (float)(X0 + x) + 0.5f, (float)(Y0 + y) + 0.5f, V.r_px, V.half_inv_S,
+                                         fr)) {
                         ++n_cand;
                         kbuf_insert<K>(slots, pack_frag(fr.key, S.F[f].id));
                     }
@@ -1021,20 +1026,21 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
     }
 }
 
-// one CTA per tile
-template <int K, bool BWD, int TT>
-__global__ void __launch_bounds__(NT, BWD ? 2 : 3) k_tile(Globals g)
+// one CTA per tile.  Three CTAs per SM (80 registers) except for the adjoint that
+// re-rasterizes, which holds both the raster and the adjoint state (two CTAs).
+template <int K, int MODE, int TT>
+__global__ void __launch_bounds__(NT, MODE == 1 ? 2 : 3) k_tile(Globals g)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
     unsigned long long *kbuf = reinterpret_cast<unsigned long long *>(smem_raw + sizeof(Smem));
-    tile_body<K, BWD, TT>(g, S, kbuf, blockIdx.x);
+    tile_body<K, MODE, TT>(g, S, kbuf, blockIdx.x);
 }
 
 // persistent: as many CTAs as fit on the GPU pull tiles from one queue, in the
 // order of g.tile_order (longest face list first) when it is given
-template <int K, bool BWD, int TT>
-__global__ void __launch_bounds__(NT, BWD ? 2 : 3) k_tile_persistent(Globals g)
+template <int K, int MODE, int TT>
+__global__ void __launch_bounds__(NT, MODE == 1 ? 2 : 3) k_tile_persistent(Globals g)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
@@ -1045,7 +1051,7 @@ __global__ void __launch_bounds__(NT, BWD ? 2 : 3) k_tile_persistent(Globals g)
         const int q = S.next;
         if (q >= g.total_tiles) break;
         const int t = g.tile_order ? g.tile_order[q] : q;
-        tile_body<K, BWD, TT>(g, S, kbuf, t);
+        tile_body<K, MODE, TT>(g, S, kbuf, t);
         __syncthreads();   // the tile's shared memory is free again
     }
 }
@@ -1060,7 +1066,7 @@ constexpr size_t tile_smem_bytes()
 // memory per SM, 1 KB of it reserved per CTA
 static_assert(3 * (tile_smem_bytes<3, 16>() + 1024) <= 228 * 1024, "K = 3 tiles no longer fit three CTAs per SM");
 
-template <int K, bool BWD, int TT>
+template <int K, int MODE, int TT>
 static void launch_kk(const Globals &g, cudaStream_t s)
 {
     // per process: the attributes are per function, the SM count per device
@@ -1068,46 +1074,43 @@ static void launch_kk(const Globals &g, cudaStream_t s)
     static int per_sm = 1, sms = 1;
     const size_t smem = tile_smem_bytes<K, TT>();
     if (!configured) {
-        cudaFuncSetAttribute(k_tile<K, BWD, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_tile_persistent<K, BWD, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_tile<K, MODE, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_tile_persistent<K, MODE, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_persistent<K, BWD, TT>, NT, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_persistent<K, MODE, TT>, NT, smem);
         if (per_sm < 1) per_sm = 1;
         if (sms < 1) sms = 1;
         configured = true;
     }
     if (g.persistent) {
         const int grid = std::min(g.total_tiles, per_sm * sms);
-        k_tile_persistent<K, BWD, TT><<<grid, NT, smem, s>>>(g);
+        k_tile_persistent<K, MODE, TT><<<grid, NT, smem, s>>>(g);
     } else {
-        k_tile<K, BWD, TT><<<g.total_tiles, NT, smem, s>>>(g);
+        k_tile<K, MODE, TT><<<g.total_tiles, NT, smem, s>>>(g);
     }
 }
 
-template <bool BWD, int TT>
+template <int MODE, int TT>
 static void launch_k(const Globals &g, cudaStream_t s)
 {
     switch (g.K) {
-    case 1: launch_kk<1, BWD, TT>(g, s); break;
-    case 2: launch_kk<2, BWD, TT>(g, s); break;
-    case 3: launch_kk<3, BWD, TT>(g, s); break;
-    case 4: launch_kk<4, BWD, TT>(g, s); break;
-    default: launch_kk<5, BWD, TT>(g, s); break;
+    case 1: launch_kk<1, MODE, TT>(g, s); break;
+    case 2: launch_kk<2, MODE, TT>(g, s); break;
+    case 3: launch_kk<3, MODE, TT>(g, s); break;
+    case 4: launch_kk<4, MODE, TT>(g, s); break;
+    default: launch_kk<5, MODE, TT>(g, s); break;
     }
 }
 
-void launch_tile(const Globals &g, bool backward, cudaStream_t s)
+// the per-tile kernel of one mode (0 forward, 1 adjoint re-rasterizing, 2 adjoint from
+// stored layer ids); instantiated by that mode's translation unit
+template <int MODE>
+void launch_tile_mode(const Globals &g, cudaStream_t s)
 {
-    if (g.tile == 32) {
-        if (backward) launch_k<true, 32>(g, s);
-        else launch_k<false, 32>(g, s);
-    } else {
-        if (backward) launch_k<true, 16>(g, s);
-        else launch_k<false, 16>(g, s);
-    }
-    count_launch(1);
+    if (g.tile == 32) launch_k<MODE, 32>(g, s);
+    else launch_k<MODE, 16>(g, s);
 }
 
 }  // namespace dressi
