@@ -272,7 +272,10 @@ struct Frag {
 // face R at pixel centre (px, py).  Returns false when the face is not a candidate
 // (farther than r_px outside).  Pure function of (R, px, py, r_px, half_inv_S).
 // Every array index below is a compile-time constant (canonical endpoints are
-// chosen by selects), so nothing spills to local memory.
+// chosen by selects), so nothing spills to local memory.  An edge distance is the
+// canonical cross product times the record's 1/L and a corner distance the square
+// root at the shared corner, so the faces around a shared edge or corner compute
+// bit-identical distances to it.
 // With LAMBDA false the closest point's parameter o.t is left at 0: the peel needs the
 // key alone, shading and the adjoint re-evaluate the kept layers with LAMBDA.
 template <bool LAMBDA = true>
@@ -316,11 +319,7 @@ __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, 
         feat = 0;
         if (F[1] < a) { a = F[1]; feat = 1; }
         if (F[2] < a) { a = F[2]; feat = 2; }
-        // the selected distance itself correctly rounded: Fn / L
-        float fnw = o.Fn[0], Lw = R.L[0];
-        if (feat == 1) { fnw = o.Fn[1]; Lw = R.L[1]; }
-        if (feat == 2) { fnw = o.Fn[2]; Lw = R.L[2]; }
-        dist = __fdiv_rn(fnw, Lw);
+        dist = a;
     } else {
         float best = 3.4e38f, btn = 0.f, btd = 1.f;
         feat = 0;
@@ -350,15 +349,8 @@ __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, 
                 btn = tP; btd = ffma(ex, ex, fmul(ey, ey));
             }
         }
-        if (feat < 3) {
-            // edge interior: recompute the selected distance correctly rounded, |c| / L,
-            // and the closest point's parameter along the edge
-            float cw = c[0], Lw = R.L[0];
-            if (feat == 1) { cw = c[1]; Lw = R.L[1]; }
-            if (feat == 2) { cw = c[2]; Lw = R.L[2]; }
-            best = __fdiv_rn(fabsf(cw), Lw);
-            if (LAMBDA) bt = __fdiv_rn(btn, btd);
-        }
+        // edge interior: the closest point's parameter along the edge
+        if (LAMBDA && feat < 3) bt = __fdiv_rn(btn, btd);
         dist = -best;
     }
     if (!(dist >= -r_px)) return false;
