@@ -105,22 +105,6 @@ __device__ __forceinline__ float approx_fmin(const Pre &P, float lx, float ly)
     return fminf(f0, fminf(f1, f2));
 }
 
-// Per-pixel pre-test: false when the face is certainly farther than r; otherwise a
-// lower bound of its Shift() key (outside: the distance is at least the largest
-// edge-line distance; inside: the depth is at least the smallest corner depth).
-__device__ __forceinline__ bool approx_candidate(const Pre &P, float lx, float ly, float r_px, float half_inv_S,
-                                                 float &klb)
-{
-    const float eps = APPROX_EPS;
-    if (lx < P.bx0 - eps || lx > P.bx1 + eps || ly < P.by0 - eps || ly > P.by1 + eps) return false;
-    const float fmin = approx_fmin(P, lx, ly);
-    if (fmin < -r_px - eps) return false;
-    if (fmin > eps) klb = 0.5f * P.zmin * (1.f - 1e-6f);
-    else if (fmin < -eps) klb = fmaf(-fmin - eps, half_inv_S, 0.5f);
-    else klb = 0.f;
-    return true;
-}
-
 // position of halo pixel h in the ring of width rho around a TT x TT tile (tile-local)
 template <int TT>
 __device__ __forceinline__ void halo_pos(int h, int rho, int &hx, int &hy)
@@ -513,7 +497,7 @@ struct Smem {
     Pre P[CH];
     int rect[CH];        // tile pairs: x0 | y0 << 8 | w << 16 | h << 24 (tile-local, x0/y0 >= 0)
     int hrect[CH];       // ring pairs: (x0 + 16) | (y0 + 16) << 8 | w << 16 | h << 24
-    int start[CH];       // exclusive prefix of tile pairs
+    int start[CH];       // exclusive prefix of tile segments (4-pixel row pieces of the rects)
     int hstart[CH];      // exclusive prefix of ring pairs
     int2 hash[HASH];     // (face id, slot) of the last staged chunk
     int wsum[2][NT / 32];
@@ -810,7 +794,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                     const int y1 = min(hlim - 1, (int)floorf(P.by1 - 0.5f + APPROX_EPS));
                     const int w = x1 - x0 + 1, h = y1 - y0 + 1;
                     if (w > 0 && h > 0) {
-                        cnt = w * h;
+                        cnt = ((w + 3) >> 2) * h;   // segments of up to 4 pixels per row
                         S.rect[tid] = x0 | (y0 << 8) | (w << 16) | (h << 24);
                     }
                     if (rho > 0) {
@@ -865,43 +849,73 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
             }
             __syncthreads();
             const int total = S.totals[0], htotal = S.totals[1];
-            // (face, pixel) pairs of the tile, in batches of QN: (1) every pair takes the
-            // approximate test and the survivors are queued, (2) the queue takes the exact
-            // evaluation with full warps.  A queue entry is x | y << 5 | face << 10 with the
-            // top 14 bits of the key lower bound above (truncated: still a lower bound).
-            if (g.stats) n_pairs += (total > tid) ? (total - tid + NT - 1) / NT : 0;
+            // (face, 4-pixel row segment) items of the tile's pairs, one per thread and
+            // batch: (1) every item takes the approximate test at its (up to) four pixel
+            // centres -- inside the face's grown bbox by construction of the rect -- with
+            // the edge equations stepped along x, and the pixels that pass are queued;
+            // (2) the queue takes the exact evaluation with full warps.  A queue entry is
+            // x | y << 5 | face << 10 with the top 14 bits of the key lower bound above
+            // (truncated: still a lower bound).
             const int lane = tid & 31;
-            for (int b0 = 0; b0 < total; b0 += QN) {
+            for (int b0 = 0; b0 < total; b0 += NT) {
                 int *qn = &S.qn[batch & 1];
-                const int rounds = min(QN / NT, (total - b0 + NT - 1) / NT);
-                for (int r = 0; r < rounds; ++r) {
-                    const int i = b0 + r * NT + tid;
-                    bool pass = false;
-                    unsigned ent = 0u;
-                    if (i < total) {
-                        const int f = pair_face(S.start, blk, nch, i - lane, i);
-                        const int rc = S.rect[f];
-                        int x, y;
-                        rect_xy(i - S.start[f], (rc >> 16) & 0xff, x, y);
-                        x += rc & 0xff;
-                        y += (rc >> 8) & 0xff;
-                        float klb;
-                        if (approx_candidate(S.P[f], (float)x + 0.5f, (float)y + 0.5f, V.r_px, V.half_inv_S, klb)) {
-                            const unsigned long long last = kbuf[(y * TT + x) * K + K - 1];
-                            if (!(klb > __uint_as_float((unsigned int)(last >> 32)))) {
-                                pass = true;
-                                ent = (__float_as_uint(klb) & 0xfffc0000u) | ((unsigned)f << 10) |
-                                      ((unsigned)y << 5) | (unsigned)x;
+                const int i = b0 + tid;
+                unsigned pm = 0u;   // pass bits of the segment's pixels
+                float kl[4] = {0.f, 0.f, 0.f, 0.f};
+                int f = 0, x = 0, y = 0;
+                if (i < total) {
+                    f = pair_face(S.start, blk, nch, i - lane, i);
+                    const int rc = S.rect[f];
+                    const int w = (rc >> 16) & 0xff;
+                    int qx, qy;
+                    rect_xy(i - S.start[f], (w + 3) >> 2, qx, qy);
+                    x = (rc & 0xff) + 4 * qx;
+                    y = ((rc >> 8) & 0xff) + qy;
+                    const int np = min(4, (rc & 0xff) + w - x);
+                    if (g.stats) n_pairs += np;
+                    const Pre &P = S.P[f];
+                    const float fx = (float)x + 0.5f, fy = (float)y + 0.5f;
+                    float e0 = fmaf(P.nx[0], fx, fmaf(P.ny[0], fy, P.c[0]));
+                    float e1 = fmaf(P.nx[1], fx, fmaf(P.ny[1], fy, P.c[1]));
+                    float e2 = fmaf(P.nx[2], fx, fmaf(P.ny[2], fy, P.c[2]));
+                    const float klb_in = 0.5f * P.zmin * (1.f - 1e-6f);
+                    const unsigned long long *last = kbuf + (y * TT + x) * K + K - 1;
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        // F(p) ~ the smallest edge value: outside, the distance is at least
+                        // -F; inside, the depth is at least the smallest corner depth
+                        const float fmin = fminf(e0, fminf(e1, e2));
+                        if (d < np && fmin >= -V.r_px - APPROX_EPS) {
+                            const float klb = fmin > APPROX_EPS    ? klb_in
+                                              : fmin < -APPROX_EPS ? fmaf(-fmin - APPROX_EPS, V.half_inv_S, 0.5f)
+                                                                   : 0.f;
+                            if (!(klb > __uint_as_float((unsigned int)(last[d * K] >> 32)))) {
+                                pm |= 1u << d;
+                                kl[d] = klb;
                             }
                         }
+                        e0 += P.nx[0];
+                        e1 += P.nx[1];
+                        e2 += P.nx[2];
                     }
-                    const unsigned m = __ballot_sync(0xffffffffu, pass);
-                    if (m) {
-                        int qb = 0;
-                        if (lane == 0) qb = atomicAdd(qn, __popc(m));
-                        qb = __shfl_sync(0xffffffffu, qb, 0);
-                        if (pass) qbuf[qb + __popc(m & ((1u << lane) - 1u))] = ent;
-                    }
+                }
+                // warp-wide prefix of the pass counts, one queue reservation per warp
+                const int c = __popc(pm);
+                int incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+                if (wtot) {
+                    int qb = 0;
+                    if (lane == 0) qb = atomicAdd(qn, wtot);
+                    qb = __shfl_sync(0xffffffffu, qb, 0) + incl - c;
+                    const unsigned base = ((unsigned)f << 10) | ((unsigned)y << 5) | (unsigned)x;
+#pragma unroll
+                    for (int d = 0; d < 4; ++d)
+                        if ((pm >> d) & 1u) qbuf[qb++] = (__float_as_uint(kl[d]) & 0xfffc0000u) | (base + d);
                 }
                 __syncthreads();   // queue complete
                 const int nq = *qn;
