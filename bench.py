@@ -43,7 +43,7 @@ L2_FLUSH_BYTES = 512 << 20
 WORKLOADS = ("multiview", "textured", "ragged", "large")
 
 
-def workload_scene(rank=0, world=1, n_views=64, res=512, workload="multiview"):
+def workload_scene(rank=0, world=1, n_views=None, res=512, workload="multiview"):
     """The benchmark workloads.  multiview (default): 64 views of 512^2 of a 20,480-tri
     displaced UV sphere, 1024^2 FP32 texture, Lambert.  textured: one 256^2 view of a
     5,120-tri sphere with a 512^2 texture.  ragged: 32 meshes of 1k..200k tris at mixed
@@ -51,14 +51,14 @@ def workload_scene(rank=0, world=1, n_views=64, res=512, workload="multiview"):
     of 2048^2, checkpointed backward.  With several ranks every rank renders its own
     views (directions strided over ranks): weak scaling."""
     if workload == "multiview":
-        s = synth.config3(n_views=n_views * world, res=res)
+        s = synth.config3(n_views=(n_views or 64) * world, res=res)
     elif workload == "textured":
         s = synth.config2()
         s.views = s.views * world
     elif workload == "ragged":
         s = synth.config4()
     else:
-        s = synth.config5(n_views=8 * world)
+        s = synth.config5(n_views=(n_views or 8) * world)
     s.views = s.views[rank::world]
     return s
 
@@ -457,7 +457,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-views", type=int, default=12)
-    ap.add_argument("--views", type=int, default=64, help="views per rank (64 = the benchmark workload)")
+    ap.add_argument("--views", type=int, default=None,
+                    help="views per rank of the multiview (default 64) or large (default 8) workload")
     ap.add_argument("--tile", type=int, default=0, choices=[0, 16, 32],
                     help="screen tile edge in pixels (0: chosen by the autotuner)")
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 1, 2],

@@ -321,7 +321,8 @@ __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, 
         if (F[2] < a) { a = F[2]; feat = 2; }
         dist = a;
     } else {
-        float best = 3.4e38f, btn = 0.f, btd = 1.f;
+        // squared distances compared without branches; one square root for a corner
+        float best2 = 3.4e38f, bsel = -1.f, btn = 0.f, btd = 1.f;
         feat = 0;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
@@ -329,29 +330,21 @@ __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, 
             const int ia = i, ib = (i + 1) % 3;
             const float ex = fsub(pX[i], qX[i]), ey = fsub(pY[i], qY[i]);   // V_Q - V_P
             const float tP = ffma(pX[i], ex, fmul(pY[i], ey));
-            float s;
-            int ft;
-            if (tP <= 0.f) {
-                s = __fsqrt_rn(ffma(pX[i], pX[i], fmul(pY[i], pY[i])));
-                ft = 3 + (sw ? ib : ia);
-            } else {
-                const float tQ = ffma(qX[i], ex, fmul(qY[i], ey));
-                if (tQ >= 0.f) {
-                    s = __fsqrt_rn(ffma(qX[i], qX[i], fmul(qY[i], qY[i])));
-                    ft = 3 + (sw ? ia : ib);
-                } else {
-                    s = fmul(fabsf(c[i]), R.invL[i]);
-                    ft = i;
-                }
-            }
-            if (s < best) {
-                best = s; feat = ft;
+            const float tQ = ffma(qX[i], ex, fmul(qY[i], ey));
+            const float dP2 = ffma(pX[i], pX[i], fmul(pY[i], pY[i]));
+            const float dQ2 = ffma(qX[i], qX[i], fmul(qY[i], qY[i]));
+            const float se = fmul(fabsf(c[i]), R.invL[i]);
+            const bool atP = tP <= 0.f, atQ = !atP && tQ >= 0.f;
+            const float s2 = atP ? dP2 : atQ ? dQ2 : fmul(se, se);
+            const int ft = atP ? 3 + (sw ? ib : ia) : atQ ? 3 + (sw ? ia : ib) : i;
+            if (s2 < best2) {
+                best2 = s2; feat = ft; bsel = (atP || atQ) ? -1.f : se;
                 btn = tP; btd = ffma(ex, ex, fmul(ey, ey));
             }
         }
         // edge interior: the closest point's parameter along the edge
         if (LAMBDA && feat < 3) bt = __fdiv_rn(btn, btd);
-        dist = -best;
+        dist = -(bsel >= 0.f ? bsel : __fsqrt_rn(best2));
     }
     if (!(dist >= -r_px)) return false;
     o.dist = dist;
