@@ -62,12 +62,12 @@ struct __align__(16) VRec {
     int pad;
 };
 
-// per-face record used by every pixel evaluation
-// 32 words (128 bytes, one cache line): word 22 holds the flags
+// per-face record used by every pixel evaluation.  28 words (112 bytes; word 19 holds
+// the flags): staged in shared memory, the records of 8 consecutive faces fall into
+// distinct banks for 16-byte loads.
 struct __align__(16) FaceRec {
     float xh[3], xl[3], yh[3], yl[3];
-    float L[3];      // length of edge i (canonical)
-    float invL[3];   // 1 / L
+    float invL[3];   // 1 / length of edge i (canonical), correctly rounded
     float z[3];
     float invA;      // 1 / |twice the signed area|
     int flags;       // bit 0: orient > 0; bits 1-3: edge i swapped; bits 4-6: edge i owns;
@@ -75,9 +75,9 @@ struct __align__(16) FaceRec {
     int id;          // face index local to the mesh
     int vi[3];       // vertex indices local to the mesh
     float iw[3];     // 1 / w of the corners
-    int pad[2];
+    int pad;
 };
-static_assert(sizeof(FaceRec) == 128, "FaceRec is one 128-byte line");
+static_assert(sizeof(FaceRec) == 112, "FaceRec is 28 words");
 
 struct Globals {
     const ViewK *views;
@@ -196,7 +196,6 @@ __device__ __forceinline__ bool face_load(const Globals &g, const MeshK &m, cons
         const float ex = fadd(fsub(Qxh, Pxh), fsub(Qxl, Pxl));
         const float ey = fadd(fsub(Qyh, Pyh), fsub(Qyl, Pyl));
         const float L = __fsqrt_rn(ffma(ex, ex, fmul(ey, ey)));
-        R.L[i] = L;
         R.invL[i] = __fdiv_rn(1.f, L);
         // oriented edge ia -> ib
         const float eox = sw ? -ex : ex, eoy = sw ? -ey : ey;
@@ -220,25 +219,25 @@ __device__ __forceinline__ bool face_get(const Globals &g, const ViewK &V, const
         return false;
     }
     const float4 *src = reinterpret_cast<const float4 *>(g.frec + V.frec_off + f);
-    float w[32];
+    float w[28];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < 7; ++i) {
         const float4 q = __ldg(src + i);
         w[4 * i] = q.x; w[4 * i + 1] = q.y; w[4 * i + 2] = q.z; w[4 * i + 3] = q.w;
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         R.xh[i] = w[i]; R.xl[i] = w[3 + i]; R.yh[i] = w[6 + i]; R.yl[i] = w[9 + i];
-        R.L[i] = w[12 + i]; R.invL[i] = w[15 + i]; R.z[i] = w[18 + i];
-        R.vi[i] = __float_as_int(w[24 + i]); R.iw[i] = w[27 + i];
+        R.invL[i] = w[12 + i]; R.z[i] = w[15 + i];
+        R.vi[i] = __float_as_int(w[21 + i]); R.iw[i] = w[24 + i];
     }
-    R.invA = w[21];
-    R.flags = __float_as_int(w[22]);
-    R.id = __float_as_int(w[23]);
+    R.invA = w[18];
+    R.flags = __float_as_int(w[19]);
+    R.id = __float_as_int(w[20]);
     return (R.flags & FLAG_LIVE) != 0;
 }
 
-// face_get into shared memory: eight 16-byte copies
+// face_get into shared memory: seven 16-byte copies
 __device__ __forceinline__ bool face_stage(const Globals &g, const ViewK &V, const MeshK &m, int f, FaceRec &dst)
 {
     if ((unsigned)f >= (unsigned)m.nF) {
@@ -250,10 +249,10 @@ __device__ __forceinline__ bool face_stage(const Globals &g, const ViewK &V, con
     float4 *d = reinterpret_cast<float4 *>(&dst);
     int flags = 0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < 7; ++i) {
         const float4 q = __ldg(src + i);
         d[i] = q;
-        if (i == 5) flags = __float_as_int(q.z);   // word 22
+        if (i == 4) flags = __float_as_int(q.w);   // word 19
     }
     return (flags & FLAG_LIVE) != 0;
 }

@@ -122,7 +122,7 @@ __global__ void k_normal_csr(Globals g)
 // ---------------------------------------------------------------------------
 // face table: the record of every (view, face) -- screen corners, canonical edges,
 // lengths, area, flags -- built once per call and read by binning, staging,
-// shading and the adjoint (one 128-byte line each)
+// shading and the adjoint (112 bytes each)
 // ---------------------------------------------------------------------------
 __global__ void k_face(Globals g)
 {
@@ -141,11 +141,11 @@ __global__ void k_face(Globals g)
         dst[0] = make_float4(R.xh[0], R.xh[1], R.xh[2], R.xl[0]);
         dst[1] = make_float4(R.xl[1], R.xl[2], R.yh[0], R.yh[1]);
         dst[2] = make_float4(R.yh[2], R.yl[0], R.yl[1], R.yl[2]);
-        dst[3] = make_float4(R.L[0], R.L[1], R.L[2], R.invL[0]);
-        dst[4] = make_float4(R.invL[1], R.invL[2], R.z[0], R.z[1]);
-        dst[5] = make_float4(R.z[2], R.invA, __int_as_float(R.flags), __int_as_float(R.id));
-        dst[6] = make_float4(__int_as_float(R.vi[0]), __int_as_float(R.vi[1]), __int_as_float(R.vi[2]), R.iw[0]);
-        dst[7] = make_float4(R.iw[1], R.iw[2], 0.f, 0.f);
+        dst[3] = make_float4(R.invL[0], R.invL[1], R.invL[2], R.z[0]);
+        dst[4] = make_float4(R.z[1], R.z[2], R.invA, __int_as_float(R.flags));
+        dst[5] = make_float4(__int_as_float(R.id), __int_as_float(R.vi[0]), __int_as_float(R.vi[1]),
+                             __int_as_float(R.vi[2]));
+        dst[6] = make_float4(R.iw[0], R.iw[1], R.iw[2], 0.f);
     }
 }
 

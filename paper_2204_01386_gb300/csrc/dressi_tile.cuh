@@ -39,19 +39,25 @@ constexpr unsigned long long EMPTY = ~0ULL;
 constexpr int QN = 4 * NT;             // queued candidate pairs per batch
 constexpr int NBLK = 2048;             // pair blocks of 32 with a table entry (65,536 pairs)
 
-// conservative tile-local data of a staged face: edge equations and bbox in pixels
-// relative to the tile origin (FP32, a few 1e-6 px of error), and the smallest depth
+// conservative tile-local data of a staged face: edge equations in pixels relative to
+// the tile origin (FP32, a few 1e-6 px of error) and the smallest corner depth.  12 words:
+// the records of 8 consecutive faces fall into distinct banks for 16-byte loads.
 struct Pre {
     float nx[3], ny[3], c[3];    // F_i(p) ~ nx p.x + ny p.y + c, inward unit normal
-    float bx0, bx1, by0, by1;    // bbox grown by r
     float zmin;
     float pad[2];
 };
+static_assert(sizeof(Pre) == 48, "Pre is 12 words");
 
-__device__ __forceinline__ void make_pre(const FaceRec &R, bool live, float tx0, float ty0, float r_px, Pre &P)
+// the face's bounding box in tile-local pixels, grown by r
+struct Box {
+    float bx0, bx1, by0, by1;
+};
+
+__device__ __forceinline__ void make_pre(const FaceRec &R, bool live, float tx0, float ty0, float r_px, Pre &P, Box &B)
 {
     if (!live) {
-        P.bx0 = 3.0e38f; P.bx1 = -3.0e38f; P.by0 = 3.0e38f; P.by1 = -3.0e38f;
+        B.bx0 = 3.0e38f; B.bx1 = -3.0e38f; B.by0 = 3.0e38f; B.by1 = -3.0e38f;
 #pragma unroll
         for (int i = 0; i < 3; ++i) { P.nx[i] = 0.f; P.ny[i] = 0.f; P.c[i] = -3.0e38f; }
         P.zmin = 3.0e38f;
@@ -76,24 +82,11 @@ __device__ __forceinline__ void make_pre(const FaceRec &R, bool live, float tx0,
         P.nx[i] = nx; P.ny[i] = ny;
         P.c[i] = -(nx * vx[i] + ny * vy[i]);
     }
-    P.bx0 = fminf(vx[0], fminf(vx[1], vx[2])) - r_px;
-    P.bx1 = fmaxf(vx[0], fmaxf(vx[1], vx[2])) + r_px;
-    P.by0 = fminf(vy[0], fminf(vy[1], vy[2])) - r_px;
-    P.by1 = fmaxf(vy[0], fmaxf(vy[1], vy[2])) + r_px;
+    B.bx0 = fminf(vx[0], fminf(vx[1], vx[2])) - r_px;
+    B.bx1 = fmaxf(vx[0], fmaxf(vx[1], vx[2])) + r_px;
+    B.by0 = fminf(vy[0], fminf(vy[1], vy[2])) - r_px;
+    B.by1 = fmaxf(vy[0], fmaxf(vy[1], vy[2])) + r_px;
     P.zmin = fminf(R.z[0], fminf(R.z[1], R.z[2]));
-}
-
-// may some pixel centre of the box (cx +- hx, cy +- hy) be within r of the face?
-__device__ __forceinline__ bool pretest_box(const Pre &P, float cx, float cy, float hx, float hy, float r_px)
-{
-    const float eps = APPROX_EPS;
-    if (P.bx1 < cx - hx - eps || P.bx0 > cx + hx + eps || P.by1 < cy - hy - eps || P.by0 > cy + hy + eps) return false;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const float F = P.nx[i] * cx + P.ny[i] * cy + P.c[i] + fabsf(P.nx[i]) * hx + fabsf(P.ny[i]) * hy;
-        if (F < -r_px - eps) return false;
-    }
-    return true;
 }
 
 // smallest approximate edge value of the face at one tile-local pixel centre
@@ -784,14 +777,14 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                 const int f = fallback ? c0 + tid : g.lists[lb + c0 + tid];
                 FaceRec &R = S.F[tid];
                 const bool live = face_stage(g, V, M, f, R);
-                Pre &P = S.P[tid];
-                make_pre(R, live, (float)X0, (float)Y0, V.r_px, P);
+                Box B;
+                make_pre(R, live, (float)X0, (float)Y0, V.r_px, S.P[tid], B);
                 if (live) {
                     // pixel centres lx + 1/2 inside [bx0, bx1] (grown by r), clipped to the tile and image
-                    const int x0 = max(0, (int)ceilf(P.bx0 - 0.5f - APPROX_EPS));
-                    const int x1 = min(wlim - 1, (int)floorf(P.bx1 - 0.5f + APPROX_EPS));
-                    const int y0 = max(0, (int)ceilf(P.by0 - 0.5f - APPROX_EPS));
-                    const int y1 = min(hlim - 1, (int)floorf(P.by1 - 0.5f + APPROX_EPS));
+                    const int x0 = max(0, (int)ceilf(B.bx0 - 0.5f - APPROX_EPS));
+                    const int x1 = min(wlim - 1, (int)floorf(B.bx1 - 0.5f + APPROX_EPS));
+                    const int y0 = max(0, (int)ceilf(B.by0 - 0.5f - APPROX_EPS));
+                    const int y1 = min(hlim - 1, (int)floorf(B.by1 - 0.5f + APPROX_EPS));
                     const int w = x1 - x0 + 1, h = y1 - y0 + 1;
                     if (w > 0 && h > 0) {
                         cnt = ((w + 3) >> 2) * h;   // segments of up to 4 pixels per row
@@ -800,10 +793,10 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                     if (rho > 0) {
                         // hard bbox (without r) against the ring [-rho, TT + rho), clipped to the image
                         const float r = V.r_px;
-                        const int hx0 = max(max(-rho, -X0), (int)ceilf(P.bx0 + r - 0.5f - APPROX_EPS));
-                        const int hx1 = min(min(TT + rho, V.W - X0) - 1, (int)floorf(P.bx1 - r - 0.5f + APPROX_EPS));
-                        const int hy0 = max(max(-rho, -Y0), (int)ceilf(P.by0 + r - 0.5f - APPROX_EPS));
-                        const int hy1 = min(min(TT + rho, V.H - Y0) - 1, (int)floorf(P.by1 - r - 0.5f + APPROX_EPS));
+                        const int hx0 = max(max(-rho, -X0), (int)ceilf(B.bx0 + r - 0.5f - APPROX_EPS));
+                        const int hx1 = min(min(TT + rho, V.W - X0) - 1, (int)floorf(B.bx1 - r - 0.5f + APPROX_EPS));
+                        const int hy0 = max(max(-rho, -Y0), (int)ceilf(B.by0 + r - 0.5f - APPROX_EPS));
+                        const int hy1 = min(min(TT + rho, V.H - Y0) - 1, (int)floorf(B.by1 - r - 0.5f + APPROX_EPS));
                         const int hw = hx1 - hx0 + 1, hh = hy1 - hy0 + 1;
                         // only faces reaching outside the tile interior have ring pixels
                         const bool ring = hx0 < 0 || hy0 < 0 || hx1 >= TT || hy1 >= TT;
