@@ -33,7 +33,7 @@ constexpr int TT_MAX = 32;             // tile edges: 16 (one pixel per thread) 
 constexpr int RHO_MAX = 8;             // largest supported edge-mask radius
 constexpr int HS_MAX = TT_MAX + 2 * RHO_MAX;
 constexpr float APPROX_EPS = 1e-3f;    // pixel slack of the tile-local (approximate) edge equations
-constexpr int CH = 256;                // faces staged per round (one per thread)
+constexpr int CH = 128;                // faces staged per round (one per thread of the first half)
 constexpr int HASH = 2 * CH;           // face id -> staged slot, open addressing
 constexpr unsigned long long EMPTY = ~0ULL;
 constexpr int QN = 4 * NT;             // queued candidate pairs per batch
@@ -486,6 +486,14 @@ __device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, 
 // smallest pairs in order, whatever the interleaving.
 // ---------------------------------------------------------------------------
 struct Smem {
+    // every mode
+    int view, totals[2], next;
+    int qn[2];           // queue fill of the current batch, by batch parity
+    unsigned long long m0[HS_MAX], m1[HS_MAX];   // per halo row: columns with S^H = 0 / 1
+    unsigned char sh[HS_MAX * HS_MAX];
+    // the raster (forward and re-rasterizing adjoint) only: the adjoint from stored ids
+    // is launched with the shared memory up to F, leaving the rest of the SM's unified
+    // L1 / shared storage to the L1 cache
     FaceRec F[CH];
     Pre P[CH];
     int rect[CH];        // tile pairs: x0 | y0 << 8 | w << 16 | h << 24 (tile-local, x0/y0 >= 0)
@@ -494,10 +502,6 @@ struct Smem {
     int hstart[CH];      // exclusive prefix of ring pairs
     int2 hash[HASH];     // (face id, slot) of the last staged chunk
     int wsum[2][NT / 32];
-    int view, totals[2], next;
-    int qn[2];           // queue fill of the current batch, by batch parity
-    unsigned long long m0[HS_MAX], m1[HS_MAX];   // per halo row: columns with S^H = 0 / 1
-    unsigned char sh[HS_MAX * HS_MAX];
 };
 
 __device__ __forceinline__ unsigned long long pack_frag(float key, int id)
@@ -754,7 +758,8 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
         const int hx = X0 - rho + i % hs, hy = Y0 - rho + i / hs;
         S.sh[i] = (hx >= 0 && hy >= 0 && hx < V.W && hy < V.H) ? 0 : 2;
     }
-    for (int i = tid; i < TT * TT * K; i += NT) kbuf[i] = EMPTY;
+    if (MODE != 2)
+        for (int i = tid; i < TT * TT * K; i += NT) kbuf[i] = EMPTY;
 
     constexpr bool BWD = MODE != 0;
     constexpr bool from_ids = MODE == 2;
@@ -1033,10 +1038,14 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
     }
 }
 
-// one CTA per tile.  Three CTAs per SM (80 registers) except for the adjoint that
-// re-rasterizes, which holds both the raster and the adjoint state (two CTAs).
+// one CTA per tile.  CTAs per SM: four for the forward (64 registers), three for the
+// adjoint from stored ids (80), two for the adjoint that re-rasterizes, which holds
+// both the raster and the adjoint state.
+template <int MODE>
+constexpr int tile_min_ctas() { return MODE == 0 ? 4 : MODE == 2 ? 3 : 2; }
+
 template <int K, int MODE, int TT>
-__global__ void __launch_bounds__(NT, MODE == 1 ? 2 : 3) k_tile(Globals g)
+__global__ void __launch_bounds__(NT, tile_min_ctas<MODE>()) k_tile(Globals g)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
@@ -1047,7 +1056,7 @@ __global__ void __launch_bounds__(NT, MODE == 1 ? 2 : 3) k_tile(Globals g)
 // persistent: as many CTAs as fit on the GPU pull tiles from one queue, in the
 // order of g.tile_order (longest face list first) when it is given
 template <int K, int MODE, int TT>
-__global__ void __launch_bounds__(NT, MODE == 1 ? 2 : 3) k_tile_persistent(Globals g)
+__global__ void __launch_bounds__(NT, tile_min_ctas<MODE>()) k_tile_persistent(Globals g)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
@@ -1063,15 +1072,17 @@ __global__ void __launch_bounds__(NT, MODE == 1 ? 2 : 3) k_tile_persistent(Globa
     }
 }
 
-template <int K, int TT>
+template <int K, int MODE, int TT>
 constexpr size_t tile_smem_bytes()
 {
-    // Smem, the K-lists, the candidate queue, the two pair-block tables
-    return sizeof(Smem) + sizeof(unsigned long long) * TT * TT * K + sizeof(unsigned) * QN + 2 * NBLK;
+    // the adjoint from stored ids: the first part of Smem; otherwise Smem, the K-lists,
+    // the candidate queue, the two pair-block tables
+    return MODE == 2 ? offsetof(Smem, F)
+                     : sizeof(Smem) + sizeof(unsigned long long) * TT * TT * K + sizeof(unsigned) * QN + 2 * NBLK;
 }
-// three CTAs of the default configuration (K = 3, 16 px tiles) per SM: 228 KB of shared
-// memory per SM, 1 KB of it reserved per CTA
-static_assert(3 * (tile_smem_bytes<3, 16>() + 1024) <= 228 * 1024, "K = 3 tiles no longer fit three CTAs per SM");
+// four forward CTAs of the default configuration (K = 3, 16 px tiles) per SM: 228 KB of
+// shared memory per SM, 1 KB of it reserved per CTA
+static_assert(4 * (tile_smem_bytes<3, 0, 16>() + 1024) <= 228 * 1024, "K = 3 forward tiles no longer fit four CTAs per SM");
 
 template <int K, int MODE, int TT>
 static void launch_kk(const Globals &g, cudaStream_t s)
@@ -1079,7 +1090,7 @@ static void launch_kk(const Globals &g, cudaStream_t s)
     // per process: the attributes are per function, the SM count per device
     static bool configured = false;
     static int per_sm = 1, sms = 1;
-    const size_t smem = tile_smem_bytes<K, TT>();
+    const size_t smem = tile_smem_bytes<K, MODE, TT>();
     if (!configured) {
         cudaFuncSetAttribute(k_tile<K, MODE, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_tile_persistent<K, MODE, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
