@@ -1038,14 +1038,15 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
     }
 }
 
-// one CTA per tile.  CTAs per SM: four for the forward (64 registers), three for the
-// adjoint from stored ids (80), two for the adjoint that re-rasterizes, which holds
-// both the raster and the adjoint state.
-template <int MODE>
-constexpr int tile_min_ctas() { return MODE == 0 ? 4 : MODE == 2 ? 3 : 2; }
+// one CTA per tile.  CTAs per SM (measured best): four for the forward (64 registers),
+// three for the adjoint from stored ids (80); the adjoint that re-rasterizes holds both
+// the raster and the adjoint state: four with 16 px tiles, three with 32 px tiles (whose
+// K-lists limit the shared memory to three CTAs anyway).
+template <int MODE, int TT>
+constexpr int tile_min_ctas() { return MODE == 0 ? 4 : MODE == 2 ? 3 : (TT == 16 ? 4 : 3); }
 
 template <int K, int MODE, int TT>
-__global__ void __launch_bounds__(NT, tile_min_ctas<MODE>()) k_tile(Globals g)
+__global__ void __launch_bounds__(NT, tile_min_ctas<MODE, TT>()) k_tile(Globals g)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
@@ -1056,7 +1057,7 @@ __global__ void __launch_bounds__(NT, tile_min_ctas<MODE>()) k_tile(Globals g)
 // persistent: as many CTAs as fit on the GPU pull tiles from one queue, in the
 // order of g.tile_order (longest face list first) when it is given
 template <int K, int MODE, int TT>
-__global__ void __launch_bounds__(NT, tile_min_ctas<MODE>()) k_tile_persistent(Globals g)
+__global__ void __launch_bounds__(NT, tile_min_ctas<MODE, TT>()) k_tile_persistent(Globals g)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
