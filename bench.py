@@ -197,12 +197,10 @@ def recorded_traffic(kernel, pixels):
     csrc = os.path.join(ROOT, "paper_2204_01386_gb300", "csrc")
     h = hashlib.sha1(open(os.path.join(csrc, "dressi_tile.cuh"), "rb").read() +
                      open(os.path.join(csrc, "dressi_core.cuh"), "rb").read()).hexdigest()[:16]
-    if rec.get("source_hash") != h:
+    if rec.get("source_hash") != h or kernel not in rec:
         return None
-    for d in ("fwd", "bwd"):
-        if rec.get(d + "_kernel") == kernel:
-            return int(rec[d + "_bytes"]) * pixels / int(rec["pixels_captured"])
-    return None
+    nbytes, npix = rec[kernel].split()
+    return int(nbytes) * pixels / int(npix)
 
 
 def ours(args, rank, world, local_rank):
