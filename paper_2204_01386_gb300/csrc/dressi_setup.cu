@@ -1,4 +1,4 @@
-// dressi_setup.cu -- per-vertex and per-face stages: FP64 vertex transform,
+// dressi_setup.cu -- per-vertex and per-face stages: double-float vertex transform,
 // vertex normals, tile binning (count / scan / fill) and the per-vertex end of
 // the adjoint (screen -> clip -> object space, normals -> positions).
 #include "dressi_core.cuh"
@@ -8,9 +8,64 @@ namespace dressi {
 
 // ---------------------------------------------------------------------------
 // vertex transform (render-graph listing: homogeneous position, MVP, face lookup)
-// clip = MVP (p, 1) in FP64 with each operation rounded as written, then
-// X = (x/w + 1)/2 W, Y = (y/w + 1)/2 H, depth z/w; stored as float pairs.
+// clip = MVP (p, 1), X = (x/w + 1)/2 W, Y = (y/w + 1)/2 H, depth z/w, evaluated in
+// double-float arithmetic (an unevaluated sum hi + lo of two FP32 numbers, ~2^-45
+// relative accuracy) built from the error-free transformations two-sum (Knuth) and
+// two-product with FMA (as in Ogita, Rump and Oishi, "Accurate sum and dot product",
+// 2005).  The screen position comes out as the float pair the records keep; products
+// of FP32 inputs are exact, so integer geometry with w = 1 stays exact.  GB300's FP64
+// rate is low, FP32 is not.
 // ---------------------------------------------------------------------------
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ DF quick_two_sum(float a, float b)   // |a| >= |b|
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DF two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ DF df_add(DF x, DF y)
+{
+    const DF s = two_sum(x.hi, y.hi);
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+
+__device__ __forceinline__ DF df_mul(DF x, DF y)
+{
+    const DF p = two_prod(x.hi, y.hi);
+    return quick_two_sum(p.hi, __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo)));
+}
+
+__device__ __forceinline__ DF df_mul_f(DF x, float b)
+{
+    const DF p = two_prod(x.hi, b);
+    return quick_two_sum(p.hi, __fmaf_rn(x.lo, b, p.lo));
+}
+
+// 1 / w: the rounded reciprocal and one Newton correction from the exact residual
+__device__ __forceinline__ DF df_recip(DF w)
+{
+    const float r = __frcp_rn(w.hi);
+    const float e = __fmaf_rn(-w.lo, r, __fmaf_rn(-w.hi, r, 1.f));   // 1 - w r (w.hi r exact in the FMA)
+    return quick_two_sum(r, __fmul_rn(e, r));
+}
+
 __global__ void k_vertex(Globals g)
 {
     const ViewK &V = g.views[blockIdx.y];
@@ -20,31 +75,30 @@ __global__ void k_vertex(Globals g)
     bool bad = false;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M.nV; i += gridDim.x * blockDim.x) {
         const long long gi = M.vert_off + i;
-        const double p0 = (double)__ldg(g.pos + gi), p1 = (double)__ldg(g.pos + nvt + gi),
-                     p2 = (double)__ldg(g.pos + 2 * nvt + gi);
-        double c[4];
+        const float p0 = __ldg(g.pos + gi), p1 = __ldg(g.pos + nvt + gi), p2 = __ldg(g.pos + 2 * nvt + gi);
+        DF c[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const float *m = V.mvp + 4 * r;
-            c[r] = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)m[0], p0), __dmul_rn((double)m[1], p1)),
-                                       __dmul_rn((double)m[2], p2)),
-                             (double)m[3]);
+            c[r] = df_add(df_add(df_add(two_prod(m[0], p0), two_prod(m[1], p1)), two_prod(m[2], p2)), DF{m[3], 0.f});
         }
-        // one FP64 reciprocal, then products: within an FP64 ulp of the quotients, and
-        // exact where w = 1
-        const double iw = __ddiv_rn(1.0, c[3]);
-        const double X = __dmul_rn(__dmul_rn(__dadd_rn(__dmul_rn(c[0], iw), 1.0), 0.5), (double)V.W);
-        const double Y = __dmul_rn(__dmul_rn(__dadd_rn(__dmul_rn(c[1], iw), 1.0), 0.5), (double)V.H);
-        const double Z = __dmul_rn(c[2], iw);
+        const DF iw = df_recip(c[3]);
+        const DF X = df_mul_f(df_add(df_mul(c[0], iw), DF{1.f, 0.f}), 0.5f * (float)V.W);
+        const DF Y = df_mul_f(df_add(df_mul(c[1], iw), DF{1.f, 0.f}), 0.5f * (float)V.H);
+        const DF Z = df_mul(c[2], iw);
         VRec r;
-        r.xh = __double2float_rn(X);
-        r.xl = __double2float_rn(__dsub_rn(X, (double)r.xh));
-        r.yh = __double2float_rn(Y);
-        r.yl = __double2float_rn(__dsub_rn(Y, (double)r.yh));
-        r.z = __double2float_rn(Z);
-        r.iw = __double2float_rn(iw);
-        const bool fin = isfinite(X) && isfinite(Y) && isfinite(Z);
-        r.valid = (c[3] > 1e-6) && (Z >= 0.0) && (Z <= 1.0) && fin && fabs(X) < 1e30 && fabs(Y) < 1e30;
+        r.xh = X.hi;
+        r.xl = X.lo;
+        r.yh = Y.hi;
+        r.yl = Y.lo;
+        r.z = Z.hi;
+        r.iw = iw.hi;
+        const bool fin = isfinite(X.hi) && isfinite(Y.hi) && isfinite(Z.hi) && isfinite(X.lo) && isfinite(Y.lo);
+        // the signs of w - 1e-6, Z and 1 - Z from the pairs (hi carries the sign unless it is 0)
+        const bool w_pos = c[3].hi > 1e-6f || (c[3].hi == 1e-6f && c[3].lo > 0.f);
+        const bool z_ge0 = Z.hi > 0.f || (Z.hi == 0.f && Z.lo >= 0.f);
+        const bool z_le1 = Z.hi < 1.f || (Z.hi == 1.f && Z.lo <= 0.f);
+        r.valid = w_pos && z_ge0 && z_le1 && fin && fabsf(X.hi) < 1e30f && fabsf(Y.hi) < 1e30f;
         r.pad = 0;
         if (!(isfinite(p0) && isfinite(p1) && isfinite(p2))) bad = true;
         out[i] = r;
