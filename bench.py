@@ -185,6 +185,16 @@ def algorithmic_bytes(scene, K, backward, store_layers=True):
     return px * (16 + ids) + per_view + acc + tex_bytes + 2 * 16 * texels
 
 
+def kernel_source_hash(text):
+    """Hash of CUDA source with comments and whitespace removed: a comment edit keeps a
+    capture valid, any code change does not."""
+    import hashlib
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return hashlib.sha1(re.sub(r"\s+", "", text).encode()).hexdigest()[:16]
+
+
 def recorded_traffic(kernel, pixels):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled to
     `pixels`, or None when the kernel sources changed since the capture."""
@@ -195,8 +205,8 @@ def recorded_traffic(kernel, pixels):
     except OSError:
         return None
     csrc = os.path.join(ROOT, "paper_2204_01386_gb300", "csrc")
-    h = hashlib.sha1(open(os.path.join(csrc, "dressi_tile.cuh"), "rb").read() +
-                     open(os.path.join(csrc, "dressi_core.cuh"), "rb").read()).hexdigest()[:16]
+    h = kernel_source_hash(open(os.path.join(csrc, "dressi_tile.cuh")).read() +
+                           open(os.path.join(csrc, "dressi_core.cuh")).read())
     if rec.get("source_hash") != h or kernel not in rec:
         return None
     nbytes, npix = rec[kernel].split()

@@ -3,18 +3,18 @@
  *
  * HardSoftRas is the soft rasterizer of "Dressi: A Hardware-Agnostic
  * Differentiable Renderer with Reactive Shader Packing and Soft Rasterization"
- * (arXiv 2204.01386), Sec. 3.3.  One call renders (or back-propagates through)
+ * (arXiv 2204.01386), Sec. 3.4.  One call renders (or back-propagates through)
  * a ragged batch of views, each view showing one mesh of a packed scene:
  *
- *   transform and triangle setup      (Sec. 3.3.2; the render-graph listing's
+ *   transform and triangle setup      (Sec. 3.4.2; the render-graph listing's
  *                                      vertex transform and face lookup)
- *   per-tile binning of faces grown by r   (Enlarge(), Sec. 3.3.2)
+ *   per-tile binning of faces grown by r   (Enlarge(), Sec. 3.4.2)
  *   SignedDist, hard test, Shift, K-layer peel  (Alg. 2, Eq. Shift)
- *   perspective-correct interpolation, bilinear texture, shading  (Sec. 3.2.2, 3.3.3)
+ *   perspective-correct interpolation, bilinear texture, shading  (Sec. 3.3.2, 3.3.3)
  *   D_k = sigmoid(dist_k / sigma), edge mask E, colour and silhouette blend
- *                                      (the three blend equations of Sec. 3.3.3)
+ *                                      (the three blend equations of Sec. 3.4.3)
  *   adjoint of all of the above back to vertex positions, vertex colours and
- *   texels (Sec. 3.3: the gradient dL/dTheta by the chain rule).
+ *   texels (Sec. 3.4: the gradient dL/dTheta by the chain rule).
  *
  * Conventions shared by every entry point
  *   - Screen space: pixel (x, y) has its centre at (x + 1/2, y + 1/2); the
@@ -50,7 +50,7 @@ extern "C" {
 #endif
 
 #define DRESSI_ABI_VERSION 1
-#define DRESSI_MAX_K 5          /* the paper keeps K at most five (Sec. 3.3.2) */
+#define DRESSI_MAX_K 5          /* the paper keeps K at most five (Sec. 3.4.2) */
 #define DRESSI_MAX_VIEWS 65535
 #define DRESSI_MAX_MESHES 4096
 
@@ -103,7 +103,7 @@ typedef struct {
                            occupies pixels [pix_off, pix_off + width*height), row-major */
 } dressi_view;
 
-/* Soft-raster parameters (Sec. 3.3.2-3.3.3) and execution choices. */
+/* Soft-raster parameters (Sec. 3.4.2-3.3.3) and execution choices. */
 typedef struct {
     int32_t K;          /* peel layers, 1..DRESSI_MAX_K (Alg. 2) */
     float r;            /* blur radius: faces grow to reach r (Enlarge) */
@@ -129,7 +129,7 @@ typedef struct {
 DRESSI_API size_t dressi_workspace_size(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
                              const dressi_params *params);
 
-/* Forward pass (Alg. 2 and the blend equations of Sec. 3.3.3).
+/* Forward pass (Alg. 2 and the blend equations of Sec. 3.4.3).
      out_rgba   DEVICE [n_pix][4] float: colour I_c in rgb, silhouette I_s in alpha,
                 at the views' pixel offsets.  Pixels of no view are left untouched.
      layer_ids  DEVICE [K][n_pix] int32 or NULL: per peel layer, the face index (local to

@@ -3,7 +3,7 @@
  *
  * Plain, slow, brute-force restatement of the soft rasterizer of
  * "Dressi: A Hardware-Agnostic Differentiable Renderer with Reactive Shader
- * Packing and Soft Rasterization" (arXiv 2204.01386), Sec. 3.3, used to check
+ * Packing and Soft Rasterization" (arXiv 2204.01386), Sec. 3.4, used to check
  * the CUDA path.  Only tests/, __graft_entry__.smoke() and bench.py's CPU
  * baseline may load it; the product never does.  It shares no code, header or
  * constant with the CUDA library.
@@ -11,13 +11,13 @@
  * Everything is FP64.  Per view and per pixel centre p = (x + 1/2, y + 1/2)
  * (pixel units, y down) it evaluates every face and takes, in order:
  *   1. transform      clip = MVP (pos, 1); X = (x/w + 1)/2 W, Y = (y/w + 1)/2 H,
- *                     depth z/w (Eq. of f_render, Sec. 3.3.1; Vulkan clip space)
+ *                     depth z/w (Eq. of f_render, Sec. 3.4.1; Vulkan clip space)
  *   2. culling        a face is skipped when a corner has w <= 1e-6 or depth
  *                     outside [0, 1], or its screen area is zero (reading: the
  *                     paper does not clip; no back-face culling because depth
  *                     peeling must see occluded and back faces)
  *   3. SignedDist     Euclidean pixel-to-boundary distance, positive inside the
- *                     hard face (Sec. 3.3.2, Alg. 2).  Each edge is evaluated
+ *                     hard face (Sec. 3.4.2, Alg. 2).  Each edge is evaluated
  *                     from its lexicographically smaller endpoint so that two
  *                     faces sharing an edge or a vertex get identical values.
  *   4. Enlarge        a face is a candidate at p iff dist >= -r (reading of
@@ -27,14 +27,14 @@
  *   7. peel           the K smallest (key, face id) pairs (Alg. 2 outer loop)
  *   8. barycentrics   perspective correct; a soft fragment takes the barycentrics
  *                     of its closest point of the hard face (reading: soft faces
- *                     extend the hard face, Sec. 3.3.2)
+ *                     extend the hard face, Sec. 3.4.2)
  *   9. normals        area-weighted vertex normals (listing BuildNormalCompute)
  *  10. texture        bilinear, texel centres at i + 1/2, REPEAT wrap
  *  11. shading        vertex colour / unlit texture / texture * max(0, n.l)
- *  12. D_k = sigmoid(dist_k / sigma)                      (Sec. 3.3.3)
- *  13. S^H, edge mask E by a Chebyshev window of radius rho (Sec. 3.3.3)
+ *  12. D_k = sigmoid(dist_k / sigma)                      (Sec. 3.4.3)
+ *  13. S^H, edge mask E by a Chebyshev window of radius rho (Sec. 3.4.3)
  *  14-16. blend: I = E I^e + (1 - E) I^ne for colour and silhouette
- *                     (the three blend equations of Sec. 3.3.3)
+ *                     (the three blend equations of Sec. 3.4.3)
  * and the reverse-mode adjoint of 8-16 back to positions, colours, texels.
  * Distances handed to sigmoid and Shift are in normalised screen units:
  * pixel distance / max(W, H).

@@ -1,4 +1,4 @@
-"""GB300-native HardSoftRas (the soft rasterizer of arXiv 2204.01386, Sec. 3.3):
+"""GB300-native HardSoftRas (the soft rasterizer of arXiv 2204.01386, Sec. 3.4):
 forward and hand-written adjoint as CUDA kernels for sm_103a behind a C ABI
 (include/dressi.h), with a thin Python binding."""
 from .binding import DressiError, load  # noqa: F401

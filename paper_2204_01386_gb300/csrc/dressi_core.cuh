@@ -4,7 +4,7 @@
 //   * the vertex transform runs in FP64 with explicitly rounded operations, and
 //     each pixel-space corner is kept as an unevaluated float pair hi + lo, so
 //     that p - V is accurate to one float ulp of |p - V| (not of |V|): the
-//     sigmoid of Sec. 3.3.3 is steep (sigma is a fraction of a pixel), so the
+//     sigmoid of Sec. 3.4.3 is steep (sigma is a fraction of a pixel), so the
 //     distance must be accurate to ~1e-7 px even at 2048^2;
 //   * every geometric quantity of an edge is computed from its canonical
 //     (lexicographically smaller) endpoint, so two faces sharing an edge or a

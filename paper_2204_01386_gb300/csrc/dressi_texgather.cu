@@ -1,5 +1,5 @@
 // dressi_texgather.cu -- deterministic texel gradients: the texel-space gather
-// alternative to red.global atomics (Sec. 3.2.2: the gradients of the four texels a
+// alternative to red.global atomics (Sec. 3.3.2: the gradients of the four texels a
 // bilinear sample reads "should be summed up").
 //
 // The adjoint writes one record per (pixel, layer) into a slot fixed by the pixel:

@@ -15,7 +15,7 @@
 //      known without a second pass over the image;
 //   4. forward: each layer is re-evaluated, shaded (perspective-correct
 //      interpolation, bilinear texture, Lambert) and blended (D_k = sigmoid(dist/sigma),
-//      colour and silhouette equations of Sec. 3.3.3); adjoint: the same values are
+//      colour and silhouette equations of Sec. 3.4.3); adjoint: the same values are
 //      rebuilt and dL/dI is pushed back to the screen-space corners, vertex colours,
 //      vertex normals and texels.
 // With layer ids stored by the forward (mode 2), the adjoint skips steps 1-3: S^H of
@@ -156,7 +156,7 @@ struct PeelState {
 };
 
 // ---------------------------------------------------------------------------
-// per-layer shading (Sec. 3.2.2 texture sampling, Sec. 3.3.3 shading)
+// per-layer shading (Sec. 3.3.2 texture sampling, Sec. 3.4.3 shading)
 // ---------------------------------------------------------------------------
 struct Shade {
     int vi[3];
@@ -600,7 +600,7 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
     for (int k = 0; k < K; ++k) nl += (ids[k] != 0x7fffffff) ? 1 : 0;
     const bool SH = S.sh[(ly + rho) * hs + (lx + rho)] == 1;
 
-    // edge mask (Sec. 3.3.3): the window of radius rho sees both S^H = 0 and 1
+    // edge mask (Sec. 3.4.3): the window of radius rho sees both S^H = 0 and 1
     bool E = g.edge_mode == 1;
     if (g.edge_mode == 0) {
         unsigned long long a0 = 0ull, a1 = 0ull;

@@ -21,7 +21,7 @@ def _render(scene, **kw):
 
 
 # ----------------------------------------------------------------------------
-# fill rule (Sec. 3.3.2 hard faces; top-left rule is the reading for points on edges)
+# fill rule (Sec. 3.4.2 hard faces; top-left rule is the reading for points on edges)
 # ----------------------------------------------------------------------------
 
 @pytest.mark.parametrize("a", [1, 2, 5, 8, 13])
@@ -70,7 +70,7 @@ def test_closed_convex_mesh_two_hard_layers():
 
 
 # ----------------------------------------------------------------------------
-# SignedDist + sigmoid (Sec. 3.3.3): K = 1, E = 1 gives alpha = sigmoid(dist / sigma)
+# SignedDist + sigmoid (Sec. 3.4.3): K = 1, E = 1 gives alpha = sigmoid(dist / sigma)
 # ----------------------------------------------------------------------------
 
 def _boundary_distance(tri, pts, n=200001):
@@ -174,7 +174,7 @@ def test_two_layer_order_and_keys():
 
 
 # ----------------------------------------------------------------------------
-# edge mask (Sec. 3.3.3): window of radius rho around p sees both S^H = 0 and 1
+# edge mask (Sec. 3.4.3): window of radius rho around p sees both S^H = 0 and 1
 # ----------------------------------------------------------------------------
 
 @pytest.mark.parametrize("rho_px", [1, 2, 3])
