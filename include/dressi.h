@@ -49,7 +49,7 @@ extern "C" {
 #define DRESSI_API
 #endif
 
-#define DRESSI_ABI_VERSION 1
+#define DRESSI_ABI_VERSION 2   /* 2: layer ids carry the soft flag; dressi_forward_from_layers */
 #define DRESSI_MAX_K 5          /* the paper keeps K at most five (Sec. 3.4.2) */
 #define DRESSI_MAX_VIEWS 65535
 #define DRESSI_MAX_MESHES 4096
@@ -144,6 +144,25 @@ DRESSI_API size_t dressi_workspace_size(const dressi_scene *scene, const dressi_
 DRESSI_API int dressi_forward(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
                    const dressi_params *params, float *out_rgba, int32_t *layer_ids, int64_t n_pix,
                    void *ws, size_t ws_bytes, int32_t *dev_status, void *stream);
+
+/* Forward from stored layers: the cached-rasterization counterpart of the reactive cache
+   of Sec. 3.3.3 (Stage Packing), which skips passes whose inputs did not change -- here,
+   when the geometry and views are static (texture, colour or light optimisation), the
+   binning, raster and peel of Sec. 3.4.2 are skipped and only shading and blending
+   (Sec. 3.4.3) run on the layers an earlier dressi_forward stored.
+     layer_ids  DEVICE [K][n_pix] from dressi_forward with the same positions, faces,
+                views, K and r (same encoding; the hard flags give S^H).  Colours,
+                textures, shade_mode, the light, sigma, delta and edge_mode may differ;
+                the result then equals dressi_forward with the new values bit for bit.
+     out_rgba, n_pix, ws, ws_bytes, dev_status, stream as for dressi_forward (the
+                workspace size is the same).
+   Layer ids that do not match the scene give wrong images but no fault: a face index out
+   of its mesh's range makes that layer contribute nothing.
+   The adjoint of this call is dressi_backward with the same layer_ids. */
+DRESSI_API int dressi_forward_from_layers(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
+                                          const dressi_params *params, const int32_t *layer_ids, float *out_rgba,
+                                          int64_t n_pix, void *ws, size_t ws_bytes, int32_t *dev_status,
+                                          void *stream);
 
 /* Adjoint of dressi_forward for the pixel gradient grad_rgba = dL/d(out_rgba).
      grad_rgba  DEVICE [n_pix][4] float.

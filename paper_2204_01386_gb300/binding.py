@@ -44,6 +44,8 @@ class DressiParams(C.Structure):
 
 
 # every symbol declared in include/dressi.h, with its ctypes signature
+ABI_VERSION = 2   # DRESSI_ABI_VERSION of include/dressi.h
+
 SIGNATURES = {
     "dressi_workspace_size": (C.c_size_t, [C.POINTER(DressiScene), C.POINTER(DressiView), C.c_int32,
                                            C.POINTER(DressiParams)]),
@@ -52,6 +54,9 @@ SIGNATURES = {
     "dressi_backward": (C.c_int, [C.POINTER(DressiScene), C.POINTER(DressiView), C.c_int32, C.POINTER(DressiParams),
                                   C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
+    "dressi_forward_from_layers": (C.c_int, [C.POINTER(DressiScene), C.POINTER(DressiView), C.c_int32,
+                                             C.POINTER(DressiParams), C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                             C.c_size_t, C.c_void_p, C.c_void_p]),
     "dressi_forward_static_scratch": (C.c_int, [C.POINTER(DressiScene), C.POINTER(DressiView), C.c_int32,
                                                 C.POINTER(DressiParams), C.c_void_p, C.c_void_p, C.c_int64,
                                                 C.c_void_p, C.c_void_p]),
@@ -87,7 +92,7 @@ def load(path: str = LIB_PATH):
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
-            if lib.dressi_abi_version() != 1:
+            if lib.dressi_abi_version() != ABI_VERSION:
                 raise DressiError("libdressi.so ABI version mismatch")
             _lib = lib
     return _lib

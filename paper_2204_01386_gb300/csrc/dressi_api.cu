@@ -27,11 +27,14 @@ static cudaEvent_t g_prof[4] = {nullptr, nullptr, nullptr, nullptr};
 // optional device work counters of the per-tile kernel (statistics hook)
 static unsigned long long *g_stats = nullptr;
 
-static void launch_tile_profiled(const Globals &g, bool bwd, cudaStream_t s)
+// pass: 0 forward, 1 adjoint, 2 forward from stored layer ids (timed as a forward)
+static void launch_tile_profiled(const Globals &g, int pass, cudaStream_t s)
 {
+    const bool bwd = pass == 1;
     cudaEvent_t b = g_prof[bwd ? 2 : 0], e = g_prof[bwd ? 3 : 1];
     if (b) cudaEventRecord(b, s);
-    launch_tile(g, bwd, s);
+    if (pass == 2) launch_tile_shade(g, s);
+    else launch_tile(g, bwd, s);
     if (e) cudaEventRecord(e, s);
 }
 
@@ -293,7 +296,7 @@ static void run_setup(const Globals &g, const Plan &P, char *ws, bool need_bins,
 
 // the per-tile kernel, persistent (longest face list first when the lists exist) or
 // one CTA per tile
-static void run_tiles(Globals &g, const Plan &P, char *ws, bool bins_built, bool bwd, cudaStream_t s)
+static void run_tiles(Globals &g, const Plan &P, char *ws, bool bins_built, int pass, cudaStream_t s)
 {
     if (g.persistent) {
         cudaMemsetAsync(ws + P.lay.queue, 0, sizeof(int) * 4, s);
@@ -303,7 +306,7 @@ static void run_tiles(Globals &g, const Plan &P, char *ws, bool bins_built, bool
             launch_lpt_order(g, s);
         }
     }
-    launch_tile_profiled(g, bwd, s);
+    launch_tile_profiled(g, pass, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -402,7 +405,7 @@ int dressi_forward(const dressi_scene *scene, const dressi_view *views, int32_t 
     g.out = out_rgba;
     g.ids = layer_ids;
     run_setup(g, P, w, true, s);
-    run_tiles(g, P, w, true, false, s);
+    run_tiles(g, P, w, true, 0, s);
     return cudaGetLastError() == cudaSuccess ? DRESSI_OK : DRESSI_ERR_LAUNCH;
 }
 
@@ -418,6 +421,26 @@ int dressi_forward_static_scratch(const dressi_scene *scene, const dressi_view *
     if (!ws) return DRESSI_ERR_LAUNCH;
     return dressi_forward(scene, views, n_views, params, out_rgba, layer_ids, n_pix, ws,
                           (size_t)DRESSI_STATIC_SCRATCH_BYTES, dev_status, stream);
+}
+
+int dressi_forward_from_layers(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
+                               const dressi_params *params, const int32_t *layer_ids, float *out_rgba, int64_t n_pix,
+                               void *ws, size_t ws_bytes, int32_t *dev_status, void *stream)
+{
+    Plan P;
+    if (!layer_ids || !out_rgba || !dev_status || n_pix < 1) return DRESSI_ERR_ARG;
+    if (!make_plan(scene, views, n_views, params, n_pix, P)) return DRESSI_ERR_ARG;
+    if (!ws || ws_bytes < P.lay.total) return DRESSI_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaGetLastError();
+    char *w = static_cast<char *>(ws);
+    Globals g = make_globals(scene, params, P, w, n_pix, dev_status);
+    g.out = out_rgba;
+    g.ids_in = layer_ids;
+    // vertex records, face table and normals (shading needs them), no binning
+    run_setup(g, P, w, false, s);
+    run_tiles(g, P, w, false, 2, s);
+    return cudaGetLastError() == cudaSuccess ? DRESSI_OK : DRESSI_ERR_LAUNCH;
 }
 
 int dressi_backward(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
@@ -449,7 +472,7 @@ int dressi_backward(const dressi_scene *scene, const dressi_view *views, int32_t
     if (!gather) g.texgrad_mode = 0;
     if (gather) cudaMemsetAsync(w + P.lay.tg_keys, 0xff, sizeof(unsigned) * (size_t)P.lay.tg_slots, s);
     run_setup(g, P, w, layer_ids == nullptr, s);
-    run_tiles(g, P, w, layer_ids == nullptr, true, s);
+    run_tiles(g, P, w, layer_ids == nullptr, 1, s);
     if (gather)
         launch_tex_gather(g, P.lay.tg_slots, P.n_texels, (int)P.meshes.size(), P.max_texels, w + P.lay.tg_scratch,
                           ALIGN, s);

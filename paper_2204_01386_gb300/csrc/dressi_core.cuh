@@ -366,9 +366,9 @@ __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, 
 __device__ __forceinline__ void frag_lambda(const FaceRec &R, const Frag &fr, float lam[3])
 {
     if (fr.hard) {
-        lam[0] = fr.Fn[1] * R.invA;
-        lam[1] = fr.Fn[2] * R.invA;
-        lam[2] = fr.Fn[0] * R.invA;
+        lam[0] = fmul(fr.Fn[1], R.invA);
+        lam[1] = fmul(fr.Fn[2], R.invA);
+        lam[2] = fmul(fr.Fn[0], R.invA);
         return;
     }
     if (fr.feat >= 3) {
@@ -380,7 +380,7 @@ __device__ __forceinline__ void frag_lambda(const FaceRec &R, const Frag &fr, fl
     const bool sw = (R.flags >> (1 + i)) & 1;
     const int P = sw ? (i + 1) % 3 : i, Q = sw ? i : (i + 1) % 3;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) lam[j] = (j == P) ? 1.f - fr.t : ((j == Q) ? fr.t : 0.f);
+    for (int j = 0; j < 3; ++j) lam[j] = (j == P) ? fsub(1.f, fr.t) : ((j == Q) ? fr.t : 0.f);
 }
 
 // Hard test only (for S^H of halo pixels): true if p lies in the closed face under

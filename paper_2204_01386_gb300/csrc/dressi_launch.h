@@ -11,6 +11,7 @@ void launch_normals(const Globals &g, int n_meshes, int max_nf, int max_nv, cuda
 void launch_face(const Globals &g, int n_views, int max_nf, cudaStream_t s);
 void launch_bin(const Globals &g, int n_views, int max_nf, cudaStream_t s);
 void launch_tile(const Globals &g, bool backward, cudaStream_t s);
+void launch_tile_shade(const Globals &g, cudaStream_t s);
 void launch_lpt_order(const Globals &g, cudaStream_t s);
 size_t texgather_scratch_bytes(long long slots, long long n_texels, size_t align);
 void launch_scan_inplace(int *a, int n, int *partial, cudaStream_t s);

@@ -198,39 +198,41 @@ __device__ __forceinline__ void texcoord(const float b[3], const float u[3], flo
     float hi[3], lo[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        hi[i] = u[i] * Wt;
-        lo[i] = fmaf(u[i], Wt, -hi[i]);
+        hi[i] = fmul(u[i], Wt);
+        lo[i] = ffma(u[i], Wt, -hi[i]);
     }
     rel[0] = 0.f;
-    rel[1] = (hi[1] - hi[0]) + (lo[1] - lo[0]);
-    rel[2] = (hi[2] - hi[0]) + (lo[2] - lo[0]);
-    const float delta = fmaf(b[1], rel[1], fmaf(b[2], rel[2], lo[0]));
-    const float A = hi[0] - 0.5f;
+    rel[1] = fadd(fsub(hi[1], hi[0]), fsub(lo[1], lo[0]));
+    rel[2] = fadd(fsub(hi[2], hi[0]), fsub(lo[2], lo[0]));
+    const float delta = ffma(b[1], rel[1], ffma(b[2], rel[2], lo[0]));
+    const float A = fsub(hi[0], 0.5f);
     const float fA = floorf(A);
-    const float t = (A - fA) + delta;
+    const float t = fadd(fsub(A, fA), delta);
     const float ft = floorf(t);
-    f = t - ft;
+    f = fsub(t, ft);
     i0 = (int)fA + (int)ft;
 }
 
-// b, C, D and the sampling state of one layer from S.vi, S.iw, S.lam and dist
+// b, C, D and the sampling state of one layer from S.vi, S.iw, S.lam and dist.  Every
+// operation is rounded as written (no contraction left to the compiler), so the kernels
+// that shade a layer -- forward, forward from stored layers, adjoint -- agree bit for bit.
 __device__ __forceinline__ void shade(const Globals &g, const ViewK &V, const MeshK &M, float dist, Shade &S)
 {
     float q[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) q[i] = S.lam[i] * S.iw[i];
-    S.Q = q[0] + q[1] + q[2];
-    const float iQ = 1.f / S.Q;
+    for (int i = 0; i < 3; ++i) q[i] = fmul(S.lam[i], S.iw[i]);
+    S.Q = fadd(fadd(q[0], q[1]), q[2]);
+    const float iQ = __fdiv_rn(1.f, S.Q);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) S.b[i] = q[i] * iQ;
-    S.D = sigmoidf_stable(dist * V.inv_sigma_px);
+    for (int i = 0; i < 3; ++i) S.b[i] = fmul(q[i], iQ);
+    S.D = sigmoidf_stable(fmul(dist, V.inv_sigma_px));
     const long long nvt = g.n_verts_total;
     if (g.shade_mode == 0) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             float a = 0.f;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) a = fmaf(S.b[i], __ldg(g.col + c * nvt + M.vert_off + S.vi[i]), a);
+            for (int i = 0; i < 3; ++i) a = ffma(S.b[i], __ldg(g.col + c * nvt + M.vert_off + S.vi[i]), a);
             S.C[c] = a;
         }
         return;
@@ -251,11 +253,11 @@ __device__ __forceinline__ void shade(const Globals &g, const ViewK &V, const Me
     const float4 t10 = load_texel(g, tb + (long long)S.iy[0] * M.tex_w + S.ix[1]);
     const float4 t01 = load_texel(g, tb + (long long)S.iy[1] * M.tex_w + S.ix[0]);
     const float4 t11 = load_texel(g, tb + (long long)S.iy[1] * M.tex_w + S.ix[1]);
-    const float w00 = (1.f - S.fx) * (1.f - S.fy), w10 = S.fx * (1.f - S.fy), w01 = (1.f - S.fx) * S.fy,
-                w11 = S.fx * S.fy;
-    S.A[0] = w00 * t00.x + w10 * t10.x + w01 * t01.x + w11 * t11.x;
-    S.A[1] = w00 * t00.y + w10 * t10.y + w01 * t01.y + w11 * t11.y;
-    S.A[2] = w00 * t00.z + w10 * t10.z + w01 * t01.z + w11 * t11.z;
+    const float gx = fsub(1.f, S.fx), gy = fsub(1.f, S.fy);
+    const float w00 = fmul(gx, gy), w10 = fmul(S.fx, gy), w01 = fmul(gx, S.fy), w11 = fmul(S.fx, S.fy);
+    S.A[0] = ffma(w11, t11.x, ffma(w01, t01.x, ffma(w10, t10.x, fmul(w00, t00.x))));
+    S.A[1] = ffma(w11, t11.y, ffma(w01, t01.y, ffma(w10, t10.y, fmul(w00, t00.y))));
+    S.A[2] = ffma(w11, t11.z, ffma(w01, t01.z, ffma(w10, t10.z, fmul(w00, t00.z))));
     if (g.shade_mode == 1) {
         S.C[0] = S.A[0]; S.C[1] = S.A[1]; S.C[2] = S.A[2];
         return;
@@ -264,16 +266,16 @@ __device__ __forceinline__ void shade(const Globals &g, const ViewK &V, const Me
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const float4 nv = g.nrm[M.vert_off + S.vi[i]];
-        m[0] = fmaf(S.b[i], nv.x, m[0]);
-        m[1] = fmaf(S.b[i], nv.y, m[1]);
-        m[2] = fmaf(S.b[i], nv.z, m[2]);
+        m[0] = ffma(S.b[i], nv.x, m[0]);
+        m[1] = ffma(S.b[i], nv.y, m[1]);
+        m[2] = ffma(S.b[i], nv.z, m[2]);
     }
-    S.mlen = sqrtf(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
-    const float il = S.mlen > 0.f ? 1.f / S.mlen : 0.f;
-    S.n[0] = m[0] * il; S.n[1] = m[1] * il; S.n[2] = m[2] * il;
-    S.ndl = S.n[0] * V.light[0] + S.n[1] * V.light[1] + S.n[2] * V.light[2];
+    S.mlen = __fsqrt_rn(ffma(m[0], m[0], ffma(m[1], m[1], fmul(m[2], m[2]))));
+    const float il = S.mlen > 0.f ? __fdiv_rn(1.f, S.mlen) : 0.f;
+    S.n[0] = fmul(m[0], il); S.n[1] = fmul(m[1], il); S.n[2] = fmul(m[2], il);
+    S.ndl = ffma(S.n[2], V.light[2], ffma(S.n[1], V.light[1], fmul(S.n[0], V.light[0])));
     const float sl = fmaxf(S.ndl, 0.f);
-    S.C[0] = S.A[0] * sl; S.C[1] = S.A[1] * sl; S.C[2] = S.A[2] * sl;
+    S.C[0] = fmul(S.A[0], sl); S.C[1] = fmul(S.A[1], sl); S.C[2] = fmul(S.A[2], sl);
 }
 
 // a layer rebuilt from its face id (adjoint): record, fragment, shading
@@ -491,9 +493,9 @@ struct Smem {
     int qn[2];           // queue fill of the current batch, by batch parity
     unsigned long long m0[HS_MAX], m1[HS_MAX];   // per halo row: columns with S^H = 0 / 1
     unsigned char sh[HS_MAX * HS_MAX];
-    // the raster (forward and re-rasterizing adjoint) only: the adjoint from stored ids
-    // is launched with the shared memory up to F, leaving the rest of the SM's unified
-    // L1 / shared storage to the L1 cache
+    // the raster (forward and re-rasterizing adjoint) only: the modes from stored layer
+    // ids are launched with the shared memory up to F, leaving the rest of the SM's
+    // unified L1 / shared storage to the L1 cache
     FaceRec F[CH];
     Pre P[CH];
     int rect[CH];        // tile pairs: x0 | y0 << 8 | w << 16 | h << 24 (tile-local, x0/y0 >= 0)
@@ -644,17 +646,17 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
 #pragma unroll
             for (int i = 0; i < 3; ++i) { Sh.vi[i] = R.vi[i]; Sh.iw[i] = R.iw[i]; }
             shade(g, V, M, fr.dist, Sh);
-            Cs[0] = fmaf(Sh.D, Sh.C[0], Cs[0]);
-            Cs[1] = fmaf(Sh.D, Sh.C[1], Cs[1]);
-            Cs[2] = fmaf(Sh.D, Sh.C[2], Cs[2]);
-            Ds += Sh.D;
-            prod *= 1.f - Sh.D;
+            Cs[0] = ffma(Sh.D, Sh.C[0], Cs[0]);
+            Cs[1] = ffma(Sh.D, Sh.C[1], Cs[1]);
+            Cs[2] = ffma(Sh.D, Sh.C[2], Cs[2]);
+            Ds = fadd(Ds, Sh.D);
+            prod = fmul(prod, fsub(1.f, Sh.D));
             if (k == 0) { C1[0] = Sh.C[0]; C1[1] = Sh.C[1]; C1[2] = Sh.C[2]; }
         }
         float4 o;
         if (E) {
-            const float iD = Ds > 0.f ? 1.f / Ds : 0.f;
-            o = make_float4(Cs[0] * iD, Cs[1] * iD, Cs[2] * iD, 1.f - prod);
+            const float iD = Ds > 0.f ? __fdiv_rn(1.f, Ds) : 0.f;
+            o = make_float4(fmul(Cs[0], iD), fmul(Cs[1], iD), fmul(Cs[2], iD), fsub(1.f, prod));
         } else {
             o = SH ? make_float4(C1[0], C1[1], C1[2], 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -730,7 +732,8 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
 }
 
 // everything one CTA does for global tile t.  MODE: 0 forward, 1 adjoint that
-// re-rasterizes, 2 adjoint from stored layer ids
+// re-rasterizes, 2 adjoint from stored layer ids, 3 forward from stored layer ids
+// (re-shading a static geometry: no binning, raster or peel)
 template <int K, int MODE, int TT>
 __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned long long *kbuf, const int t)
 {
@@ -758,11 +761,10 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
         const int hx = X0 - rho + i % hs, hy = Y0 - rho + i / hs;
         S.sh[i] = (hx >= 0 && hy >= 0 && hx < V.W && hy < V.H) ? 0 : 2;
     }
-    if (MODE != 2)
+    constexpr bool BWD = MODE == 1 || MODE == 2;
+    constexpr bool from_ids = MODE == 2 || MODE == 3;
+    if (!from_ids)
         for (int i = tid; i < TT * TT * K; i += NT) kbuf[i] = EMPTY;
-
-    constexpr bool BWD = MODE != 0;
-    constexpr bool from_ids = MODE == 2;
     bool single_chunk = false;
     unsigned n_pairs = 0, n_exact = 0, n_cand = 0, n_layers = 0;
     int batch = 0;   // candidate-queue batches so far (selects the queue counter)
@@ -1043,7 +1045,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
 // the raster and the adjoint state: four with 16 px tiles, three with 32 px tiles (whose
 // K-lists limit the shared memory to three CTAs anyway).
 template <int MODE, int TT>
-constexpr int tile_min_ctas() { return MODE == 0 ? 4 : MODE == 2 ? 3 : (TT == 16 ? 4 : 3); }
+constexpr int tile_min_ctas() { return MODE == 0 || MODE == 3 ? 4 : MODE == 2 ? 3 : (TT == 16 ? 4 : 3); }
 
 template <int K, int MODE, int TT>
 __global__ void __launch_bounds__(NT, tile_min_ctas<MODE, TT>()) k_tile(Globals g)
@@ -1076,9 +1078,9 @@ __global__ void __launch_bounds__(NT, tile_min_ctas<MODE, TT>()) k_tile_persiste
 template <int K, int MODE, int TT>
 constexpr size_t tile_smem_bytes()
 {
-    // the adjoint from stored ids: the first part of Smem; otherwise Smem, the K-lists,
+    // from stored ids: the first part of Smem; otherwise Smem, the K-lists,
     // the candidate queue, the two pair-block tables
-    return MODE == 2 ? offsetof(Smem, F)
+    return MODE == 2 || MODE == 3 ? offsetof(Smem, F)
                      : sizeof(Smem) + sizeof(unsigned long long) * TT * TT * K + sizeof(unsigned) * QN + 2 * NBLK;
 }
 // four forward CTAs of the default configuration (K = 3, 16 px tiles) per SM: 228 KB of
@@ -1124,7 +1126,8 @@ static void launch_k(const Globals &g, cudaStream_t s)
 }
 
 // the per-tile kernel of one mode (0 forward, 1 adjoint re-rasterizing, 2 adjoint from
-// stored layer ids); instantiated by that mode's translation unit
+// stored layer ids, 3 forward from stored layer ids); instantiated by that mode's
+// translation unit
 template <int MODE>
 void launch_tile_mode(const Globals &g, cudaStream_t s)
 {

@@ -214,6 +214,21 @@ class Renderer:
         B.check(code, "dressi_forward")
         return out, ids
 
+    def forward_from_layers(self, ids: torch.Tensor, out: Optional[torch.Tensor] = None, pos=None, col=None,
+                            tex=None):
+        """Re-shades the layers ``ids`` stored by an earlier ``forward`` of the same
+        geometry and views (skips binning, raster and peel); colours, textures, light
+        and the blend parameters may have changed."""
+        dev = self.scene.device
+        if out is None:
+            out = torch.empty(self.n_pix, 4, dtype=torch.float32, device=dev)
+        sc = self.scene.c_struct(pos, col, tex)
+        code = self.lib.dressi_forward_from_layers(C.byref(sc), self.views, self.n_views, C.byref(self.params),
+                                                   ids.data_ptr(), out.data_ptr(), self.n_pix, self.ws.data_ptr(),
+                                                   self.ws_bytes, self.status.data_ptr(), self._stream())
+        B.check(code, "dressi_forward_from_layers")
+        return out
+
     def backward(self, grad_rgba: torch.Tensor, ids: Optional[torch.Tensor] = None, grad_pos=None, grad_col=None,
                  grad_tex=None, pos=None, col=None, tex=None):
         dev = self.scene.device

@@ -135,7 +135,7 @@ def test_status_strings(lib):
         assert lib.dressi_status_string(c)
     for b in (0, 1, 2, 4):
         assert lib.dressi_dev_status_string(b)
-    assert lib.dressi_abi_version() == 1
+    assert lib.dressi_abi_version() == B.ABI_VERSION == 2
 
 
 def test_product_has_no_fallback(monkeypatch, tmp_path):
