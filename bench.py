@@ -399,6 +399,43 @@ def ours(args, rank, world, local_rank):
                  "note": "one forward/loss/adjoint call per view, one CTA per tile, no graph"}
         del rv
 
+    # 3b) the same step with a static geometry (texture / colour optimisation): the
+    #     forward re-shades the layers the benchmark's forward stored (binning, raster and
+    #     peel skipped), then the loss and the adjoint from the same layers
+    cached = None
+    if store and world == 1 and not args.no_cached:
+        ids0 = ids.clone()
+
+        def cached_step():
+            r.forward_from_layers(ids0, out=out)
+            loss.zero_()
+            r.l2_grad(out, target, grad, loss)
+            r.backward(grad, ids=ids0, grad_pos=gp, grad_tex=gt)
+
+        for _ in range(2):
+            cached_step()
+        torch.cuda.synchronize()
+        crun = cached_step
+        if use_graph:
+            cgc = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(cgc):
+                cached_step()
+            cgc.replay()
+            torch.cuda.synchronize()
+            crun = cgc.replay
+        n_c = max(3, args.steps // 2)
+        ce = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_c)]
+        for k in range(n_c):
+            flush.fill_(float(k))
+            ce[k][0].record(stream)
+            crun()
+            ce[k][1].record(stream)
+        torch.cuda.synchronize()
+        cms = sum(a.elapsed_time(b) for a, b in ce)
+        cached = {"value": s.pixels * n_c / (cms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": cms / n_c,
+                  "note": "static geometry: forward from the stored layers (no binning, raster or peel) + loss "
+                          "+ adjoint from the same layers, CUDA graph"}
+
     # 4) end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -452,7 +489,8 @@ def ours(args, rank, world, local_rank):
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(launches_per_step * args.steps), "clocks": clock_info, "plain_per_view": plain}
+                "gpu_launches": int(launches_per_step * args.steps), "clocks": clock_info, "plain_per_view": plain,
+                "cached_geometry": cached}
         print(json.dumps(line), flush=True)
 
 
@@ -471,6 +509,7 @@ def main():
                     help="screen tile edge in pixels (0: chosen by the autotuner)")
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 1, 2],
                     help="per-tile kernel: 1 one CTA per tile, 2 persistent longest-first (0: autotuner)")
+    ap.add_argument("--no-cached", action="store_true", help="skip the static-geometry (cached layers) step")
     ap.add_argument("--workload", default="multiview", choices=WORKLOADS)
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--texgrad", type=int, default=0, choices=[0, 1],
