@@ -77,6 +77,10 @@ def _load():
             lib.orc_backward.argtypes = [C.POINTER(_View), C.POINTER(_Params), C.POINTER(_Window),
                                          C.POINTER(C.c_double), C.POINTER(C.c_double),
                                          C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            lib.orc_backward_ex.argtypes = [C.POINTER(_View), C.POINTER(_Params), C.POINTER(_Window),
+                                            C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double), C.POINTER(C.c_double)]
             _lib = lib
     return _lib
 
@@ -164,10 +168,12 @@ def render(mesh, view, params, window=None, brute_force=False):
     return res
 
 
-def backward(mesh, view, params, grad_rgba, window=None, brute_force=False):
+def backward(mesh, view, params, grad_rgba, window=None, brute_force=False, camera=False):
     """Adjoint of ``render`` for dL/d(rgba) = ``grad_rgba [h,w,4]`` over ``window``.
 
-    Returns ``(grad_pos [V,3], grad_col [V,3] or None, grad_tex [Ht,Wt,4] or None)``.
+    Returns ``(grad_pos [V,3], grad_col [V,3] or None, grad_tex [Ht,Wt,4] or None)``,
+    and with ``camera`` also ``grad_mvp [16]`` (row-major, as ``view.mvp``) and
+    ``grad_light [3]`` (Sec. 3.4.1: the camera and light parameters of Theta).
     """
     lib = _load()
     inp = _Inputs(mesh, view, params, brute_force)
@@ -176,10 +182,13 @@ def backward(mesh, view, params, grad_rgba, window=None, brute_force=False):
     gp = np.zeros_like(inp.pos)
     gc = np.zeros_like(inp.pos) if inp.col is not None else None
     gt = np.zeros_like(inp.tex) if inp.tex is not None else None
-    st = lib.orc_backward(C.byref(inp.view), C.byref(inp.params), C.byref(win), _dp(g), _dp(gp), _dp(gc), _dp(gt))
+    gm = np.zeros(16) if camera else None
+    gl = np.zeros(3) if camera else None
+    st = lib.orc_backward_ex(C.byref(inp.view), C.byref(inp.params), C.byref(win), _dp(g), _dp(gp), _dp(gc),
+                             _dp(gt), _dp(gm), _dp(gl))
     if st & 1:
         raise ValueError("oracle: invalid argument")
-    return gp, gc, gt
+    return (gp, gc, gt, gm, gl) if camera else (gp, gc, gt)
 
 
 def render_scene(scene, windows=None, brute_force=False):

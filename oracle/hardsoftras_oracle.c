@@ -696,8 +696,13 @@ static void tex_backward(const orc_view *v, const shade_t *s, const double gA[3]
     guv[1] = gy * v->tex_h;
 }
 
-int orc_backward(const orc_view *v, const orc_params *prm, const orc_window *w,
-                 const double *grad_rgba, double *grad_pos, double *grad_col, double *grad_tex)
+/* The adjoint also gives the gradients of the camera and the light, the parameters
+   theta_C and theta_L of Theta (Sec. 3.4.1): grad_mvp [16] (row-major, as mvp; the
+   depth row stays 0, depth only enters the discrete Shift keys) and grad_light [3]
+   (the light treated as a free 3-vector, as the forward uses it).  Either may be NULL. */
+int orc_backward_ex(const orc_view *v, const orc_params *prm, const orc_window *w,
+                    const double *grad_rgba, double *grad_pos, double *grad_col, double *grad_tex,
+                    double *grad_mvp, double *grad_light)
 {
     if (!check_args(v, prm, w) || !grad_rgba) return ORC_BAD_ARG;
     ctx_t c;
@@ -770,6 +775,9 @@ int orc_backward(const orc_view *v, const orc_params *prm, const orc_window *w,
                         double gs = 0;
                         for (int ch = 0; ch < 3; ++ch) { gA[ch] = gC[k][ch] * lam; gs += gC[k][ch] * sk->albedo[ch]; }
                         if (sk->ndl > 0 && sk->mlen > 0) {
+                            /* C = albedo max(0, n.l): dL/dl = (sum_c gC_c albedo_c) n */
+                            if (grad_light)
+                                for (int ch = 0; ch < 3; ++ch) grad_light[ch] += gs * sk->n[ch];
                             double gn[3] = {gs * v->light[0], gs * v->light[1], gs * v->light[2]};
                             double nd = sk->n[0] * gn[0] + sk->n[1] * gn[1] + sk->n[2] * gn[2];
                             double gm[3];
@@ -797,8 +805,8 @@ int orc_backward(const orc_view *v, const orc_params *prm, const orc_window *w,
                 lam_grad(t, fr, px, py, glam, cg);
             }
         }
-    /* corners -> clip -> object-space positions */
-    if (grad_pos) {
+    /* corners -> clip -> object-space positions and the matrix */
+    if (grad_pos || grad_mvp) {
         for (int f = 0; f < v->n_faces; ++f) {
             const face_t *t = &c.F[f];
             if (!t->live) continue;
@@ -816,13 +824,23 @@ int orc_backward(const orc_view *v, const orc_params *prm, const orc_window *w,
                 double gcw = -CG[f].X[j] * 0.5 * v->width * cl[0] / (cw * cw)
                              - CG[f].Y[j] * 0.5 * v->height * cl[1] / (cw * cw)
                              - CG[f].IW[j] / (cw * cw);
-                for (int col = 0; col < 3; ++col)
-                    grad_pos[3 * (size_t)vi + col] += v->mvp[0 * 4 + col] * gcx + v->mvp[1 * 4 + col] * gcy +
-                                                      v->mvp[3 * 4 + col] * gcw;
+                if (grad_pos)
+                    for (int col = 0; col < 3; ++col)
+                        grad_pos[3 * (size_t)vi + col] += v->mvp[0 * 4 + col] * gcx + v->mvp[1 * 4 + col] * gcy +
+                                                          v->mvp[3 * 4 + col] * gcw;
+                if (grad_mvp) {
+                    /* clip_r = sum_c mvp[r][c] (p, 1)_c */
+                    const double ph[4] = {p[0], p[1], p[2], 1.0};
+                    for (int col = 0; col < 4; ++col) {
+                        grad_mvp[0 * 4 + col] += gcx * ph[col];
+                        grad_mvp[1 * 4 + col] += gcy * ph[col];
+                        grad_mvp[3 * 4 + col] += gcw * ph[col];
+                    }
+                }
             }
         }
         /* normals -> positions: n_v = m_v / |m_v|, m_v = sum of face cross products */
-        if (prm->shade_mode == 2) {
+        if (grad_pos && prm->shade_mode == 2) {
             double *gM = (double *)calloc(3 * (size_t)(v->n_verts > 0 ? v->n_verts : 1), sizeof(double));
             for (int i = 0; i < v->n_verts; ++i) {
                 const double *m = c.Mn + 3 * i, *n = c.N + 3 * i, *gn = gN + 3 * i;
@@ -857,6 +875,12 @@ int orc_backward(const orc_view *v, const orc_params *prm, const orc_window *w,
     int st = c.status;
     ctx_free(&c);
     return st;
+}
+
+int orc_backward(const orc_view *v, const orc_params *prm, const orc_window *w,
+                 const double *grad_rgba, double *grad_pos, double *grad_col, double *grad_tex)
+{
+    return orc_backward_ex(v, prm, w, grad_rgba, grad_pos, grad_col, grad_tex, NULL, NULL);
 }
 
 /* size of the structs, so the Python loader can verify its layout */

@@ -443,6 +443,54 @@ def test_adjoint_matches_central_differences(shade_mode, edge_mode, K):
     assert np.abs(num - ana).max() < 1e-5 * np.abs(ana).max()
 
 
+@pytest.mark.parametrize("shade_mode,edge_mode,K", [(0, 0, 3), (1, 1, 2), (2, 0, 3), (2, 1, 2), (2, 2, 1)])
+def test_camera_and_light_adjoint_match_central_differences(shade_mode, edge_mode, K):
+    """dL/dMVP and dL/dlight (the camera and light parameters of Theta, Sec. 3.4.1)
+    against central differences of the oracle's forward; the depth row of the matrix
+    has no gradient (depth only orders the layers), nor has the light without Lambert."""
+    mesh, view = _fd_scene(shade_mode, 17 + shade_mode)
+    r_px = 3.0
+    prm = synth.Params(K=K, r=r_px / 28, sigma=r_px / 28 / 5, delta=2 / 28, edge_mode=edge_mode, shade_mode=shade_mode)
+    g = np.random.default_rng(9).normal(size=(28, 28, 4))
+    st0 = _state(oracle.render(mesh, view, prm))
+    _, _, _, gm, gl = oracle.backward(mesh, view, prm, g, camera=True)
+
+    def fd(attr, idx, h):
+        arr = np.asarray(getattr(view, attr), np.float64)
+        plus, minus = arr.copy(), arr.copy()
+        plus[idx] += h
+        minus[idx] -= h
+        vp = synth.View(**{**view.__dict__, attr: plus})
+        vm = synth.View(**{**view.__dict__, attr: minus})
+        rp, rm = oracle.render(mesh, vp, prm), oracle.render(mesh, vm, prm)
+        if _state(rp) != st0 or _state(rm) != st0:
+            return None
+        return ((g * rp["rgba"]).sum() - (g * rm["rgba"]).sum()) / (2 * h)
+
+    num, ana = [], []
+    for e in range(16):
+        d = fd("mvp", e, 1e-6)
+        if d is not None:
+            num.append(d)
+            ana.append(gm[e])
+    assert len(num) >= 12
+    assert np.all(gm[8:12] == 0)
+    for c in range(3):
+        d = fd("light", c, 1e-6)
+        if d is not None:
+            num.append(d)
+            ana.append(gl[c])
+    if shade_mode != 2:
+        assert np.all(gl == 0)
+    else:
+        assert np.abs(gl).max() > 0
+    num, ana = np.array(num), np.array(ana)
+    assert np.abs(ana).max() > 0
+    err = np.linalg.norm(num - ana) / np.linalg.norm(ana)
+    assert err < 1e-6, err
+    assert np.abs(num - ana).max() < 1e-5 * np.abs(ana).max()
+
+
 # ----------------------------------------------------------------------------
 # brute force equals the bbox pre-tested variant bit for bit
 # ----------------------------------------------------------------------------
