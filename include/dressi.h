@@ -49,7 +49,8 @@ extern "C" {
 #define DRESSI_API
 #endif
 
-#define DRESSI_ABI_VERSION 2   /* 2: layer ids carry the soft flag; dressi_forward_from_layers */
+#define DRESSI_ABI_VERSION 2   /* 2: layer ids carry the soft flag; dressi_forward_from_layers,
+                                  dressi_backward_ex */
 #define DRESSI_MAX_K 5          /* the paper keeps K at most five (Sec. 3.4.2) */
 #define DRESSI_MAX_VIEWS 65535
 #define DRESSI_MAX_MESHES 4096
@@ -177,6 +178,20 @@ DRESSI_API int dressi_backward(const dressi_scene *scene, const dressi_view *vie
                     const dressi_params *params, const float *grad_rgba, const int32_t *layer_ids,
                     int64_t n_pix, float *grad_pos, float *grad_col, float *grad_tex,
                     void *ws, size_t ws_bytes, int32_t *dev_status, void *stream);
+
+/* dressi_backward that also returns the gradients of the camera and the light, the
+   parameters theta_C and theta_L of Theta (Sec. 3.4.1):
+     grad_mvp   DEVICE [n_views][16] float or NULL, OVERWRITTEN with dL/dMVP per view
+                (row-major like dressi_view.mvp; row 2, the depth row, stays 0: depth only
+                orders the layers, a discrete choice).
+     grad_light DEVICE [n_views][3] float or NULL, OVERWRITTEN with dL/dlight per view
+                (shade_mode 2; the light is used as given, not renormalised; 0 otherwise).
+   All other arguments as for dressi_backward, which is this call with both NULL. */
+DRESSI_API int dressi_backward_ex(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
+                                  const dressi_params *params, const float *grad_rgba, const int32_t *layer_ids,
+                                  int64_t n_pix, float *grad_pos, float *grad_col, float *grad_tex,
+                                  float *grad_mvp, float *grad_light, void *ws, size_t ws_bytes,
+                                  int32_t *dev_status, void *stream);
 
 /* Size of the library's static device scratch array used by
    dressi_forward_static_scratch (bytes; held on every GPU that loads the library). */

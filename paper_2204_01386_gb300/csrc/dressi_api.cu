@@ -448,6 +448,15 @@ int dressi_backward(const dressi_scene *scene, const dressi_view *views, int32_t
                     float *grad_pos, float *grad_col, float *grad_tex, void *ws, size_t ws_bytes,
                     int32_t *dev_status, void *stream)
 {
+    return dressi_backward_ex(scene, views, n_views, params, grad_rgba, layer_ids, n_pix, grad_pos, grad_col, grad_tex,
+                              nullptr, nullptr, ws, ws_bytes, dev_status, stream);
+}
+
+int dressi_backward_ex(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
+                       const dressi_params *params, const float *grad_rgba, const int32_t *layer_ids, int64_t n_pix,
+                       float *grad_pos, float *grad_col, float *grad_tex, float *grad_mvp, float *grad_light,
+                       void *ws, size_t ws_bytes, int32_t *dev_status, void *stream)
+{
     Plan P;
     if (!grad_rgba || !grad_pos || !dev_status || n_pix < 1) return DRESSI_ERR_ARG;
     if (!make_plan(scene, views, n_views, params, n_pix, P)) return DRESSI_ERR_ARG;
@@ -461,6 +470,10 @@ int dressi_backward(const dressi_scene *scene, const dressi_view *views, int32_t
     g.gpos = grad_pos;
     g.gcol = params->shade_mode == 0 ? grad_col : nullptr;
     g.gtex = params->shade_mode != 0 ? grad_tex : nullptr;
+    g.gmvp = grad_mvp;
+    g.glight = grad_light;
+    if (grad_mvp) cudaMemsetAsync(grad_mvp, 0, sizeof(float) * 16 * (size_t)n_views, s);
+    if (grad_light) cudaMemsetAsync(grad_light, 0, sizeof(float) * 3 * (size_t)n_views, s);
     const long long nvt = scene->n_verts_total;
     cudaMemsetAsync(grad_pos, 0, sizeof(float) * 3 * (size_t)nvt, s);
     if (grad_col) cudaMemsetAsync(grad_col, 0, sizeof(float) * 3 * (size_t)nvt, s);

@@ -121,6 +121,8 @@ struct Globals {
     float4 *sgrad;        // per (view, vertex): dX, dY, d(1/w)
     float4 *ngrad;        // [n_verts_total] gradient of the normalized vertex normals
     float *gpos, *gcol, *gtex;
+    float *gmvp;          // [n_views][16] dL/dMVP or nullptr
+    float *glight;        // [n_views][3] dL/dlight or nullptr
     // texel-space gather of the texture gradient (texgrad_mode 1): one record per
     // (pixel, layer) at slot (slot_base + pixel) * K + layer
     unsigned long long *stats;  // optional work counters (see dressi_set_stats_buffer) or nullptr

@@ -299,6 +299,11 @@ __global__ void k_vertex_bwd(Globals g)
     const MeshK &M = g.meshes[V.mesh];
     const float4 *sg = g.sgrad + V.vrec_off;
     const long long nvt = g.n_verts_total;
+    // dL/dMVP of this view: dL/dclip_r (p, 1)_c for the x, y and w rows (depth only
+    // orders the layers and has no gradient)
+    float am[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) am[q] = 0.f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M.nV; i += gridDim.x * blockDim.x) {
         float4 s = sg[i];
         if (s.x == 0.f && s.y == 0.f && s.z == 0.f) continue;
@@ -318,6 +323,25 @@ __global__ void k_vertex_bwd(Globals g)
         for (int col = 0; col < 3; ++col) {
             float gp = V.mvp[col] * gcx + V.mvp[4 + col] * gcy + V.mvp[12 + col] * gcw;
             atomicAdd(g.gpos + col * nvt + gi, gp);
+        }
+        if (g.gmvp) {
+            const float ph[4] = {p[0], p[1], p[2], 1.f};
+#pragma unroll
+            for (int col = 0; col < 4; ++col) {
+                am[col] = fmaf(gcx, ph[col], am[col]);
+                am[4 + col] = fmaf(gcy, ph[col], am[4 + col]);
+                am[8 + col] = fmaf(gcw, ph[col], am[8 + col]);
+            }
+        }
+    }
+    if (g.gmvp) {
+        float *out = g.gmvp + 16 * (long long)blockIdx.y;
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            float v = am[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0 && v != 0.f) atomicAdd(out + (q < 8 ? q : q + 4), v);
         }
     }
 }

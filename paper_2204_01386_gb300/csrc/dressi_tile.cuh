@@ -300,8 +300,10 @@ __device__ __forceinline__ bool layer_build(const Globals &g, const ViewK &V, co
 // ---------------------------------------------------------------------------
 // adjoint of one layer: gC = dL/dC_k, gD = dL/dD_k
 // ---------------------------------------------------------------------------
+// gl: this thread's dL/dlight accumulator, or nullptr
 __device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, const MeshK &M, const Layer &L,
-                                              float px, float py, const float gC[3], float gD, long long slot)
+                                              float px, float py, const float gC[3], float gD, long long slot,
+                                              float *gl)
 {
     const long long nvt = g.n_verts_total;
     const FaceRec &R = L.R;
@@ -368,6 +370,12 @@ __device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, 
                 gA[0] = gC[0] * sl; gA[1] = gC[1] * sl; gA[2] = gC[2] * sl;
                 if (S.ndl > 0.f && S.mlen > 0.f) {
                     const float gs = gC[0] * S.A[0] + gC[1] * S.A[1] + gC[2] * S.A[2];
+                    if (gl) {
+                        // C = A max(0, n.l): dL/dl = (gC . A) n
+                        gl[0] = fmaf(gs, S.n[0], gl[0]);
+                        gl[1] = fmaf(gs, S.n[1], gl[1]);
+                        gl[2] = fmaf(gs, S.n[2], gl[2]);
+                    }
                     const float gn[3] = {gs * V.light[0], gs * V.light[1], gs * V.light[2]};
                     const float nd = S.n[0] * gn[0] + S.n[1] * gn[1] + S.n[2] * gn[2];
                     const float il = 1.f / S.mlen;
@@ -492,6 +500,7 @@ struct Smem {
     int view, totals[2], next;
     int qn[2];           // queue fill of the current batch, by batch parity
     unsigned long long m0[HS_MAX], m1[HS_MAX];   // per halo row: columns with S^H = 0 / 1
+    float gl[NT][3];     // adjoint: each thread's share of dL/dlight
     unsigned char sh[HS_MAX * HS_MAX];
     // the raster (forward and re-rasterizing adjoint) only: the modes from stored layer
     // ids are launched with the shared memory up to F, leaving the rest of the SM's
@@ -590,7 +599,7 @@ __device__ __forceinline__ bool kept_hard(const Globals &g, const ViewK &V, cons
 template <int K, bool BWD, int TT>
 __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S, const ViewK &V, const MeshK &M,
                                              int X0, int Y0, int lx, int ly, int rho,
-                                             const int (&ids)[K], unsigned hardbits, bool single_chunk)
+                                             const int (&ids)[K], unsigned hardbits, bool single_chunk, float *gl)
 {
     const int X = X0 + lx, Y = Y0 + ly;
     const int lx_g = X, ly_g = Y;   // view-local pixel coordinates
@@ -724,7 +733,7 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
             const long long slot = (V.slot_base + (long long)ly_g * V.W + lx_g) * K + k;
             if (any && layer_build(g, V, M, ids[k], px, py, L)) {
                 ++layers;
-                layer_adjoint(g, V, M, L, px, py, gCl, gDl, slot);
+                layer_adjoint(g, V, M, L, px, py, gCl, gDl, slot, gl);
             }
         }
     }
@@ -763,6 +772,9 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
     }
     constexpr bool BWD = MODE == 1 || MODE == 2;
     constexpr bool from_ids = MODE == 2 || MODE == 3;
+    const bool light_grad = BWD && g.glight != nullptr && g.shade_mode == 2;
+    float *glacc = light_grad ? S.gl[tid] : nullptr;
+    if (light_grad) glacc[0] = glacc[1] = glacc[2] = 0.f;
     if (!from_ids)
         for (int i = tid; i < TT * TT * K; i += NT) kbuf[i] = EMPTY;
     bool single_chunk = false;
@@ -1026,7 +1038,17 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                 ids[k] = id == -1 ? 0x7fffffff : (id & 0x7fffffff);
             }
         }
-        n_layers += finish_pixel<K, BWD, TT>(g, S, V, M, X0, Y0, lx, ly, rho, ids, hardbits, single_chunk);
+        n_layers += finish_pixel<K, BWD, TT>(g, S, V, M, X0, Y0, lx, ly, rho, ids, hardbits, single_chunk, glacc);
+    }
+    if (light_grad) {
+        // this tile's dL/dlight: warp sums, one atomic per warp and component
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float v = glacc[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((tid & 31) == 0 && v != 0.f) atomicAdd(g.glight + 3 * (long long)S.view + c, v);
+        }
     }
     if (g.stats) {
         // work counters: pairs enumerated, exact evaluations, candidates kept, layers shaded

@@ -230,7 +230,9 @@ class Renderer:
         return out
 
     def backward(self, grad_rgba: torch.Tensor, ids: Optional[torch.Tensor] = None, grad_pos=None, grad_col=None,
-                 grad_tex=None, pos=None, col=None, tex=None):
+                 grad_tex=None, pos=None, col=None, tex=None, camera: bool = False):
+        """Adjoint of ``forward``: ``(grad_pos, grad_col, grad_tex)``, and with ``camera``
+        also ``grad_mvp [n_views, 16]`` and ``grad_light [n_views, 3]``."""
         dev = self.scene.device
         sc = self.scene.c_struct(pos, col, tex)
         grad_rgba = grad_rgba.contiguous()
@@ -240,13 +242,19 @@ class Renderer:
             grad_col = torch.empty(3, self.scene.n_verts_total, dtype=torch.float32, device=dev)
         if grad_tex is None and self.scene.tex is not None and self.params.shade_mode != 0:
             grad_tex = torch.empty(self.scene.n_texels, 4, dtype=torch.float32, device=dev)
-        code = self.lib.dressi_backward(C.byref(sc), self.views, self.n_views, C.byref(self.params),
-                                        grad_rgba.data_ptr(), ids.data_ptr() if ids is not None else None,
-                                        self.n_pix, grad_pos.data_ptr(),
-                                        grad_col.data_ptr() if grad_col is not None else None,
-                                        grad_tex.data_ptr() if grad_tex is not None else None,
-                                        self.ws.data_ptr(), self.ws_bytes, self.status.data_ptr(), self._stream())
-        B.check(code, "dressi_backward")
+        gm = torch.empty(self.n_views, 16, dtype=torch.float32, device=dev) if camera else None
+        gl = torch.empty(self.n_views, 3, dtype=torch.float32, device=dev) if camera else None
+        code = self.lib.dressi_backward_ex(C.byref(sc), self.views, self.n_views, C.byref(self.params),
+                                           grad_rgba.data_ptr(), ids.data_ptr() if ids is not None else None,
+                                           self.n_pix, grad_pos.data_ptr(),
+                                           grad_col.data_ptr() if grad_col is not None else None,
+                                           grad_tex.data_ptr() if grad_tex is not None else None,
+                                           gm.data_ptr() if gm is not None else None,
+                                           gl.data_ptr() if gl is not None else None,
+                                           self.ws.data_ptr(), self.ws_bytes, self.status.data_ptr(), self._stream())
+        B.check(code, "dressi_backward_ex")
+        if camera:
+            return grad_pos, grad_col, grad_tex, gm, gl
         return grad_pos, grad_col, grad_tex
 
     def l2_grad(self, out: torch.Tensor, target: torch.Tensor, grad: Optional[torch.Tensor] = None,

@@ -76,15 +76,20 @@ class GpuRun:
         """Hard flag of each layer (False where empty)."""
         return decode_layer_ids(self.view_raw_ids(i))[1]
 
-    def backward(self, grads_per_view, use_ids=True):
+    def backward(self, grads_per_view, use_ids=True, camera=False):
+        """Per-mesh gradients; with ``camera`` also the per-view dL/dMVP [n_views, 16]
+        and dL/dlight [n_views, 3] as numpy arrays."""
         g = torch.zeros(self.r.n_pix, 4, dtype=torch.float32, device=self.ps.device)
         for i, gv in enumerate(grads_per_view):
             v = self.r.views[i]
             g[v.pix_off: v.pix_off + v.width * v.height] = torch.as_tensor(
                 np.asarray(gv, np.float32).reshape(-1, 4), device=self.ps.device)
-        gp, gc, gt = self.r.backward(g, ids=self.ids if use_ids else None)
+        res = self.r.backward(g, ids=self.ids if use_ids else None, camera=camera)
         torch.cuda.synchronize()
-        return self.split(gp, gc, gt)
+        per_mesh = self.split(*res[:3])
+        if camera:
+            return per_mesh, res[3].cpu().numpy().astype(np.float64), res[4].cpu().numpy().astype(np.float64)
+        return per_mesh
 
     def split(self, gp, gc, gt):
         """Per-mesh numpy gradients [V,3], [V,3] or None, [Ht,Wt,4] or None."""
@@ -113,7 +118,7 @@ def window_of(view, win):
 
 
 def compare_scene(scene, windows=None, seed=0, grad_from_target=None, store_layers=True, list_cap=0,
-                  check_grads=True, report=None, tile=0):
+                  check_grads=True, report=None, tile=0, camera=False):
     """Runs both paths on every view (restricted to ``windows``) and asserts parity.
     Returns a dict of the measured errors."""
     gpu = GpuRun(scene, list_cap=list_cap, tile=tile)
@@ -152,18 +157,35 @@ def compare_scene(scene, windows=None, seed=0, grad_from_target=None, store_laye
         stats.setdefault("per_view", []).append((gv, win))
     assert stats["fwd_err"] <= FWD_TOL, f"forward max-abs error {stats['fwd_err']:.3e} > {FWD_TOL}"
     if check_grads:
-        g_gpu = gpu.backward(grads, use_ids=store_layers)
+        if camera:
+            g_gpu, gm_gpu, gl_gpu = gpu.backward(grads, use_ids=store_layers, camera=True)
+        else:
+            g_gpu = gpu.backward(grads, use_ids=store_layers)
         res = [[np.zeros(m.pos.shape), None if m.col is None else np.zeros(m.col.shape),
                 None if m.tex is None else np.zeros(m.tex.shape)] for m in scene.meshes]
+        errs = {}
         for i, v in enumerate(scene.views):
             gv, win = stats["per_view"][i]
-            gp, gc, gt = oracle.backward(scene.meshes[v.mesh], v, scene.params, gv, window=win)
+            if camera:
+                gp, gc, gt, gm, gl = oracle.backward(scene.meshes[v.mesh], v, scene.params, gv, window=win, camera=True)
+                if np.any(gm):
+                    e = rel_l2(gm_gpu[i], gm)
+                    errs[f"mvp{i}"] = e
+                    assert e <= GRAD_TOL, f"view {i} grad_mvp rel-L2 {e:.3e} > {GRAD_TOL}"
+                if scene.params.shade_mode == 2 and np.any(gl):
+                    e = rel_l2(gl_gpu[i], gl)
+                    errs[f"light{i}"] = e
+                    assert e <= GRAD_TOL, f"view {i} grad_light rel-L2 {e:.3e} > {GRAD_TOL}"
+                else:
+                    assert not np.any(gl) and not np.any(gl_gpu[i])
+                assert not np.any(gm_gpu[i][8:12])   # the depth row
+            else:
+                gp, gc, gt = oracle.backward(scene.meshes[v.mesh], v, scene.params, gv, window=win)
             res[v.mesh][0] += gp
             if gc is not None:
                 res[v.mesh][1] += gc
             if gt is not None:
                 res[v.mesh][2] += gt
-        errs = {}
         for mi, (o_, g_) in enumerate(zip(res, g_gpu)):
             for name, a, b in (("pos", g_[0], o_[0]), ("col", g_[1], o_[1]), ("tex", g_[2], o_[2])):
                 if a is None or b is None or not np.any(b):
