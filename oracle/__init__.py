@@ -56,6 +56,13 @@ class _Window(C.Structure):
     _fields_ = [("x0", C.c_int32), ("y0", C.c_int32), ("w", C.c_int32), ("h", C.c_int32)]
 
 
+class _InvUV(C.Structure):
+    """Inverse-UV records (Sec. 3.3.2, Alg. 1); see orc_inv_uv."""
+    _fields_ = [("jitter", C.c_double * 2), ("pix_base", C.c_int64), ("cap", C.c_int64), ("n", C.c_int64),
+                ("slot", C.POINTER(C.c_int64)), ("texel", C.POINTER(C.c_int32)), ("m_tex", C.POINTER(C.c_double)),
+                ("m_cand", C.POINTER(C.c_double)), ("gA", C.POINTER(C.c_double))]
+
+
 class _FwdOut(C.Structure):
     _fields_ = [("rgba", C.POINTER(C.c_double)), ("ids", C.POINTER(C.c_int32)),
                 ("hard", C.POINTER(C.c_int32)), ("dist", C.POINTER(C.c_double)),
@@ -80,7 +87,7 @@ def _load():
             lib.orc_backward_ex.argtypes = [C.POINTER(_View), C.POINTER(_Params), C.POINTER(_Window),
                                             C.POINTER(C.c_double), C.POINTER(C.c_double),
                                             C.POINTER(C.c_double), C.POINTER(C.c_double),
-                                            C.POINTER(C.c_double), C.POINTER(C.c_double)]
+                                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(_InvUV)]
             _lib = lib
     return _lib
 
@@ -168,12 +175,15 @@ def render(mesh, view, params, window=None, brute_force=False):
     return res
 
 
-def backward(mesh, view, params, grad_rgba, window=None, brute_force=False, camera=False):
+def backward(mesh, view, params, grad_rgba, window=None, brute_force=False, camera=False, inverse_uv=None):
     """Adjoint of ``render`` for dL/d(rgba) = ``grad_rgba [h,w,4]`` over ``window``.
 
     Returns ``(grad_pos [V,3], grad_col [V,3] or None, grad_tex [Ht,Wt,4] or None)``,
     and with ``camera`` also ``grad_mvp [16]`` (row-major, as ``view.mvp``) and
     ``grad_light [3]`` (Sec. 3.4.1: the camera and light parameters of Theta).
+    With ``inverse_uv = (jitter, pix_base)`` the texel gradient is not accumulated and
+    the inverse-UV writes of the window's samples are returned last, as a dict of
+    arrays (see ``inverse_uv_texels``).
     """
     lib = _load()
     inp = _Inputs(mesh, view, params, brute_force)
@@ -181,38 +191,54 @@ def backward(mesh, view, params, grad_rgba, window=None, brute_force=False, came
     g = np.ascontiguousarray(np.asarray(grad_rgba, np.float64).reshape(win.h, win.w, 4))
     gp = np.zeros_like(inp.pos)
     gc = np.zeros_like(inp.pos) if inp.col is not None else None
-    gt = np.zeros_like(inp.tex) if inp.tex is not None else None
+    gt = np.zeros_like(inp.tex) if inp.tex is not None and inverse_uv is None else None
     gm = np.zeros(16) if camera else None
     gl = np.zeros(3) if camera else None
+    inv, rec = None, None
+    if inverse_uv is not None:
+        cap = win.w * win.h * params.K
+        rec = dict(slot=np.zeros(cap, np.int64), texel=np.zeros(cap, np.int32), m_tex=np.zeros(cap),
+                   m_cand=np.zeros(cap), gA=np.zeros((cap, 3)))
+        inv = _InvUV()
+        inv.jitter[0], inv.jitter[1] = float(inverse_uv[0][0]), float(inverse_uv[0][1])
+        inv.pix_base, inv.cap, inv.n = int(inverse_uv[1]), cap, 0
+        inv.slot = rec["slot"].ctypes.data_as(C.POINTER(C.c_int64))
+        inv.texel = _ip(rec["texel"])
+        inv.m_tex, inv.m_cand, inv.gA = _dp(rec["m_tex"]), _dp(rec["m_cand"]), _dp(rec["gA"])
     st = lib.orc_backward_ex(C.byref(inp.view), C.byref(inp.params), C.byref(win), _dp(g), _dp(gp), _dp(gc),
-                             _dp(gt), _dp(gm), _dp(gl))
+                             _dp(gt), _dp(gm), _dp(gl), C.byref(inv) if inv is not None else None)
     if st & 1:
         raise ValueError("oracle: invalid argument")
-    return (gp, gc, gt, gm, gl) if camera else (gp, gc, gt)
-
-
-def render_scene(scene, windows=None, brute_force=False):
-    """Per-view forward results for a whole scene (list of dicts)."""
-    out = []
-    for i, v in enumerate(scene.views):
-        win = None if windows is None else windows[i]
-        out.append(render(scene.meshes[v.mesh], v, scene.params, win, brute_force))
+    out = (gp, gc, gt, gm, gl) if camera else (gp, gc, gt)
+    if rec is not None:
+        rec = {k: v[:inv.n] for k, v in rec.items()}
+        out = out + (rec,)
     return out
 
 
-def backward_scene(scene, grads, windows=None):
-    """Gradients summed over the views of a scene, per mesh."""
-    res = []
-    for m in scene.meshes:
-        res.append([np.zeros(m.pos.shape), None if m.col is None else np.zeros(m.col.shape),
-                    None if m.tex is None else np.zeros(m.tex.shape)])
-    for i, v in enumerate(scene.views):
-        win = None if windows is None else windows[i]
-        gp, gc, gt = backward(scene.meshes[v.mesh], v, scene.params, grads[i], win)
-        r = res[v.mesh]
-        r[0] += gp
-        if gc is not None:
-            r[1] += gc
-        if gt is not None:
-            r[2] += gt
-    return res
+def inverse_uv_texels(records, tex_w, tex_h, tau_tex=1e-4, tau_px=1e-4):
+    """Resolves inverse-UV writes (records of one or more views, any order) into the
+    texel gradient of Alg. 1: each texel takes the dL/d(albedo) of its last writer,
+    the largest sample number.  Returns ``(grad [n_texels, 3], winner [n_texels]
+    (-1: none), stable [n_texels])``.  A texel is unstable when a write whose discrete
+    decisions lie within the margins could land on it: a texel floor within ``tau_tex``
+    of an edge (the 3 x 3 texels around it, with REPEAT wrap) or a candidate test
+    within ``tau_px`` of dist = -r (its texel)."""
+    n_texels = tex_w * tex_h
+    cat = (lambda k, empty: np.concatenate([r[k] for r in records]) if records else empty)
+    slot, texel = cat("slot", np.zeros(0, np.int64)), cat("texel", np.zeros(0, np.int32))
+    m_tex, m_cand, gA = cat("m_tex", np.zeros(0)), cat("m_cand", np.zeros(0)), cat("gA", np.zeros((0, 3)))
+    winner = np.full(n_texels, -1, np.int64)
+    np.maximum.at(winner, texel, slot)
+    grad = np.zeros((n_texels, 3))
+    row_of = dict(zip(slot.tolist(), range(len(slot))))
+    for t in np.nonzero(winner >= 0)[0]:
+        grad[t] = gA[row_of[int(winner[t])]]
+    stable = np.ones(n_texels, bool)
+    stable[texel[m_cand < tau_px]] = False
+    for t in texel[m_tex < tau_tex]:
+        ty, tx = divmod(int(t), tex_w)
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                stable[((ty + dy) % tex_h) * tex_w + (tx + dx) % tex_w] = False
+    return grad, winner, stable

@@ -696,13 +696,53 @@ static void tex_backward(const orc_view *v, const shade_t *s, const double gA[3]
     guv[1] = gy * v->tex_h;
 }
 
+/* Inverse UV (Sec. 3.3.2, Alg. 1): the texture-gradient lookup of the paper's Vulkan
+   path.  Every shaded sample (a pixel's layer that the forward shades) has a screen
+   position, the pixel centre plus a jitter given by the caller (the paper adds a Sobol
+   point per frame), and writes its sample number into the texel that holds the layer's
+   UV at that position; the last writer of a texel wins, and the texel's gradient is
+   the winner's dL/d(albedo).  The oracle lists every write as a record (in sample
+   order) with the margins of its discrete decisions; oracle/__init__.py resolves the
+   winners (largest sample number) and the texel gradients from them. */
+typedef struct {
+    double jitter[2];      /* sample offset from the pixel centre, in pixels */
+    int64_t pix_base;      /* the view's first pixel in the packed numbering of all views */
+    int64_t cap, n;        /* record capacity; records written */
+    int64_t *slot;         /* [cap] sample number (pix_base + Y W + X) K + k */
+    int32_t *texel;        /* [cap] texel ty * tex_w + tx written */
+    double *m_tex;         /* [cap] distance of the sample's u W, v H to the nearest texel edge */
+    double *m_cand;        /* [cap] |dist + r| in pixels of the jittered evaluation */
+    double *gA;            /* [cap][3] the sample's dL/d(albedo) at its pixel centre */
+} orc_inv_uv;
+
+static void inv_uv_write(const orc_view *v, const orc_params *prm, const ctx_t *c, const face_t *t, int id,
+                         int X, int Y, int k, const double gA[3], orc_inv_uv *inv)
+{
+    double qx = X + 0.5 + inv->jitter[0], qy = Y + 0.5 + inv->jitter[1];
+    frag_t fj;
+    double d = eval_face(t, id, qx, qy, c->S, &fj);
+    if (!(d >= -c->r_px)) return;          /* not a candidate at the jittered position */
+    shade_t sj;
+    shade(v, prm, t, &fj, c->N, &sj);
+    double x = sj.uv[0] * v->tex_w, y = sj.uv[1] * v->tex_h;
+    double fx = floor(x), fy = floor(y);
+    if (inv->n >= inv->cap) return;
+    int64_t r = inv->n++;
+    inv->slot[r] = (inv->pix_base + (int64_t)Y * v->width + X) * prm->K + k;
+    inv->texel[r] = wrap((long long)fy, v->tex_h) * v->tex_w + wrap((long long)fx, v->tex_w);
+    double mx = fmin(x - fx, fx + 1.0 - x), my = fmin(y - fy, fy + 1.0 - y);
+    inv->m_tex[r] = fmin(mx, my);
+    inv->m_cand[r] = fabs(d + c->r_px);
+    for (int ch = 0; ch < 3; ++ch) inv->gA[3 * r + ch] = gA[ch];
+}
+
 /* The adjoint also gives the gradients of the camera and the light, the parameters
    theta_C and theta_L of Theta (Sec. 3.4.1): grad_mvp [16] (row-major, as mvp; the
    depth row stays 0, depth only enters the discrete Shift keys) and grad_light [3]
    (the light treated as a free 3-vector, as the forward uses it).  Either may be NULL. */
 int orc_backward_ex(const orc_view *v, const orc_params *prm, const orc_window *w,
                     const double *grad_rgba, double *grad_pos, double *grad_col, double *grad_tex,
-                    double *grad_mvp, double *grad_light)
+                    double *grad_mvp, double *grad_light, orc_inv_uv *inv)
 {
     if (!check_args(v, prm, w) || !grad_rgba) return ORC_BAD_ARG;
     ctx_t c;
@@ -791,6 +831,7 @@ int orc_backward_ex(const orc_view *v, const orc_params *prm, const orc_window *
                     }
                     double guv[2];
                     tex_backward(v, sk, gA, grad_tex, guv);
+                    if (inv && (E || k == 0)) inv_uv_write(v, prm, &c, t, fr->id, X, Y, k, gA, inv);
                     for (int i = 0; i < 3; ++i)
                         gb[i] += guv[0] * v->uv[2 * t->vi[i]] + guv[1] * v->uv[2 * t->vi[i] + 1];
                 }
@@ -880,7 +921,7 @@ int orc_backward_ex(const orc_view *v, const orc_params *prm, const orc_window *
 int orc_backward(const orc_view *v, const orc_params *prm, const orc_window *w,
                  const double *grad_rgba, double *grad_pos, double *grad_col, double *grad_tex)
 {
-    return orc_backward_ex(v, prm, w, grad_rgba, grad_pos, grad_col, grad_tex, NULL, NULL);
+    return orc_backward_ex(v, prm, w, grad_rgba, grad_pos, grad_col, grad_tex, NULL, NULL, NULL);
 }
 
 /* size of the structs, so the Python loader can verify its layout */

@@ -492,6 +492,51 @@ def test_camera_and_light_adjoint_match_central_differences(shade_mode, edge_mod
 
 
 # ----------------------------------------------------------------------------
+# inverse UV (Sec. 3.3.2, Alg. 1): closed forms on a pixel-aligned textured quad
+# ----------------------------------------------------------------------------
+
+def _uv_quad(tex_w, W=16):
+    """Screen-filling quad whose UV puts pixel centre X + 1/2 at u W = X + 1/2 (so at
+    u tex_w = (X + 1/2) tex_w / W); unlit texture, one hard layer."""
+    V = np.array([[-1, -1], [W + 1, -1], [W + 1, W + 1], [-1, W + 1]], np.float64)
+    uv = V / W
+    tex = np.zeros((W, tex_w, 4))
+    tex[..., :3] = np.random.default_rng(2).random((W, tex_w, 3))
+    mesh = pixel_mesh(V, [[0, 1, 2], [0, 2, 3]], W, W, uv=uv, tex=tex)
+    return pixel_scene(mesh, W, W, K=1, r=1 / W, sigma=0.3 / W, delta=1 / W, edge_mode=2, shade_mode=1)
+
+
+@pytest.mark.parametrize("jitter,shift", [((0.0, 0.0), 0), ((0.6, 0.0), 1), ((0.0, -0.7), -1)])
+def test_inverse_uv_pixel_aligned(jitter, shift):
+    """One texel per pixel: the inverse UV is the identity, shifted by one texel when the
+    jitter moves the sample across a texel edge (REPEAT wrap); the texel gradient is
+    the pixel gradient moved the same way."""
+    W = 16
+    s = _uv_quad(W, W)
+    g = np.random.default_rng(4).normal(size=(W, W, 4))
+    *_, rec = oracle.backward(s.meshes[0], s.views[0], s.params, g, inverse_uv=(jitter, 0))
+    grad, winner, stable = oracle.inverse_uv_texels([rec], W, W)
+    axis = 1 if jitter[0] else 0
+    expect = np.roll(g[..., :3], shift, axis=axis).reshape(-1, 3)
+    np.testing.assert_allclose(grad, expect, rtol=0, atol=1e-12)
+    assert stable.all() and (winner >= 0).all()
+
+
+def test_inverse_uv_last_writer_wins():
+    """Two pixels per texel (the texture is half as wide as the view): the texel keeps
+    the later sample, the right pixel of each pair."""
+    W = 16
+    s = _uv_quad(W // 2, W)
+    g = np.random.default_rng(6).normal(size=(W, W, 4))
+    *_, rec = oracle.backward(s.meshes[0], s.views[0], s.params, g, inverse_uv=((0.0, 0.0), 0))
+    assert len(rec["slot"]) == W * W
+    grad, winner, _ = oracle.inverse_uv_texels([rec], W // 2, W)
+    np.testing.assert_allclose(grad, g[:, 1::2, :3].reshape(-1, 3), rtol=0, atol=1e-12)
+    ys, xs = np.divmod(np.arange(W * W // 2), W // 2)
+    np.testing.assert_array_equal(winner, ys * W + 2 * xs + 1)   # K = 1: sample = pixel
+
+
+# ----------------------------------------------------------------------------
 # brute force equals the bbox pre-tested variant bit for bit
 # ----------------------------------------------------------------------------
 
