@@ -483,7 +483,7 @@ def ours(args, rank, world, local_rank):
                "sample": f"{nv} of {len(s.views)} views, forward + adjoint, FP64 C oracle, single thread, {dt:.1f} s"}
     if rank == 0:
         cfg = workload_desc(s, args.workload)
-        cfg.update({"texgrad": "texel-space gather" if args.texgrad else "atomics", "tile": tile, "schedule": "persistent longest-first" if schedule == 2 else "CTA per tile",
+        cfg.update({"texgrad": ["atomics", "texel-space gather", "inverse UV"][args.texgrad], "tile": tile, "schedule": "persistent longest-first" if schedule == 2 else "CTA per tile",
                     "autotuned": tuned is not None, "list_cap": int(r.params.list_cap), "cuda_graph": use_graph})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -512,8 +512,8 @@ def main():
     ap.add_argument("--no-cached", action="store_true", help="skip the static-geometry (cached layers) step")
     ap.add_argument("--workload", default="multiview", choices=WORKLOADS)
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--texgrad", type=int, default=0, choices=[0, 1],
-                    help="texel gradients: 0 vector red.global atomics, 1 deterministic sort + texel-space gather")
+    ap.add_argument("--texgrad", type=int, default=0, choices=[0, 1, 2],
+                    help="texel gradient: 0 atomics, 1 deterministic texel gather, 2 inverse UV (approximate)")
     ap.add_argument("--no-plain", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

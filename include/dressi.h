@@ -114,7 +114,9 @@ typedef struct {
                            from the colour blend) */
     int32_t edge_mode;  /* 0 edge mask from S^H, 1 E = 1 everywhere (SoftRas-like), 2 E = 0 (hard) */
     int32_t shade_mode; /* 0 vertex colour, 1 unlit texture, 2 texture * max(0, n.l) */
-    int32_t texgrad_mode; /* 0 warp-aggregated atomics, 1 texel-space gather (deterministic) */
+    int32_t texgrad_mode; /* 0 warp-aggregated atomics, 1 texel-space gather (deterministic),
+                             2 inverse UV (Sec. 3.3.2, Alg. 1; approximate: each texel takes the
+                             dL/d(albedo) of the last shaded sample that lands on it) */
     int32_t tile;       /* tile edge in pixels: 16 or 32; 0 = 16 */
     int32_t schedule;   /* per-tile kernel: 0 auto (= 1), 1 one CTA per tile, 2 persistent CTAs
                            pulling (view, tile) items longest face list first */
@@ -122,6 +124,9 @@ typedef struct {
                            max(4 x faces over all views, 64 x tiles).  Clamped to
                            2^31 - 2.  A tile whose list ends past it falls back to the
                            view's whole mesh and sets DRESSI_DEV_TILE_OVERFLOW */
+    float uv_jitter[2]; /* texgrad_mode 2: offset (pixels) of every sample from its pixel
+                           centre for the inverse-UV lookup; the paper draws a Sobol point per
+                           frame (the caller supplies it; [-0.5, 0.5)^2 keeps it in the pixel) */
 } dressi_params;
 
 /* Size in bytes of the workspace that dressi_forward / dressi_backward need for
@@ -259,6 +264,14 @@ DRESSI_API int dressi_set_profile_events(void *fwd_begin, void *fwd_end, void *b
    shaded (forward) or back-propagated (adjoint).  NULL disables.  Process-wide
    setting, not thread safe; the counting costs one atomic per warp and tile. */
 DRESSI_API int dressi_set_stats_buffer(void *dev_counters);
+
+/* Inspection hook for texgrad_mode 2 (no counterpart in the paper): when set, each
+   dressi_backward(_ex) with texgrad_mode 2 copies the inverse-UV texture -- per texel
+   (packed like grad_tex) the number of the sample that wrote it last,
+   (view pixel offset + y W + x) K + layer with the views' pixels counted in order, or
+   -1 -- into this DEVICE int32 [sum texels] buffer.  NULL disables.  Process-wide
+   setting, not thread safe. */
+DRESSI_API int dressi_set_inverse_uv_buffer(int32_t *dev_buffer);
 
 /* Number of kernels this library has launched since it was loaded (process-wide). */
 DRESSI_API unsigned long long dressi_launch_count(void);

@@ -40,7 +40,7 @@ class DressiParams(C.Structure):
     _fields_ = [("K", C.c_int32), ("r", C.c_float), ("sigma", C.c_float), ("delta", C.c_float),
                 ("gamma", C.c_float), ("edge_mode", C.c_int32), ("shade_mode", C.c_int32),
                 ("texgrad_mode", C.c_int32), ("tile", C.c_int32), ("schedule", C.c_int32),
-                ("list_cap", C.c_int64)]
+                ("list_cap", C.c_int64), ("uv_jitter", C.c_float * 2)]
 
 
 # every symbol declared in include/dressi.h, with its ctypes signature
@@ -73,6 +73,7 @@ SIGNATURES = {
     "dressi_set_profile_events": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dressi_launch_count": (C.c_ulonglong, []),
     "dressi_set_stats_buffer": (C.c_int, [C.c_void_p]),
+    "dressi_set_inverse_uv_buffer": (C.c_int, [C.c_void_p]),
 }
 
 _lock = threading.Lock()

@@ -26,6 +26,7 @@ void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memo
 static cudaEvent_t g_prof[4] = {nullptr, nullptr, nullptr, nullptr};
 // optional device work counters of the per-tile kernel (statistics hook)
 static unsigned long long *g_stats = nullptr;
+static int *g_inv_uv_out = nullptr;
 
 // pass: 0 forward, 1 adjoint, 2 forward from stored layer ids (timed as a forward)
 static void launch_tile_profiled(const Globals &g, int pass, cudaStream_t s)
@@ -41,7 +42,7 @@ static void launch_tile_profiled(const Globals &g, int pass, cudaStream_t s)
 struct Layout {
     size_t views, meshes, vrec, frec, tile_count, tile_off, tile_cursor, lists, nrm, adj_off, adj_cur, adj, scan_partial,
         sgrad, ngrad, queue,
-        tile_order, lpt_hist, tg_keys, tg_pay0, tg_pay1, tg_scratch, total;
+        tile_order, lpt_hist, tg_keys, tg_pay0, tg_pay1, tg_scratch, inv_uv, total;
     long long tg_slots;   // texel-gather record slots (0 unless texgrad_mode 1 with a texture)
     long long n_vrec;
     int total_tiles;
@@ -65,7 +66,8 @@ static bool check_params(const dressi_params *p)
         return false;
     if (p->edge_mode < 0 || p->edge_mode > 2) return false;
     if (p->shade_mode < 0 || p->shade_mode > 2) return false;
-    if (p->texgrad_mode < 0 || p->texgrad_mode > 1) return false;
+    if (p->texgrad_mode < 0 || p->texgrad_mode > 2) return false;
+    if (!std::isfinite(p->uv_jitter[0]) || !std::isfinite(p->uv_jitter[1])) return false;
     if (p->tile != 0 && p->tile != 16 && p->tile != 32) return false;
     if (p->schedule < 0 || p->schedule > 2) return false;
     if (p->list_cap < 0) return false;
@@ -179,12 +181,16 @@ static bool make_plan(const dressi_scene *sc, const dressi_view *views, int n_vi
     L.queue = o; o = align_up(o + sizeof(int) * 4);
     L.tile_order = o; o = align_up(o + sizeof(int) * (size_t)std::max(tiles, 1));
     L.lpt_hist = o; o = align_up(o + sizeof(int) * LPT_BINS);
-    L.tg_slots = (p->texgrad_mode == 1 && textured) ? view_pixels * p->K : 0;
+    L.tg_slots = (p->texgrad_mode != 0 && textured) ? view_pixels * p->K : 0;
+    // the inverse UV stores sample numbers as int32 (atomicMax)
+    if (p->texgrad_mode == 2 && L.tg_slots > 0x7fffffffLL) return false;
+    L.inv_uv = o; o = align_up(o + sizeof(int) * (size_t)((p->texgrad_mode == 2 && textured) ? std::max<long long>(P.n_texels, 1) : 1));
     const size_t ts = (size_t)std::max<long long>(L.tg_slots, 1);
     L.tg_keys = o; o = align_up(o + sizeof(unsigned) * ts);
     L.tg_pay0 = o; o = align_up(o + sizeof(float4) * ts);
     L.tg_pay1 = o; o = align_up(o + sizeof(float) * ts);
-    L.tg_scratch = o; o = align_up(o + (L.tg_slots ? texgather_scratch_bytes(L.tg_slots, P.n_texels, ALIGN) : 0));
+    L.tg_scratch = o;
+    o = align_up(o + (L.tg_slots && p->texgrad_mode == 1 ? texgather_scratch_bytes(L.tg_slots, P.n_texels, ALIGN) : 0));
     L.total = o;
     return true;
 }
@@ -269,6 +275,9 @@ static Globals make_globals(const dressi_scene *sc, const dressi_params *p, cons
     g.tg_keys = reinterpret_cast<unsigned *>(ws + L.tg_keys);
     g.tg_pay0 = reinterpret_cast<float4 *>(ws + L.tg_pay0);
     g.tg_pay1 = reinterpret_cast<float *>(ws + L.tg_pay1);
+    g.inv_uv = reinterpret_cast<int *>(ws + L.inv_uv);
+    g.uv_jx = p->uv_jitter[0];
+    g.uv_jy = p->uv_jitter[1];
     g.n_texels_max_key = P.n_texels;
     return g;
 }
@@ -353,6 +362,12 @@ int dressi_set_profile_events(void *fwd_begin, void *fwd_end, void *bwd_begin, v
 }
 
 unsigned long long dressi_launch_count(void) { return g_launches.load(); }
+
+int dressi_set_inverse_uv_buffer(int32_t *dev_buffer)
+{
+    g_inv_uv_out = dev_buffer;
+    return DRESSI_OK;
+}
 
 int dressi_set_stats_buffer(void *dev_counters)
 {
@@ -481,14 +496,22 @@ int dressi_backward_ex(const dressi_scene *scene, const dressi_view *views, int3
     cudaMemsetAsync(w + P.lay.sgrad, 0, sizeof(float4) * (size_t)std::max<long long>(P.lay.n_vrec, 1), s);
     if (params->shade_mode == 2)
         cudaMemsetAsync(w + P.lay.ngrad, 0, sizeof(float4) * (size_t)std::max<long long>(nvt, 1), s);
-    const bool gather = g.gtex && P.lay.tg_slots > 0;
-    if (!gather) g.texgrad_mode = 0;
+    const bool tex_records = g.gtex && P.lay.tg_slots > 0;
+    const bool gather = tex_records && params->texgrad_mode == 1;
+    const bool inv_uv = tex_records && params->texgrad_mode == 2;
+    if (!tex_records) g.texgrad_mode = 0;
     if (gather) cudaMemsetAsync(w + P.lay.tg_keys, 0xff, sizeof(unsigned) * (size_t)P.lay.tg_slots, s);
+    if (inv_uv) cudaMemsetAsync(w + P.lay.inv_uv, 0xff, sizeof(int) * (size_t)P.n_texels, s);
     run_setup(g, P, w, layer_ids == nullptr, s);
     run_tiles(g, P, w, layer_ids == nullptr, 1, s);
     if (gather)
         launch_tex_gather(g, P.lay.tg_slots, P.n_texels, (int)P.meshes.size(), P.max_texels, w + P.lay.tg_scratch,
                           ALIGN, s);
+    if (inv_uv) {
+        launch_inv_uv_apply(g, P.n_texels, s);
+        if (g_inv_uv_out) cudaMemcpyAsync(g_inv_uv_out, g.inv_uv, sizeof(int) * (size_t)P.n_texels,
+                                          cudaMemcpyDeviceToDevice, s);
+    }
     launch_vertex_bwd(g, (int)P.views.size(), P.max_nv_view, (int)P.meshes.size(), P.max_nf,
                       params->shade_mode == 2, s);
     return cudaGetLastError() == cudaSuccess ? DRESSI_OK : DRESSI_ERR_LAUNCH;

@@ -122,6 +122,8 @@ struct Globals {
     float4 *ngrad;        // [n_verts_total] gradient of the normalized vertex normals
     float *gpos, *gcol, *gtex;
     float *gmvp;          // [n_views][16] dL/dMVP or nullptr
+    int *inv_uv;          // texgrad_mode 2: [sum texels] last sample written per texel (-1 none)
+    float uv_jx, uv_jy;   // texgrad_mode 2: sample offset from the pixel centre
     float *glight;        // [n_views][3] dL/dlight or nullptr
     // texel-space gather of the texture gradient (texgrad_mode 1): one record per
     // (pixel, layer) at slot (slot_base + pixel) * K + layer

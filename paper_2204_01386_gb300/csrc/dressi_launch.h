@@ -16,6 +16,7 @@ void launch_lpt_order(const Globals &g, cudaStream_t s);
 size_t texgather_scratch_bytes(long long slots, long long n_texels, size_t align);
 void launch_scan_inplace(int *a, int n, int *partial, cudaStream_t s);
 int scan_partials_needed(long long n);
+void launch_inv_uv_apply(const Globals &g, long long n_texels, cudaStream_t s);
 void launch_tex_gather(const Globals &g, long long slots, long long n_texels, int n_meshes, int max_texels,
                        char *scratch, size_t align, cudaStream_t s);
 void launch_vertex_bwd(const Globals &g, int n_views, int max_nv, int n_meshes, int max_nf, bool normals,

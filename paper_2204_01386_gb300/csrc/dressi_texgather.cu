@@ -15,6 +15,8 @@
 #include "dressi_core.cuh"
 #include "dressi_launch.h"
 
+#include <algorithm>
+
 namespace dressi {
 
 constexpr int RS_THREADS = 256;
@@ -309,6 +311,29 @@ void launch_tex_gather(const Globals &g, long long slots, long long n_texels, in
     }
     dim3 grid(grid_of(max_texels, 256, 4096), n_meshes);
     k_tex_gather<<<grid, 256, 0, s>>>(g, kin, vin, count);
+    count_launch(1);
+}
+
+// ---------------------------------------------------------------------------
+// inverse UV (Sec. 3.3.2, Alg. 1): each texel takes the dL/d(albedo) of the sample
+// that wrote it last (the largest sample number, kept by atomicMax in the adjoint);
+// the sample's dL/dA waits in its record slot.  Texels without a writer stay 0.
+// ---------------------------------------------------------------------------
+__global__ void k_inv_uv_apply(Globals g, long long n_texels)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n_texels;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int s = g.inv_uv[t];
+        if (s < 0) continue;
+        const float4 a = g.tg_pay0[s];
+        reinterpret_cast<float4 *>(g.gtex)[t] = make_float4(a.x, a.y, a.z, 0.f);
+    }
+}
+
+void launch_inv_uv_apply(const Globals &g, long long n_texels, cudaStream_t s)
+{
+    const long long blocks = std::min<long long>((n_texels + 255) / 256, 152LL * 32);
+    k_inv_uv_apply<<<(int)std::max<long long>(blocks, 1), 256, 0, s>>>(g, n_texels);
     count_launch(1);
 }
 

@@ -300,11 +300,13 @@ __device__ __forceinline__ bool layer_build(const Globals &g, const ViewK &V, co
 // ---------------------------------------------------------------------------
 // adjoint of one layer: gC = dL/dC_k, gD = dL/dD_k
 // ---------------------------------------------------------------------------
-// gl: this thread's dL/dlight accumulator, or nullptr
-__device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, const MeshK &M, const Layer &L,
+// gl: this thread's dL/dlight accumulator, or nullptr.  Returns true when it stored
+// the sample's dL/d(albedo) in its record slot (texgrad_mode 2, the inverse UV).
+__device__ __forceinline__ bool layer_adjoint(const Globals &g, const ViewK &V, const MeshK &M, const Layer &L,
                                               float px, float py, const float gC[3], float gD, long long slot,
                                               float *gl)
 {
+    bool stored = false;
     const long long nvt = g.n_verts_total;
     const FaceRec &R = L.R;
     const Shade &S = L.S;
@@ -403,6 +405,10 @@ __device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, 
                 g.tg_keys[slot] = (unsigned)i00;
                 g.tg_pay0[slot] = make_float4(gA[0], gA[1], gA[2], S.fx);
                 g.tg_pay1[slot] = S.fy;
+            } else if (g.gtex && g.texgrad_mode == 2) {
+                // inverse UV: the sample's dL/dA waits in its slot for the texel lookup
+                g.tg_pay0[slot] = make_float4(gA[0], gA[1], gA[2], 0.f);
+                stored = true;
             } else if (g.gtex) {
                 float4 *gt = reinterpret_cast<float4 *>(g.gtex);
                 atomicAdd(gt + i00, make_float4(w00 * gA[0], w00 * gA[1], w00 * gA[2], 0.f));
@@ -480,6 +486,37 @@ __device__ __forceinline__ void layer_adjoint(const Globals &g, const ViewK &V, 
 #pragma unroll
     for (int i = 0; i < 3; ++i)
         if (gX[i] != 0.f || gY[i] != 0.f || gW[i] != 0.f) atomicAdd(sg + S.vi[i], make_float4(gX[i], gY[i], gW[i], 0.f));
+    return stored;
+}
+
+// inverse UV (Sec. 3.3.2, Alg. 1): the sample of face id at the (jittered) screen
+// position (qx, qy) claims the texel holding its UV there; the largest sample number
+// wins, as the last writer of a sequential pass over the samples would.  A face that
+// is no candidate at the jittered position writes nothing.
+__device__ __forceinline__ void inv_uv_write(const Globals &g, const ViewK &V, const MeshK &M, int id, float qx,
+                                             float qy, int rec)
+{
+    FaceRec R;
+    Frag fr;
+    if (!face_get(g, V, M, id, R) || !eval_face(R, qx, qy, V.r_px, V.half_inv_S, fr)) return;
+    float lam[3];
+    frag_lambda(R, fr, lam);
+    float q[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) q[i] = fmul(lam[i], R.iw[i]);
+    const float iQ = __fdiv_rn(1.f, fadd(fadd(q[0], q[1]), q[2]));
+    const long long nvt = g.n_verts_total;
+    float u = 0.f, v = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float b = fmul(q[i], iQ);
+        u = ffma(b, __ldg(g.uv + M.vert_off + R.vi[i]), u);
+        v = ffma(b, __ldg(g.uv + nvt + M.vert_off + R.vi[i]), v);
+    }
+    const float x = fmul(u, (float)M.tex_w), y = fmul(v, (float)M.tex_h);
+    if (!(fabsf(x) < 1e9f && fabsf(y) < 1e9f)) return;
+    const int tx = wrapi((int)floorf(x), M.tex_w), ty = wrapi((int)floorf(y), M.tex_h);
+    atomicMax(g.inv_uv + M.tex_off + (long long)ty * M.tex_w + tx, rec);
 }
 
 // ---------------------------------------------------------------------------
@@ -672,9 +709,11 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
         reinterpret_cast<float4 *>(g.out)[pix] = o;
     } else {
         if (nl == 0) return 0;
+        // the inverse UV needs every shaded sample, also those without a gradient
+        const bool inv = g.texgrad_mode == 2;
         const float4 gi4 = __ldg(reinterpret_cast<const float4 *>(g.gin) + pix);
         const float gc[3] = {gi4.x, gi4.y, gi4.z};
-        if (gc[0] == 0.f && gc[1] == 0.f && gc[2] == 0.f && gi4.w == 0.f) return 0;
+        if (!inv && gc[0] == 0.f && gc[1] == 0.f && gc[2] == 0.f && gi4.w == 0.f) return 0;
         float gCk[K][3], gDk[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) { gDk[k] = 0.f; gCk[k][0] = gCk[k][1] = gCk[k][2] = 0.f; }
@@ -724,6 +763,7 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
             gCk[0][0] = gc[0]; gCk[0][1] = gc[1]; gCk[0][2] = gc[2];
         }
         // pass 2: per-layer adjoint
+        unsigned stored = 0u;
 #pragma unroll 1
         for (int k = 0; k < nl; ++k) {
             const float gCl[3] = {gCk[k][0], gCk[k][1], gCk[k][2]};
@@ -733,7 +773,18 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
             const long long slot = (V.slot_base + (long long)ly_g * V.W + lx_g) * K + k;
             if (any && layer_build(g, V, M, ids[k], px, py, L)) {
                 ++layers;
-                layer_adjoint(g, V, M, L, px, py, gCl, gDl, slot, gl);
+                if (layer_adjoint(g, V, M, L, px, py, gCl, gDl, slot, gl)) stored |= 1u << k;
+            }
+        }
+        if (inv) {
+            // pass 3: every shaded sample (the layers the forward blends) claims its texel;
+            // a sample without a texture gradient offers dL/dA = 0
+#pragma unroll 1
+            for (int k = 0; k < nl; ++k) {
+                if (!(E || k == 0)) continue;
+                const long long slot = (V.slot_base + (long long)ly_g * V.W + lx_g) * K + k;
+                if (!((stored >> k) & 1u)) g.tg_pay0[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+                inv_uv_write(g, V, M, ids[k], fadd(px, g.uv_jx), fadd(py, g.uv_jy), (int)slot);
             }
         }
     }

@@ -104,9 +104,10 @@ def make_views(views: Sequence) -> "C.Array":
 
 
 def make_params(p, list_cap: int = 0, tile: int = 0, schedule: int = 0) -> B.DressiParams:
+    jit = getattr(p, "uv_jitter", (0.0, 0.0))
     return B.DressiParams(int(p.K), float(p.r), float(p.sigma), float(p.delta), float(getattr(p, "gamma", 0.0)),
                           int(p.edge_mode), int(p.shade_mode), int(getattr(p, "texgrad_mode", 0)), int(tile),
-                          int(schedule), int(list_cap))
+                          int(schedule), int(list_cap), (C.c_float * 2)(float(jit[0]), float(jit[1])))
 
 
 class Renderer:
