@@ -301,7 +301,9 @@ __device__ __forceinline__ bool layer_build(const Globals &g, const ViewK &V, co
 // adjoint of one layer: gC = dL/dC_k, gD = dL/dD_k
 // ---------------------------------------------------------------------------
 // gl: this thread's dL/dlight accumulator, or nullptr.  Returns true when it stored
-// the sample's dL/d(albedo) in its record slot (texgrad_mode 2, the inverse UV).
+// the sample's dL/d(albedo) in its record slot (texgrad_mode 2, the inverse UV).  EXTRA
+// compiles the light gradient and the inverse UV in (the adjoint without them is leaner).
+template <bool EXTRA>
 __device__ __forceinline__ bool layer_adjoint(const Globals &g, const ViewK &V, const MeshK &M, const Layer &L,
                                               float px, float py, const float gC[3], float gD, long long slot,
                                               float *gl)
@@ -372,7 +374,7 @@ __device__ __forceinline__ bool layer_adjoint(const Globals &g, const ViewK &V, 
                 gA[0] = gC[0] * sl; gA[1] = gC[1] * sl; gA[2] = gC[2] * sl;
                 if (S.ndl > 0.f && S.mlen > 0.f) {
                     const float gs = gC[0] * S.A[0] + gC[1] * S.A[1] + gC[2] * S.A[2];
-                    if (gl) {
+                    if (EXTRA && gl) {
                         // C = A max(0, n.l): dL/dl = (gC . A) n
                         gl[0] = fmaf(gs, S.n[0], gl[0]);
                         gl[1] = fmaf(gs, S.n[1], gl[1]);
@@ -405,7 +407,7 @@ __device__ __forceinline__ bool layer_adjoint(const Globals &g, const ViewK &V, 
                 g.tg_keys[slot] = (unsigned)i00;
                 g.tg_pay0[slot] = make_float4(gA[0], gA[1], gA[2], S.fx);
                 g.tg_pay1[slot] = S.fy;
-            } else if (g.gtex && g.texgrad_mode == 2) {
+            } else if (EXTRA && g.gtex && g.texgrad_mode == 2) {
                 // inverse UV: the sample's dL/dA waits in its slot for the texel lookup
                 g.tg_pay0[slot] = make_float4(gA[0], gA[1], gA[2], 0.f);
                 stored = true;
@@ -633,7 +635,7 @@ __device__ __forceinline__ bool kept_hard(const Globals &g, const ViewK &V, cons
 
 // S^H, edge mask, shading and blend (forward) or the adjoint (BWD) of one pixel
 // whose K layer ids are known; S.sh holds the tile's S^H with its ring.
-template <int K, bool BWD, int TT>
+template <int K, bool BWD, int TT, bool EXTRA>
 __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S, const ViewK &V, const MeshK &M,
                                              int X0, int Y0, int lx, int ly, int rho,
                                              const int (&ids)[K], unsigned hardbits, bool single_chunk, float *gl)
@@ -710,7 +712,7 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
     } else {
         if (nl == 0) return 0;
         // the inverse UV needs every shaded sample, also those without a gradient
-        const bool inv = g.texgrad_mode == 2;
+        const bool inv = EXTRA && g.texgrad_mode == 2;
         const float4 gi4 = __ldg(reinterpret_cast<const float4 *>(g.gin) + pix);
         const float gc[3] = {gi4.x, gi4.y, gi4.z};
         if (!inv && gc[0] == 0.f && gc[1] == 0.f && gc[2] == 0.f && gi4.w == 0.f) return 0;
@@ -773,7 +775,7 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
             const long long slot = (V.slot_base + (long long)ly_g * V.W + lx_g) * K + k;
             if (any && layer_build(g, V, M, ids[k], px, py, L)) {
                 ++layers;
-                if (layer_adjoint(g, V, M, L, px, py, gCl, gDl, slot, gl)) stored |= 1u << k;
+                if (layer_adjoint<EXTRA>(g, V, M, L, px, py, gCl, gDl, slot, gl)) stored |= 1u << k;
             }
         }
         if (inv) {
@@ -793,7 +795,8 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
 
 // everything one CTA does for global tile t.  MODE: 0 forward, 1 adjoint that
 // re-rasterizes, 2 adjoint from stored layer ids, 3 forward from stored layer ids
-// (re-shading a static geometry: no binning, raster or peel)
+// (re-shading a static geometry: no binning, raster or peel), 4 and 5 = 2 and 1 with
+// the light gradient and the inverse UV compiled in
 template <int K, int MODE, int TT>
 __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned long long *kbuf, const int t)
 {
@@ -821,9 +824,10 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
         const int hx = X0 - rho + i % hs, hy = Y0 - rho + i / hs;
         S.sh[i] = (hx >= 0 && hy >= 0 && hx < V.W && hy < V.H) ? 0 : 2;
     }
-    constexpr bool BWD = MODE == 1 || MODE == 2;
-    constexpr bool from_ids = MODE == 2 || MODE == 3;
-    const bool light_grad = BWD && g.glight != nullptr && g.shade_mode == 2;
+    constexpr bool EXTRA = MODE >= 4;
+    constexpr bool BWD = MODE == 1 || MODE == 2 || EXTRA;
+    constexpr bool from_ids = MODE == 2 || MODE == 3 || MODE == 4;
+    const bool light_grad = EXTRA && g.glight != nullptr && g.shade_mode == 2;
     float *glacc = light_grad ? S.gl[tid] : nullptr;
     if (light_grad) glacc[0] = glacc[1] = glacc[2] = 0.f;
     if (!from_ids)
@@ -1089,7 +1093,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                 ids[k] = id == -1 ? 0x7fffffff : (id & 0x7fffffff);
             }
         }
-        n_layers += finish_pixel<K, BWD, TT>(g, S, V, M, X0, Y0, lx, ly, rho, ids, hardbits, single_chunk, glacc);
+        n_layers += finish_pixel<K, BWD, TT, EXTRA>(g, S, V, M, X0, Y0, lx, ly, rho, ids, hardbits, single_chunk, glacc);
     }
     if (light_grad) {
         // this tile's dL/dlight: warp sums, one atomic per warp and component
@@ -1118,7 +1122,10 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
 // the raster and the adjoint state: four with 16 px tiles, three with 32 px tiles (whose
 // K-lists limit the shared memory to three CTAs anyway).
 template <int MODE, int TT>
-constexpr int tile_min_ctas() { return MODE == 0 || MODE == 3 ? 4 : MODE == 2 ? 3 : (TT == 16 ? 4 : 3); }
+constexpr int tile_min_ctas()
+{
+    return MODE == 0 || MODE == 3 ? 4 : (MODE == 2 || MODE == 4) ? 3 : (TT == 16 ? 4 : 3);
+}
 
 template <int K, int MODE, int TT>
 __global__ void __launch_bounds__(NT, tile_min_ctas<MODE, TT>()) k_tile(Globals g)
@@ -1153,7 +1160,7 @@ constexpr size_t tile_smem_bytes()
 {
     // from stored ids: the first part of Smem; otherwise Smem, the K-lists,
     // the candidate queue, the two pair-block tables
-    return MODE == 2 || MODE == 3 ? offsetof(Smem, F)
+    return MODE == 2 || MODE == 3 || MODE == 4 ? offsetof(Smem, F)
                      : sizeof(Smem) + sizeof(unsigned long long) * TT * TT * K + sizeof(unsigned) * QN + 2 * NBLK;
 }
 // four forward CTAs of the default configuration (K = 3, 16 px tiles) per SM: 228 KB of
@@ -1199,8 +1206,8 @@ static void launch_k(const Globals &g, cudaStream_t s)
 }
 
 // the per-tile kernel of one mode (0 forward, 1 adjoint re-rasterizing, 2 adjoint from
-// stored layer ids, 3 forward from stored layer ids); instantiated by that mode's
-// translation unit
+// stored layer ids, 3 forward from stored layer ids, 4 / 5: 2 / 1 with the light
+// gradient and the inverse UV); instantiated by that mode's translation unit
 template <int MODE>
 void launch_tile_mode(const Globals &g, cudaStream_t s)
 {
