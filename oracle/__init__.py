@@ -44,7 +44,7 @@ class _View(C.Structure):
                 ("uv", C.POINTER(C.c_double)), ("faces", C.POINTER(C.c_int32)),
                 ("tex_w", C.c_int32), ("tex_h", C.c_int32), ("tex", C.POINTER(C.c_double)),
                 ("mvp", C.c_double * 16), ("light", C.c_double * 3),
-                ("width", C.c_int32), ("height", C.c_int32)]
+                ("width", C.c_int32), ("height", C.c_int32), ("ntex", C.POINTER(C.c_double))]
 
 
 class _Params(C.Structure):
@@ -87,7 +87,8 @@ def _load():
             lib.orc_backward_ex.argtypes = [C.POINTER(_View), C.POINTER(_Params), C.POINTER(_Window),
                                             C.POINTER(C.c_double), C.POINTER(C.c_double),
                                             C.POINTER(C.c_double), C.POINTER(C.c_double),
-                                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(_InvUV)]
+                                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(_InvUV),
+                                            C.POINTER(C.c_double)]
             _lib = lib
     return _lib
 
@@ -118,6 +119,7 @@ class _Inputs:
         self.faces = np.ascontiguousarray(np.asarray(mesh.faces, dtype=np.int32))
         tex = getattr(mesh, "tex", None)
         self.tex = _f64(tex)
+        self.ntex = _f64(getattr(mesh, "ntex", None))
         v = _View()
         v.n_verts, v.n_faces = self.pos.shape[0], self.faces.shape[0]
         v.pos, v.col, v.uv = _dp(self.pos), _dp(self.col), _dp(self.uv)
@@ -128,6 +130,7 @@ class _Inputs:
         v.mvp[:] = [float(x) for x in np.asarray(view.mvp, np.float64).reshape(16)]
         v.light[:] = [float(x) for x in np.asarray(view.light, np.float64).reshape(3)]
         v.width, v.height = int(view.width), int(view.height)
+        v.ntex = _dp(self.ntex)
         self.view = v
         p = _Params()
         # the soft-raster parameters reach the CUDA path as float32: use the same values
@@ -175,12 +178,14 @@ def render(mesh, view, params, window=None, brute_force=False):
     return res
 
 
-def backward(mesh, view, params, grad_rgba, window=None, brute_force=False, camera=False, inverse_uv=None):
+def backward(mesh, view, params, grad_rgba, window=None, brute_force=False, camera=False, inverse_uv=None,
+             want_ntex=False):
     """Adjoint of ``render`` for dL/d(rgba) = ``grad_rgba [h,w,4]`` over ``window``.
 
     Returns ``(grad_pos [V,3], grad_col [V,3] or None, grad_tex [Ht,Wt,4] or None)``,
     and with ``camera`` also ``grad_mvp [16]`` (row-major, as ``view.mvp``) and
     ``grad_light [3]`` (Sec. 3.4.1: the camera and light parameters of Theta).
+    With ``want_ntex`` the normal-map texel gradient ``[Ht,Wt,4]`` (shade_mode 3) follows.
     With ``inverse_uv = (jitter, pix_base)`` the texel gradient is not accumulated and
     the inverse-UV writes of the window's samples are returned last, as a dict of
     arrays (see ``inverse_uv_texels``).
@@ -194,6 +199,7 @@ def backward(mesh, view, params, grad_rgba, window=None, brute_force=False, came
     gt = np.zeros_like(inp.tex) if inp.tex is not None and inverse_uv is None else None
     gm = np.zeros(16) if camera else None
     gl = np.zeros(3) if camera else None
+    gnt = np.zeros_like(inp.ntex) if (want_ntex and inp.ntex is not None) else None
     inv, rec = None, None
     if inverse_uv is not None:
         cap = win.w * win.h * params.K
@@ -206,10 +212,12 @@ def backward(mesh, view, params, grad_rgba, window=None, brute_force=False, came
         inv.texel = _ip(rec["texel"])
         inv.m_tex, inv.m_cand, inv.gA = _dp(rec["m_tex"]), _dp(rec["m_cand"]), _dp(rec["gA"])
     st = lib.orc_backward_ex(C.byref(inp.view), C.byref(inp.params), C.byref(win), _dp(g), _dp(gp), _dp(gc),
-                             _dp(gt), _dp(gm), _dp(gl), C.byref(inv) if inv is not None else None)
+                             _dp(gt), _dp(gm), _dp(gl), C.byref(inv) if inv is not None else None, _dp(gnt))
     if st & 1:
         raise ValueError("oracle: invalid argument")
     out = (gp, gc, gt, gm, gl) if camera else (gp, gc, gt)
+    if want_ntex:
+        out = out + (gnt,)
     if rec is not None:
         rec = {k: v[:inv.n] for k, v in rec.items()}
         out = out + (rec,)

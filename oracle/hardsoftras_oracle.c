@@ -30,7 +30,8 @@
  *                     extend the hard face, Sec. 3.4.2)
  *   9. normals        area-weighted vertex normals (listing BuildNormalCompute)
  *  10. texture        bilinear, texel centres at i + 1/2, REPEAT wrap
- *  11. shading        vertex colour / unlit texture / texture * max(0, n.l)
+ *  11. shading        vertex colour / unlit texture / texture * max(0, n.l) /
+ *                     texture * max(0, n'.l) with n' from a tangent-space normal map
  *  12. D_k = sigmoid(dist_k / sigma)                      (Sec. 3.4.3)
  *  13. S^H, edge mask E by a Chebyshev window of radius rho (Sec. 3.4.3)
  *  14-16. blend: I = E I^e + (1 - E) I^ne for colour and silhouette
@@ -57,13 +58,15 @@ typedef struct {
     double mvp[16];       /* row-major, clip = mvp (p, 1) */
     double light[3];
     int32_t width, height;
+    const double *ntex;   /* [tex_h][tex_w][4] tangent-space normal map (shade_mode 3) or NULL */
 } orc_view;
 
 typedef struct {
     int32_t K;
     double r, sigma, delta;
     int32_t edge_mode;  /* 0 edge mask, 1 E = 1 everywhere, 2 E = 0 everywhere */
-    int32_t shade_mode; /* 0 vertex colour, 1 unlit texture, 2 texture * Lambert */
+    int32_t shade_mode; /* 0 vertex colour, 1 unlit texture, 2 texture * Lambert,
+                           3 texture * Lambert with a tangent-space normal map */
     int32_t brute_force;/* 1: every face at every pixel; 0: same result, bbox pre-test */
 } orc_params;
 
@@ -395,19 +398,24 @@ static bil_t bilinear_coords(const orc_view *v, double u, double vv)
     return b;
 }
 
-static const double *texel(const orc_view *v, int ix, int iy)
+static const double *texel_of(const orc_view *v, const double *tex, int ix, int iy)
 {
-    return v->tex + 4 * ((size_t)iy * v->tex_w + ix);
+    return tex + 4 * ((size_t)iy * v->tex_w + ix);
 }
 
-static void bilinear_sample(const orc_view *v, const bil_t *b, double out[3])
+static const double *texel(const orc_view *v, int ix, int iy) { return texel_of(v, v->tex, ix, iy); }
+
+/* bilinear sample of `tex` (the albedo or the normal map: same size and addressing) */
+static void bilinear_sample_of(const orc_view *v, const double *tex, const bil_t *b, double out[3])
 {
-    const double *t00 = texel(v, b->ix[0], b->iy[0]), *t10 = texel(v, b->ix[1], b->iy[0]);
-    const double *t01 = texel(v, b->ix[0], b->iy[1]), *t11 = texel(v, b->ix[1], b->iy[1]);
+    const double *t00 = texel_of(v, tex, b->ix[0], b->iy[0]), *t10 = texel_of(v, tex, b->ix[1], b->iy[0]);
+    const double *t01 = texel_of(v, tex, b->ix[0], b->iy[1]), *t11 = texel_of(v, tex, b->ix[1], b->iy[1]);
     for (int c = 0; c < 3; ++c)
         out[c] = (1 - b->fx) * (1 - b->fy) * t00[c] + b->fx * (1 - b->fy) * t10[c] +
                  (1 - b->fx) * b->fy * t01[c] + b->fx * b->fy * t11[c];
 }
+
+static void bilinear_sample(const orc_view *v, const bil_t *b, double out[3]) { bilinear_sample_of(v, v->tex, b, out); }
 
 typedef struct {
     double b[3];      /* perspective-correct barycentrics */
@@ -416,6 +424,11 @@ typedef struct {
     bil_t bil;
     double albedo[3];
     double m[3], mlen, n[3], ndl; /* interpolated normal and Lambert term */
+    /* normal map (shade_mode 3): face tangent Tf and handedness h (sign of the UV
+       determinant) from the object-space edges and UV differences; T' = normalize(Tf - n (n.Tf)),
+       B' = h n x T'; map value t, nt = 2 t - 1; m' = nt0 T' + nt1 B' + nt2 n, n' = m' / |m'| */
+    double Tf[3], h, e1[3], e2[3], duv[2][2], idet;
+    double tau[3], tl, Tp[3], Bp[3], nt[3], mp[3], mpl, np[3];
     double C[3];      /* shaded colour */
 } shade_t;
 
@@ -452,7 +465,34 @@ static void shade(const orc_view *v, const orc_params *prm, const face_t *t, con
     }
     s->mlen = sqrt(s->m[0] * s->m[0] + s->m[1] * s->m[1] + s->m[2] * s->m[2]);
     for (int c = 0; c < 3; ++c) s->n[c] = s->mlen > 0 ? s->m[c] / s->mlen : 0.0;
-    s->ndl = s->n[0] * v->light[0] + s->n[1] * v->light[1] + s->n[2] * v->light[2];
+    const double *sn = s->n;
+    if (prm->shade_mode == 3) {
+        const double *P0 = v->pos + 3 * t->vi[0], *P1 = v->pos + 3 * t->vi[1], *P2 = v->pos + 3 * t->vi[2];
+        const double *U0 = v->uv + 2 * t->vi[0], *U1 = v->uv + 2 * t->vi[1], *U2 = v->uv + 2 * t->vi[2];
+        for (int c = 0; c < 3; ++c) { s->e1[c] = P1[c] - P0[c]; s->e2[c] = P2[c] - P0[c]; }
+        for (int k = 0; k < 2; ++k) { s->duv[0][k] = U1[k] - U0[k]; s->duv[1][k] = U2[k] - U0[k]; }
+        double det = s->duv[0][0] * s->duv[1][1] - s->duv[1][0] * s->duv[0][1];
+        s->idet = det != 0 ? 1.0 / det : 0.0;
+        s->h = det < 0 ? -1.0 : 1.0;
+        for (int c = 0; c < 3; ++c) {
+            s->Tf[c] = (s->e1[c] * s->duv[1][1] - s->e2[c] * s->duv[0][1]) * s->idet;
+        }
+        double nT = sn[0] * s->Tf[0] + sn[1] * s->Tf[1] + sn[2] * s->Tf[2];
+        for (int c = 0; c < 3; ++c) s->tau[c] = s->Tf[c] - sn[c] * nT;
+        s->tl = sqrt(s->tau[0] * s->tau[0] + s->tau[1] * s->tau[1] + s->tau[2] * s->tau[2]);
+        for (int c = 0; c < 3; ++c) s->Tp[c] = s->tl > 0 ? s->tau[c] / s->tl : 0.0;
+        s->Bp[0] = s->h * (sn[1] * s->Tp[2] - sn[2] * s->Tp[1]);
+        s->Bp[1] = s->h * (sn[2] * s->Tp[0] - sn[0] * s->Tp[2]);
+        s->Bp[2] = s->h * (sn[0] * s->Tp[1] - sn[1] * s->Tp[0]);
+        double tv[3];
+        bilinear_sample_of(v, v->ntex, &s->bil, tv);
+        for (int c = 0; c < 3; ++c) s->nt[c] = 2.0 * tv[c] - 1.0;
+        for (int c = 0; c < 3; ++c) s->mp[c] = s->nt[0] * s->Tp[c] + s->nt[1] * s->Bp[c] + s->nt[2] * sn[c];
+        s->mpl = sqrt(s->mp[0] * s->mp[0] + s->mp[1] * s->mp[1] + s->mp[2] * s->mp[2]);
+        for (int c = 0; c < 3; ++c) s->np[c] = s->mpl > 0 ? s->mp[c] / s->mpl : 0.0;
+        sn = s->np;
+    }
+    s->ndl = sn[0] * v->light[0] + sn[1] * v->light[1] + sn[2] * v->light[2];
     double lam = s->ndl > 0 ? s->ndl : 0.0;
     for (int c = 0; c < 3; ++c) s->C[c] = s->albedo[c] * lam;
 }
@@ -491,6 +531,8 @@ static int check_args(const orc_view *v, const orc_params *prm, const orc_window
         w->x0 + w->w > v->width || w->y0 + w->h > v->height) return 0;
     if (prm->shade_mode == 0 && !v->col) return 0;
     if (prm->shade_mode > 0 && (!v->uv || !v->tex || v->tex_w <= 0 || v->tex_h <= 0)) return 0;
+    if (prm->shade_mode == 3 && !v->ntex) return 0;
+    if (prm->shade_mode < 0 || prm->shade_mode > 3) return 0;
     return 1;
 }
 
@@ -518,7 +560,7 @@ static void ctx_build(ctx_t *c, const orc_view *v, const orc_params *prm, const 
     for (size_t i = 0; i < ne; ++i) c->sh[i] = (uint8_t)(c->pix[i].n > 0 && c->pix[i].f[0].hard);
     c->N = (double *)malloc(sizeof(double) * 3 * (size_t)(v->n_verts > 0 ? v->n_verts : 1));
     c->Mn = (double *)malloc(sizeof(double) * 3 * (size_t)(v->n_verts > 0 ? v->n_verts : 1));
-    if (prm->shade_mode == 2) vertex_normals(v, c->N, c->Mn);
+    if (prm->shade_mode >= 2) vertex_normals(v, c->N, c->Mn);
 }
 
 static void ctx_free(ctx_t *c)
@@ -675,12 +717,15 @@ static void lam_grad(const face_t *t, const frag_t *fr, double px, double py, co
     cg->X[0] += gA2 * (-wy + uy); cg->Y[0] += gA2 * (wx - ux);
 }
 
-static void tex_backward(const orc_view *v, const shade_t *s, const double gA[3], double *gtex, double guv[2])
+/* adjoint of the bilinear sample of `tex` at the layer's UV: texel gradients into gtex
+   (if not NULL) and the UV gradient */
+static void tex_backward_of(const orc_view *v, const double *tex, const shade_t *s, const double gA[3], double *gtex,
+                            double guv[2])
 {
     const bil_t *b = &s->bil;
     double w00 = (1 - b->fx) * (1 - b->fy), w10 = b->fx * (1 - b->fy), w01 = (1 - b->fx) * b->fy, w11 = b->fx * b->fy;
-    const double *t00 = texel(v, b->ix[0], b->iy[0]), *t10 = texel(v, b->ix[1], b->iy[0]);
-    const double *t01 = texel(v, b->ix[0], b->iy[1]), *t11 = texel(v, b->ix[1], b->iy[1]);
+    const double *t00 = texel_of(v, tex, b->ix[0], b->iy[0]), *t10 = texel_of(v, tex, b->ix[1], b->iy[0]);
+    const double *t01 = texel_of(v, tex, b->ix[0], b->iy[1]), *t11 = texel_of(v, tex, b->ix[1], b->iy[1]);
     double gx = 0, gy = 0;
     for (int c = 0; c < 3; ++c) {
         if (gtex) {
@@ -694,6 +739,59 @@ static void tex_backward(const orc_view *v, const shade_t *s, const double gA[3]
     }
     guv[0] = gx * v->tex_w;
     guv[1] = gy * v->tex_h;
+}
+
+static void tex_backward(const orc_view *v, const shade_t *s, const double gA[3], double *gtex, double guv[2])
+{
+    tex_backward_of(v, v->tex, s, gA, gtex, guv);
+}
+
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static void cross3(const double *a, const double *b, double *o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* adjoint of the normal-mapped shading normal (shade_mode 3) for dL/dn' = gs l: the
+   normal-map texel gradients (grad_ntex), the UV gradient of the map sample (guv), the
+   object-space corner gradients through the face tangent (grad_pos), and dL/dn of the
+   smooth interpolated normal (gn, for the vertex-normal chain) */
+static void normal_map_backward(const orc_view *v, const face_t *t, const shade_t *s, double gs, double gn[3],
+                                double *grad_ntex, double guv[2], double *grad_pos)
+{
+    double gnp[3], gmp[3], gTp[3], gBp[3], tmp[3], gtau[3], gTf[3];
+    for (int c = 0; c < 3; ++c) gnp[c] = gs * v->light[c];
+    double d = dot3(s->np, gnp);
+    for (int c = 0; c < 3; ++c) gmp[c] = (gnp[c] - s->np[c] * d) / s->mpl;     /* n' = m' / |m'| */
+    /* m' = nt0 T' + nt1 B' + nt2 n, nt = 2 t - 1 */
+    double gt[3] = {2.0 * dot3(gmp, s->Tp), 2.0 * dot3(gmp, s->Bp), 2.0 * dot3(gmp, s->n)};
+    tex_backward_of(v, v->ntex, s, gt, grad_ntex, guv);
+    for (int c = 0; c < 3; ++c) { gTp[c] = s->nt[0] * gmp[c]; gBp[c] = s->nt[1] * gmp[c]; gn[c] = s->nt[2] * gmp[c]; }
+    /* B' = h n x T' */
+    cross3(s->Tp, gBp, tmp);
+    for (int c = 0; c < 3; ++c) gn[c] += s->h * tmp[c];
+    cross3(gBp, s->n, tmp);
+    for (int c = 0; c < 3; ++c) gTp[c] += s->h * tmp[c];
+    /* T' = tau / |tau| */
+    double dT = dot3(s->Tp, gTp);
+    for (int c = 0; c < 3; ++c) gtau[c] = s->tl > 0 ? (gTp[c] - s->Tp[c] * dT) / s->tl : 0.0;
+    /* tau = Tf - n (n . Tf) */
+    double nT = dot3(s->n, s->Tf), ng = dot3(s->n, gtau);
+    for (int c = 0; c < 3; ++c) {
+        gTf[c] = gtau[c] - s->n[c] * ng;
+        gn[c] += -nT * gtau[c] - s->Tf[c] * ng;
+    }
+    /* Tf = (e1 dv2 - e2 dv1) / det, e1 = P1 - P0, e2 = P2 - P0 (the UVs are constants) */
+    if (grad_pos)
+        for (int c = 0; c < 3; ++c) {
+            double ge1 = gTf[c] * s->duv[1][1] * s->idet, ge2 = -gTf[c] * s->duv[0][1] * s->idet;
+            grad_pos[3 * (size_t)t->vi[1] + c] += ge1;
+            grad_pos[3 * (size_t)t->vi[2] + c] += ge2;
+            grad_pos[3 * (size_t)t->vi[0] + c] -= ge1 + ge2;
+        }
 }
 
 /* Inverse UV (Sec. 3.3.2, Alg. 1): the texture-gradient lookup of the paper's Vulkan
@@ -742,7 +840,7 @@ static void inv_uv_write(const orc_view *v, const orc_params *prm, const ctx_t *
    (the light treated as a free 3-vector, as the forward uses it).  Either may be NULL. */
 int orc_backward_ex(const orc_view *v, const orc_params *prm, const orc_window *w,
                     const double *grad_rgba, double *grad_pos, double *grad_col, double *grad_tex,
-                    double *grad_mvp, double *grad_light, orc_inv_uv *inv)
+                    double *grad_mvp, double *grad_light, orc_inv_uv *inv, double *grad_ntex)
 {
     if (!check_args(v, prm, w) || !grad_rgba) return ORC_BAD_ARG;
     ctx_t c;
@@ -807,18 +905,20 @@ int orc_backward_ex(const orc_view *v, const orc_params *prm, const orc_window *
                             gb[i] += gC[k][ch] * v->col[3 * t->vi[i] + ch];
                         }
                 } else {
-                    double gA[3];
+                    double gA[3], guv_n[2] = {0, 0};
                     if (prm->shade_mode == 1) {
                         for (int ch = 0; ch < 3; ++ch) gA[ch] = gC[k][ch];
                     } else {
                         double lam = sk->ndl > 0 ? sk->ndl : 0.0;
                         double gs = 0;
                         for (int ch = 0; ch < 3; ++ch) { gA[ch] = gC[k][ch] * lam; gs += gC[k][ch] * sk->albedo[ch]; }
-                        if (sk->ndl > 0 && sk->mlen > 0) {
-                            /* C = albedo max(0, n.l): dL/dl = (sum_c gC_c albedo_c) n */
+                        const int nmap = prm->shade_mode == 3;
+                        if (sk->ndl > 0 && sk->mlen > 0 && (!nmap || sk->mpl > 0)) {
+                            /* C = albedo max(0, n.l): dL/dl = (sum_c gC_c albedo_c) n (n' with a map) */
                             if (grad_light)
-                                for (int ch = 0; ch < 3; ++ch) grad_light[ch] += gs * sk->n[ch];
+                                for (int ch = 0; ch < 3; ++ch) grad_light[ch] += gs * (nmap ? sk->np[ch] : sk->n[ch]);
                             double gn[3] = {gs * v->light[0], gs * v->light[1], gs * v->light[2]};
+                            if (nmap) normal_map_backward(v, t, sk, gs, gn, grad_ntex, guv_n, grad_pos);
                             double nd = sk->n[0] * gn[0] + sk->n[1] * gn[1] + sk->n[2] * gn[2];
                             double gm[3];
                             for (int ch = 0; ch < 3; ++ch) gm[ch] = (gn[ch] - sk->n[ch] * nd) / sk->mlen;
@@ -833,7 +933,7 @@ int orc_backward_ex(const orc_view *v, const orc_params *prm, const orc_window *
                     tex_backward(v, sk, gA, grad_tex, guv);
                     if (inv && (E || k == 0)) inv_uv_write(v, prm, &c, t, fr->id, X, Y, k, gA, inv);
                     for (int i = 0; i < 3; ++i)
-                        gb[i] += guv[0] * v->uv[2 * t->vi[i]] + guv[1] * v->uv[2 * t->vi[i] + 1];
+                        gb[i] += (guv[0] + guv_n[0]) * v->uv[2 * t->vi[i]] + (guv[1] + guv_n[1]) * v->uv[2 * t->vi[i] + 1];
                 }
                 /* perspective-correct barycentrics -> screen barycentrics and 1/w */
                 double bdot = sk->b[0] * gb[0] + sk->b[1] * gb[1] + sk->b[2] * gb[2];
@@ -881,7 +981,7 @@ int orc_backward_ex(const orc_view *v, const orc_params *prm, const orc_window *
             }
         }
         /* normals -> positions: n_v = m_v / |m_v|, m_v = sum of face cross products */
-        if (grad_pos && prm->shade_mode == 2) {
+        if (grad_pos && prm->shade_mode >= 2) {
             double *gM = (double *)calloc(3 * (size_t)(v->n_verts > 0 ? v->n_verts : 1), sizeof(double));
             for (int i = 0; i < v->n_verts; ++i) {
                 const double *m = c.Mn + 3 * i, *n = c.N + 3 * i, *gn = gN + 3 * i;
@@ -921,7 +1021,7 @@ int orc_backward_ex(const orc_view *v, const orc_params *prm, const orc_window *
 int orc_backward(const orc_view *v, const orc_params *prm, const orc_window *w,
                  const double *grad_rgba, double *grad_pos, double *grad_col, double *grad_tex)
 {
-    return orc_backward_ex(v, prm, w, grad_rgba, grad_pos, grad_col, grad_tex, NULL, NULL, NULL);
+    return orc_backward_ex(v, prm, w, grad_rgba, grad_pos, grad_col, grad_tex, NULL, NULL, NULL, NULL);
 }
 
 /* size of the structs, so the Python loader can verify its layout */

@@ -252,6 +252,7 @@ class Mesh:
     col: Optional[np.ndarray] = None   # float32 [V, 3]
     uv: Optional[np.ndarray] = None    # float32 [V, 2]
     tex: Optional[np.ndarray] = None   # float32/float16 [Ht, Wt, 4]
+    ntex: Optional[np.ndarray] = None  # tangent-space normal map, like tex (shade_mode 3)
 
 
 @dataclasses.dataclass

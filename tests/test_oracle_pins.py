@@ -376,7 +376,10 @@ def _fd_scene(shade_mode, seed):
     uv = g.uniform(0.05, 0.95, (5, 2))
     tex = np.zeros((6, 5, 4))
     tex[..., :3] = g.random((6, 5, 3))
-    mesh = synth.Mesh(pos, faces, col=col, uv=uv, tex=tex)
+    ntex = np.zeros((6, 5, 4))   # tangent-space normals near +z: x, y in 0.5 +- 0.2, z in [0.75, 1]
+    ntex[..., :2] = 0.5 + g.uniform(-0.2, 0.2, (6, 5, 2))
+    ntex[..., 2] = g.uniform(0.75, 1.0, (6, 5))
+    mesh = synth.Mesh(pos, faces, col=col, uv=uv, tex=tex, ntex=ntex)
     view = synth.View(synth.camera_mvp((0.4, 0.3, 2.2), 28, 28).astype(np.float64), 0, 28, 28,
                       light=np.array([0.48, 0.6, 0.64]))
     return mesh, view
@@ -386,7 +389,8 @@ def _state(r):
     return (r["ids"].tobytes(), r["hard"].tobytes(), r["sh"].tobytes(), r["edge"].tobytes())
 
 
-@pytest.mark.parametrize("shade_mode,edge_mode,K", [(0, 0, 3), (0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 1, 3), (2, 0, 3), (2, 1, 2)])
+@pytest.mark.parametrize("shade_mode,edge_mode,K", [(0, 0, 3), (0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 1, 3), (2, 0, 3), (2, 1, 2),
+                                                    (3, 0, 3), (3, 1, 2), (3, 2, 1)])
 def test_adjoint_matches_central_differences(shade_mode, edge_mode, K):
     mesh, view = _fd_scene(shade_mode, 7 + shade_mode)
     r_px = 3.0
@@ -394,7 +398,7 @@ def test_adjoint_matches_central_differences(shade_mode, edge_mode, K):
     g = np.random.default_rng(5).normal(size=(28, 28, 4))
     base = oracle.render(mesh, view, prm)
     st0 = _state(base)
-    gp, gc, gt = oracle.backward(mesh, view, prm, g)
+    gp, gc, gt, gnt = oracle.backward(mesh, view, prm, g, want_ntex=True)
 
     def loss(m):
         r = oracle.render(m, view, prm)
@@ -435,6 +439,14 @@ def test_adjoint_matches_central_differences(shade_mode, edge_mode, K):
             if d is not None:
                 num.append(d)
                 ana.append(gt[tuple(idx)])
+    if shade_mode == 3:
+        nz = np.argwhere(np.abs(gnt) > 0)
+        assert len(nz) > 0
+        for idx in nz[:: max(1, len(nz) // 40)]:
+            d = fd("ntex", tuple(idx), 1e-5)
+            if d is not None:
+                num.append(d)
+                ana.append(gnt[tuple(idx)])
     num, ana = np.array(num), np.array(ana)
     assert checked >= 12
     assert np.abs(ana).max() > 0
@@ -443,7 +455,7 @@ def test_adjoint_matches_central_differences(shade_mode, edge_mode, K):
     assert np.abs(num - ana).max() < 1e-5 * np.abs(ana).max()
 
 
-@pytest.mark.parametrize("shade_mode,edge_mode,K", [(0, 0, 3), (1, 1, 2), (2, 0, 3), (2, 1, 2), (2, 2, 1)])
+@pytest.mark.parametrize("shade_mode,edge_mode,K", [(0, 0, 3), (1, 1, 2), (2, 0, 3), (2, 1, 2), (2, 2, 1), (3, 0, 3)])
 def test_camera_and_light_adjoint_match_central_differences(shade_mode, edge_mode, K):
     """dL/dMVP and dL/dlight (the camera and light parameters of Theta, Sec. 3.4.1)
     against central differences of the oracle's forward; the depth row of the matrix
@@ -480,7 +492,7 @@ def test_camera_and_light_adjoint_match_central_differences(shade_mode, edge_mod
         if d is not None:
             num.append(d)
             ana.append(gl[c])
-    if shade_mode != 2:
+    if shade_mode < 2:
         assert np.all(gl == 0)
     else:
         assert np.abs(gl).max() > 0
