@@ -92,6 +92,8 @@ typedef struct {
     const int32_t *faces;        /* [sum n_faces][3] vertex indices local to the face's mesh */
     const void *tex;             /* [sum texels][4] RGBx texels (row-major per mesh, v = 0 at row 0) */
     int32_t tex_dtype;           /* DRESSI_TEX_F32 or DRESSI_TEX_F16 */
+    const void *ntex;            /* shade_mode 3: tangent-space normal map, laid out and typed
+                                    like tex (same texel offsets and sizes); NULL otherwise */
 } dressi_scene;
 
 /* One view (host struct, passed as a host array). */
@@ -113,7 +115,12 @@ typedef struct {
     float gamma;        /* accepted for interface compatibility; unused (the paper drops depth
                            from the colour blend) */
     int32_t edge_mode;  /* 0 edge mask from S^H, 1 E = 1 everywhere (SoftRas-like), 2 E = 0 (hard) */
-    int32_t shade_mode; /* 0 vertex colour, 1 unlit texture, 2 texture * max(0, n.l) */
+    int32_t shade_mode; /* 0 vertex colour, 1 unlit texture, 2 texture * max(0, n.l),
+                           3 texture * max(0, n'.l) with n' from the normal map ntex: map value
+                           t, nt = 2 t - 1 in the face's tangent frame (tangent from the object
+                           edges and UV differences, orthogonalised against the interpolated
+                           normal n; bitangent h n x T', h the sign of the UV determinant),
+                           n' = normalize(nt0 T' + nt1 B' + nt2 n) */
     int32_t texgrad_mode; /* 0 warp-aggregated atomics, 1 texel-space gather (deterministic),
                              2 inverse UV (Sec. 3.3.2, Alg. 1; approximate: each texel takes the
                              dL/d(albedo) of the last shaded sample that lands on it) */
@@ -190,13 +197,15 @@ DRESSI_API int dressi_backward(const dressi_scene *scene, const dressi_view *vie
                 (row-major like dressi_view.mvp; row 2, the depth row, stays 0: depth only
                 orders the layers, a discrete choice).
      grad_light DEVICE [n_views][3] float or NULL, OVERWRITTEN with dL/dlight per view
-                (shade_mode 2; the light is used as given, not renormalised; 0 otherwise).
+                (shade_mode 2, 3; the light is used as given, not renormalised; 0 otherwise).
+     grad_ntex  DEVICE [sum texels][4] float or NULL, OVERWRITTEN with the normal-map texel
+                gradient (shade_mode 3; texgrad_mode 0: atomics); channel 3 stays zero.
    All other arguments as for dressi_backward, which is this call with both NULL. */
 DRESSI_API int dressi_backward_ex(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
                                   const dressi_params *params, const float *grad_rgba, const int32_t *layer_ids,
                                   int64_t n_pix, float *grad_pos, float *grad_col, float *grad_tex,
-                                  float *grad_mvp, float *grad_light, void *ws, size_t ws_bytes,
-                                  int32_t *dev_status, void *stream);
+                                  float *grad_mvp, float *grad_light, float *grad_ntex, void *ws,
+                                  size_t ws_bytes, int32_t *dev_status, void *stream);
 
 /* Size of the library's static device scratch array used by
    dressi_forward_static_scratch (bytes; held on every GPU that loads the library). */

@@ -28,7 +28,7 @@ class DressiMesh(C.Structure):
 class DressiScene(C.Structure):
     _fields_ = [("n_meshes", C.c_int32), ("meshes", C.POINTER(DressiMesh)), ("n_verts_total", C.c_int64),
                 ("pos", C.c_void_p), ("col", C.c_void_p), ("uv", C.c_void_p), ("faces", C.c_void_p),
-                ("tex", C.c_void_p), ("tex_dtype", C.c_int32)]
+                ("tex", C.c_void_p), ("tex_dtype", C.c_int32), ("ntex", C.c_void_p)]
 
 
 class DressiView(C.Structure):
@@ -56,7 +56,8 @@ SIGNATURES = {
                                   C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
     "dressi_backward_ex": (C.c_int, [C.POINTER(DressiScene), C.POINTER(DressiView), C.c_int32, C.POINTER(DressiParams),
                                      C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
-                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
+                                     C.c_void_p]),
     "dressi_forward_from_layers": (C.c_int, [C.POINTER(DressiScene), C.POINTER(DressiView), C.c_int32,
                                              C.POINTER(DressiParams), C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                              C.c_size_t, C.c_void_p, C.c_void_p]),

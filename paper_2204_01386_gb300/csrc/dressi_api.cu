@@ -65,7 +65,7 @@ static bool check_params(const dressi_params *p)
         !std::isfinite(p->sigma) || !std::isfinite(p->delta))
         return false;
     if (p->edge_mode < 0 || p->edge_mode > 2) return false;
-    if (p->shade_mode < 0 || p->shade_mode > 2) return false;
+    if (p->shade_mode < 0 || p->shade_mode > 3) return false;
     if (p->texgrad_mode < 0 || p->texgrad_mode > 2) return false;
     if (!std::isfinite(p->uv_jitter[0]) || !std::isfinite(p->uv_jitter[1])) return false;
     if (p->tile != 0 && p->tile != 16 && p->tile != 32) return false;
@@ -108,6 +108,7 @@ static bool make_plan(const dressi_scene *sc, const dressi_view *views, int n_vi
     if (!sc->pos || !sc->faces) return false;
     if (p->shade_mode == 0 && !sc->col) return false;
     if (textured && (!sc->uv || !sc->tex)) return false;
+    if (p->shade_mode == 3 && !sc->ntex) return false;
 
     P.views.resize(n_views);
     long long vrec = 0, view_faces = 0, view_pixels = 0;
@@ -253,6 +254,7 @@ static Globals make_globals(const dressi_scene *sc, const dressi_params *p, cons
     g.uv = sc->uv;
     g.faces = sc->faces;
     g.tex = sc->tex;
+    g.ntex = sc->ntex;
     g.vrec = reinterpret_cast<VRec *>(ws + L.vrec);
     g.frec = reinterpret_cast<FaceRec *>(ws + L.frec);
     g.tile_count = reinterpret_cast<int *>(ws + L.tile_count);
@@ -290,7 +292,7 @@ static void run_setup(const Globals &g, const Plan &P, char *ws, bool need_bins,
     upload(P.meshes.data(), sizeof(MeshK) * P.meshes.size(), ws + L.meshes, s);
     launch_vertex(g, (int)P.views.size(), P.max_nv_view, s);
     launch_face(g, (int)P.views.size(), P.max_nf_view, s);
-    if (g.shade_mode == 2) {
+    if (g.shade_mode >= 2) {
         const size_t nv = (size_t)std::max<long long>(g.n_verts_total, 1);
         cudaMemsetAsync(ws + L.adj_off, 0, sizeof(int) * (nv + 1), s);
         cudaMemsetAsync(ws + L.adj_cur, 0, sizeof(int) * nv, s);
@@ -464,13 +466,13 @@ int dressi_backward(const dressi_scene *scene, const dressi_view *views, int32_t
                     int32_t *dev_status, void *stream)
 {
     return dressi_backward_ex(scene, views, n_views, params, grad_rgba, layer_ids, n_pix, grad_pos, grad_col, grad_tex,
-                              nullptr, nullptr, ws, ws_bytes, dev_status, stream);
+                              nullptr, nullptr, nullptr, ws, ws_bytes, dev_status, stream);
 }
 
 int dressi_backward_ex(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
                        const dressi_params *params, const float *grad_rgba, const int32_t *layer_ids, int64_t n_pix,
                        float *grad_pos, float *grad_col, float *grad_tex, float *grad_mvp, float *grad_light,
-                       void *ws, size_t ws_bytes, int32_t *dev_status, void *stream)
+                       float *grad_ntex, void *ws, size_t ws_bytes, int32_t *dev_status, void *stream)
 {
     Plan P;
     if (!grad_rgba || !grad_pos || !dev_status || n_pix < 1) return DRESSI_ERR_ARG;
@@ -487,6 +489,8 @@ int dressi_backward_ex(const dressi_scene *scene, const dressi_view *views, int3
     g.gtex = params->shade_mode != 0 ? grad_tex : nullptr;
     g.gmvp = grad_mvp;
     g.glight = grad_light;
+    g.gntex = params->shade_mode == 3 ? grad_ntex : nullptr;
+    if (g.gntex && P.n_texels > 0) cudaMemsetAsync(grad_ntex, 0, sizeof(float) * 4 * (size_t)P.n_texels, s);
     if (grad_mvp) cudaMemsetAsync(grad_mvp, 0, sizeof(float) * 16 * (size_t)n_views, s);
     if (grad_light) cudaMemsetAsync(grad_light, 0, sizeof(float) * 3 * (size_t)n_views, s);
     const long long nvt = scene->n_verts_total;
@@ -494,7 +498,7 @@ int dressi_backward_ex(const dressi_scene *scene, const dressi_view *views, int3
     if (grad_col) cudaMemsetAsync(grad_col, 0, sizeof(float) * 3 * (size_t)nvt, s);
     if (grad_tex && P.n_texels > 0) cudaMemsetAsync(grad_tex, 0, sizeof(float) * 4 * (size_t)P.n_texels, s);
     cudaMemsetAsync(w + P.lay.sgrad, 0, sizeof(float4) * (size_t)std::max<long long>(P.lay.n_vrec, 1), s);
-    if (params->shade_mode == 2)
+    if (params->shade_mode >= 2)
         cudaMemsetAsync(w + P.lay.ngrad, 0, sizeof(float4) * (size_t)std::max<long long>(nvt, 1), s);
     const bool tex_records = g.gtex && P.lay.tg_slots > 0;
     const bool gather = tex_records && params->texgrad_mode == 1;
@@ -513,7 +517,7 @@ int dressi_backward_ex(const dressi_scene *scene, const dressi_view *views, int3
                                           cudaMemcpyDeviceToDevice, s);
     }
     launch_vertex_bwd(g, (int)P.views.size(), P.max_nv_view, (int)P.meshes.size(), P.max_nf,
-                      params->shade_mode == 2, s);
+                      params->shade_mode >= 2, s);
     return cudaGetLastError() == cudaSuccess ? DRESSI_OK : DRESSI_ERR_LAUNCH;
 }
 

@@ -97,6 +97,7 @@ struct Globals {
     const float *pos, *col, *uv;
     const int *faces;
     const void *tex;
+    const void *ntex;     // shade_mode 3: normal map, laid out like tex
     VRec *vrec;
     FaceRec *frec;        // per (view, face): the face's record, written by the setup
     int *tile_count, *tile_off, *tile_cursor, *lists;
@@ -122,6 +123,7 @@ struct Globals {
     float4 *ngrad;        // [n_verts_total] gradient of the normalized vertex normals
     float *gpos, *gcol, *gtex;
     float *gmvp;          // [n_views][16] dL/dMVP or nullptr
+    float *gntex;         // shade_mode 3: [sum texels][4] normal-map texel gradient or nullptr
     int *inv_uv;          // texgrad_mode 2: [sum texels] last sample written per texel (-1 none)
     float uv_jx, uv_jy;   // texgrad_mode 2: sample offset from the pixel centre
     float *glight;        // [n_views][3] dL/dlight or nullptr

@@ -171,6 +171,7 @@ struct Shade {
     float Xt[3], Yt[3];   // texel-space corner coordinates relative to corner 0
     // Lambert
     float n[3], mlen, ndl;
+    float np[3];          // the shading normal: n, or the normal-mapped n' (shade_mode 3)
 };
 
 __device__ __forceinline__ float4 load_texel(const Globals &g, long long idx)
@@ -182,6 +183,17 @@ __device__ __forceinline__ float4 load_texel(const Globals &g, long long idx)
         return make_float4(fa.x, fa.y, fb.x, fb.y);
     }
     return __ldg(reinterpret_cast<const float4 *>(g.tex) + idx);
+}
+
+__device__ __forceinline__ float4 load_ntexel(const Globals &g, long long idx)
+{
+    if (g.tex_f16) {
+        uint2 raw = __ldg(reinterpret_cast<const uint2 *>(g.ntex) + idx);
+        __half2 a = *reinterpret_cast<__half2 *>(&raw.x), b = *reinterpret_cast<__half2 *>(&raw.y);
+        float2 fa = __half22float2(a), fb = __half22float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+    return __ldg(reinterpret_cast<const float4 *>(g.ntex) + idx);
 }
 
 __device__ __forceinline__ int wrapi(int i, int n)
@@ -213,9 +225,76 @@ __device__ __forceinline__ void texcoord(const float b[3], const float u[3], flo
     i0 = (int)fA + (int)ft;
 }
 
+// normal map (shade_mode 3): the face's tangent frame and the mapped normal at the
+// layer's sample.  Tf = (e1 dv2 - e2 dv1) / det from the object-space edges and UV
+// differences, T' = normalize(Tf - n (n . Tf)), B' = h n x T' (h the sign of det); the
+// map value t decodes to nt = 2 t - 1 and n' = m' / |m'|, m' = nt0 T' + nt1 B' + nt2 n.
+// The adjoint rebuilds this from the same inputs.
+struct NMap {
+    float Tf[3], Tp[3], Bp[3], nt[3], np[3];
+    float tl, mpl, h, idet, dv1, dv2, nT;
+    float t00[3], t10[3], t01[3], t11[3];   // the four map texels (for the UV gradient)
+};
+
+__device__ __forceinline__ void nmap_eval(const Globals &g, const MeshK &M, const Shade &S, const float u[3],
+                                          const float v[3], NMap &N)
+{
+    const long long nvt = g.n_verts_total;
+    float P[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) P[i][c] = __ldg(g.pos + c * nvt + M.vert_off + S.vi[i]);
+    const float du1 = fsub(u[1], u[0]), du2 = fsub(u[2], u[0]);
+    N.dv1 = fsub(v[1], v[0]);
+    N.dv2 = fsub(v[2], v[0]);
+    const float det = fsub(fmul(du1, N.dv2), fmul(du2, N.dv1));
+    N.idet = det != 0.f ? __fdiv_rn(1.f, det) : 0.f;
+    N.h = det < 0.f ? -1.f : 1.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        N.Tf[c] = fmul(fsub(fmul(fsub(P[1][c], P[0][c]), N.dv2), fmul(fsub(P[2][c], P[0][c]), N.dv1)), N.idet);
+    N.nT = ffma(S.n[2], N.Tf[2], ffma(S.n[1], N.Tf[1], fmul(S.n[0], N.Tf[0])));
+    float tau[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tau[c] = ffma(-S.n[c], N.nT, N.Tf[c]);
+    N.tl = __fsqrt_rn(ffma(tau[2], tau[2], ffma(tau[1], tau[1], fmul(tau[0], tau[0]))));
+    const float itl = N.tl > 0.f ? __fdiv_rn(1.f, N.tl) : 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) N.Tp[c] = fmul(tau[c], itl);
+    N.Bp[0] = fmul(N.h, fsub(fmul(S.n[1], N.Tp[2]), fmul(S.n[2], N.Tp[1])));
+    N.Bp[1] = fmul(N.h, fsub(fmul(S.n[2], N.Tp[0]), fmul(S.n[0], N.Tp[2])));
+    N.Bp[2] = fmul(N.h, fsub(fmul(S.n[0], N.Tp[1]), fmul(S.n[1], N.Tp[0])));
+    const long long tb = M.tex_off;
+    const float4 a00 = load_ntexel(g, tb + (long long)S.iy[0] * M.tex_w + S.ix[0]);
+    const float4 a10 = load_ntexel(g, tb + (long long)S.iy[0] * M.tex_w + S.ix[1]);
+    const float4 a01 = load_ntexel(g, tb + (long long)S.iy[1] * M.tex_w + S.ix[0]);
+    const float4 a11 = load_ntexel(g, tb + (long long)S.iy[1] * M.tex_w + S.ix[1]);
+    N.t00[0] = a00.x; N.t00[1] = a00.y; N.t00[2] = a00.z;
+    N.t10[0] = a10.x; N.t10[1] = a10.y; N.t10[2] = a10.z;
+    N.t01[0] = a01.x; N.t01[1] = a01.y; N.t01[2] = a01.z;
+    N.t11[0] = a11.x; N.t11[1] = a11.y; N.t11[2] = a11.z;
+    const float gx = fsub(1.f, S.fx), gy = fsub(1.f, S.fy);
+    const float w00 = fmul(gx, gy), w10 = fmul(S.fx, gy), w01 = fmul(gx, S.fy), w11 = fmul(S.fx, S.fy);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float t = ffma(w11, N.t11[c], ffma(w01, N.t01[c], ffma(w10, N.t10[c], fmul(w00, N.t00[c]))));
+        N.nt[c] = ffma(2.f, t, -1.f);
+    }
+    float mp[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) mp[c] = ffma(N.nt[2], S.n[c], ffma(N.nt[1], N.Bp[c], fmul(N.nt[0], N.Tp[c])));
+    N.mpl = __fsqrt_rn(ffma(mp[2], mp[2], ffma(mp[1], mp[1], fmul(mp[0], mp[0]))));
+    const float iml = N.mpl > 0.f ? __fdiv_rn(1.f, N.mpl) : 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) N.np[c] = fmul(mp[c], iml);
+}
+
 // b, C, D and the sampling state of one layer from S.vi, S.iw, S.lam and dist.  Every
 // operation is rounded as written (no contraction left to the compiler), so the kernels
 // that shade a layer -- forward, forward from stored layers, adjoint -- agree bit for bit.
+// X: the kernel has the normal map compiled in (the kernels without it stay lean)
+template <bool X>
 __device__ __forceinline__ void shade(const Globals &g, const ViewK &V, const MeshK &M, float dist, Shade &S)
 {
     float q[3];
@@ -273,7 +352,13 @@ __device__ __forceinline__ void shade(const Globals &g, const ViewK &V, const Me
     S.mlen = __fsqrt_rn(ffma(m[0], m[0], ffma(m[1], m[1], fmul(m[2], m[2]))));
     const float il = S.mlen > 0.f ? __fdiv_rn(1.f, S.mlen) : 0.f;
     S.n[0] = fmul(m[0], il); S.n[1] = fmul(m[1], il); S.n[2] = fmul(m[2], il);
-    S.ndl = ffma(S.n[2], V.light[2], ffma(S.n[1], V.light[1], fmul(S.n[0], V.light[0])));
+    S.np[0] = S.n[0]; S.np[1] = S.n[1]; S.np[2] = S.n[2];
+    if (X && g.shade_mode == 3) {
+        NMap N;
+        nmap_eval(g, M, S, u, v, N);
+        S.np[0] = N.np[0]; S.np[1] = N.np[1]; S.np[2] = N.np[2];
+    }
+    S.ndl = ffma(S.np[2], V.light[2], ffma(S.np[1], V.light[1], fmul(S.np[0], V.light[0])));
     const float sl = fmaxf(S.ndl, 0.f);
     S.C[0] = fmul(S.A[0], sl); S.C[1] = fmul(S.A[1], sl); S.C[2] = fmul(S.A[2], sl);
 }
@@ -285,6 +370,7 @@ struct Layer {
     Shade S;
 };
 
+template <bool X>
 __device__ __forceinline__ bool layer_build(const Globals &g, const ViewK &V, const MeshK &M, int id,
                                             float px, float py, Layer &L)
 {
@@ -293,7 +379,7 @@ __device__ __forceinline__ bool layer_build(const Globals &g, const ViewK &V, co
     frag_lambda(L.R, L.fr, L.S.lam);
 #pragma unroll
     for (int i = 0; i < 3; ++i) { L.S.vi[i] = L.R.vi[i]; L.S.iw[i] = L.R.iw[i]; }
-    shade(g, V, M, L.fr.dist, L.S);
+    shade<X>(g, V, M, L.fr.dist, L.S);
     return true;
 }
 
@@ -367,6 +453,7 @@ __device__ __forceinline__ bool layer_adjoint(const Globals &g, const ViewK &V, 
             }
         } else {
             float gA[3];
+            float gxn = 0.f, gyn = 0.f;   // the normal map's texel-space UV gradient
             if (g.shade_mode == 1) {
                 gA[0] = gC[0]; gA[1] = gC[1]; gA[2] = gC[2];
             } else {
@@ -375,12 +462,83 @@ __device__ __forceinline__ bool layer_adjoint(const Globals &g, const ViewK &V, 
                 if (S.ndl > 0.f && S.mlen > 0.f) {
                     const float gs = gC[0] * S.A[0] + gC[1] * S.A[1] + gC[2] * S.A[2];
                     if (EXTRA && gl) {
-                        // C = A max(0, n.l): dL/dl = (gC . A) n
-                        gl[0] = fmaf(gs, S.n[0], gl[0]);
-                        gl[1] = fmaf(gs, S.n[1], gl[1]);
-                        gl[2] = fmaf(gs, S.n[2], gl[2]);
+                        // C = A max(0, n.l): dL/dl = (gC . A) n (n' with a normal map)
+                        gl[0] = fmaf(gs, S.np[0], gl[0]);
+                        gl[1] = fmaf(gs, S.np[1], gl[1]);
+                        gl[2] = fmaf(gs, S.np[2], gl[2]);
                     }
-                    const float gn[3] = {gs * V.light[0], gs * V.light[1], gs * V.light[2]};
+                    float gn[3] = {gs * V.light[0], gs * V.light[1], gs * V.light[2]};
+                    if (EXTRA && g.shade_mode == 3) {
+                        // normal map: dL/dn' = gs l back through n' = m' / |m'|, the map
+                        // sample and the tangent frame, to dL/dn of the smooth normal
+                        const long long nvt = g.n_verts_total;
+                        float u[3], v[3];
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            u[i] = __ldg(g.uv + M.vert_off + S.vi[i]);
+                            v[i] = __ldg(g.uv + nvt + M.vert_off + S.vi[i]);
+                        }
+                        NMap N;
+                        nmap_eval(g, M, S, u, v, N);
+                        const float d = N.np[0] * gn[0] + N.np[1] * gn[1] + N.np[2] * gn[2];
+                        const float iml = 1.f / N.mpl;
+                        float gmp[3], gTp[3], gBp[3];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) gmp[c] = (gn[c] - N.np[c] * d) * iml;
+                        const float gt[3] = {2.f * (gmp[0] * N.Tp[0] + gmp[1] * N.Tp[1] + gmp[2] * N.Tp[2]),
+                                             2.f * (gmp[0] * N.Bp[0] + gmp[1] * N.Bp[1] + gmp[2] * N.Bp[2]),
+                                             2.f * (gmp[0] * S.n[0] + gmp[1] * S.n[1] + gmp[2] * S.n[2])};
+                        // map texels (bilinear weights) and the map's texel-space UV gradient
+                        const float ox = 1.f - S.fx, oy = 1.f - S.fy;
+                        if (g.gntex) {
+                            float4 *gt4 = reinterpret_cast<float4 *>(g.gntex);
+                            const long long tb = M.tex_off;
+                            const float w[4] = {ox * oy, S.fx * oy, ox * S.fy, S.fx * S.fy};
+                            const long long ix[4] = {tb + (long long)S.iy[0] * M.tex_w + S.ix[0],
+                                                     tb + (long long)S.iy[0] * M.tex_w + S.ix[1],
+                                                     tb + (long long)S.iy[1] * M.tex_w + S.ix[0],
+                                                     tb + (long long)S.iy[1] * M.tex_w + S.ix[1]};
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                atomicAdd(gt4 + ix[q], make_float4(w[q] * gt[0], w[q] * gt[1], w[q] * gt[2], 0.f));
+                        }
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            gxn += gt[c] * (oy * (N.t10[c] - N.t00[c]) + S.fy * (N.t11[c] - N.t01[c]));
+                            gyn += gt[c] * (ox * (N.t01[c] - N.t00[c]) + S.fx * (N.t11[c] - N.t10[c]));
+                        }
+                        // m' = nt0 T' + nt1 B' + nt2 n
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            gTp[c] = N.nt[0] * gmp[c];
+                            gBp[c] = N.nt[1] * gmp[c];
+                            gn[c] = N.nt[2] * gmp[c];
+                        }
+                        // B' = h n x T': dL/dn += h T' x gB', dL/dT' += h gB' x n
+                        gn[0] += N.h * (N.Tp[1] * gBp[2] - N.Tp[2] * gBp[1]);
+                        gn[1] += N.h * (N.Tp[2] * gBp[0] - N.Tp[0] * gBp[2]);
+                        gn[2] += N.h * (N.Tp[0] * gBp[1] - N.Tp[1] * gBp[0]);
+                        gTp[0] += N.h * (gBp[1] * S.n[2] - gBp[2] * S.n[1]);
+                        gTp[1] += N.h * (gBp[2] * S.n[0] - gBp[0] * S.n[2]);
+                        gTp[2] += N.h * (gBp[0] * S.n[1] - gBp[1] * S.n[0]);
+                        // T' = tau / |tau|, tau = Tf - n (n . Tf)
+                        const float dT = N.Tp[0] * gTp[0] + N.Tp[1] * gTp[1] + N.Tp[2] * gTp[2];
+                        const float itl = N.tl > 0.f ? 1.f / N.tl : 0.f;
+                        float gtau[3];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) gtau[c] = (gTp[c] - N.Tp[c] * dT) * itl;
+                        const float ng = S.n[0] * gtau[0] + S.n[1] * gtau[1] + S.n[2] * gtau[2];
+                        // Tf = (e1 dv2 - e2 dv1) / det: object-space corners
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const float gTf = gtau[c] - S.n[c] * ng;
+                            gn[c] += -N.nT * gtau[c] - N.Tf[c] * ng;
+                            const float ge1 = gTf * N.dv2 * N.idet, ge2 = -gTf * N.dv1 * N.idet;
+                            atomicAdd(g.gpos + c * nvt + M.vert_off + S.vi[1], ge1);
+                            atomicAdd(g.gpos + c * nvt + M.vert_off + S.vi[2], ge2);
+                            atomicAdd(g.gpos + c * nvt + M.vert_off + S.vi[0], -(ge1 + ge2));
+                        }
+                    }
                     const float nd = S.n[0] * gn[0] + S.n[1] * gn[1] + S.n[2] * gn[2];
                     const float il = 1.f / S.mlen;
                     const float gm[3] = {(gn[0] - S.n[0] * nd) * il, (gn[1] - S.n[1] * nd) * il,
@@ -428,8 +586,9 @@ __device__ __forceinline__ bool layer_adjoint(const Globals &g, const ViewK &V, 
                              gA[2] * ((1.f - S.fx) * (t01.z - t00.z) + S.fx * (t11.z - t10.z));
             // x = sum b_i X_i - 1/2; adding a constant to every gb_i is invisible to the
             // perspective step below (sum b = 1), so corner offsets from corner 0 are used
+            // (the normal map, sampled at the same texel coordinates, adds gxn, gyn)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) gb[i] += gx * S.Xt[i] + gy * S.Yt[i];
+            for (int i = 0; i < 3; ++i) gb[i] += (gx + gxn) * S.Xt[i] + (gy + gyn) * S.Yt[i];
         }
         // perspective-correct barycentrics: b_i = q_i / Q, q_i = lam_i / w_i
         const float bdot = S.b[0] * gb[0] + S.b[1] * gb[1] + S.b[2] * gb[2];
@@ -693,7 +852,7 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
             frag_lambda(R, fr, Sh.lam);
 #pragma unroll
             for (int i = 0; i < 3; ++i) { Sh.vi[i] = R.vi[i]; Sh.iw[i] = R.iw[i]; }
-            shade(g, V, M, fr.dist, Sh);
+            shade<EXTRA>(g, V, M, fr.dist, Sh);
             Cs[0] = ffma(Sh.D, Sh.C[0], Cs[0]);
             Cs[1] = ffma(Sh.D, Sh.C[1], Cs[1]);
             Cs[2] = ffma(Sh.D, Sh.C[2], Cs[2]);
@@ -728,7 +887,7 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
 #pragma unroll 1
             for (int k = 0; k < nl; ++k) {
                 Layer L;
-                if (layer_build(g, V, M, ids[k], px, py, L)) {
+                if (layer_build<EXTRA>(g, V, M, ids[k], px, py, L)) {
                     Dk[k] = L.S.D;
                     Ck[k][0] = L.S.C[0]; Ck[k][1] = L.S.C[1]; Ck[k][2] = L.S.C[2];
                 }
@@ -773,7 +932,7 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
             const bool any = gDl != 0.f || gCl[0] != 0.f || gCl[1] != 0.f || gCl[2] != 0.f;
             Layer L;
             const long long slot = (V.slot_base + (long long)ly_g * V.W + lx_g) * K + k;
-            if (any && layer_build(g, V, M, ids[k], px, py, L)) {
+            if (any && layer_build<EXTRA>(g, V, M, ids[k], px, py, L)) {
                 ++layers;
                 if (layer_adjoint<EXTRA>(g, V, M, L, px, py, gCl, gDl, slot, gl)) stored |= 1u << k;
             }
@@ -795,8 +954,8 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
 
 // everything one CTA does for global tile t.  MODE: 0 forward, 1 adjoint that
 // re-rasterizes, 2 adjoint from stored layer ids, 3 forward from stored layer ids
-// (re-shading a static geometry: no binning, raster or peel), 4 and 5 = 2 and 1 with
-// the light gradient and the inverse UV compiled in
+// (re-shading a static geometry: no binning, raster or peel); 4, 5, 6, 7 = 2, 1, 0, 3
+// with the normal map, the light gradient and the inverse UV compiled in
 template <int K, int MODE, int TT>
 __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned long long *kbuf, const int t)
 {
@@ -825,9 +984,9 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
         S.sh[i] = (hx >= 0 && hy >= 0 && hx < V.W && hy < V.H) ? 0 : 2;
     }
     constexpr bool EXTRA = MODE >= 4;
-    constexpr bool BWD = MODE == 1 || MODE == 2 || EXTRA;
-    constexpr bool from_ids = MODE == 2 || MODE == 3 || MODE == 4;
-    const bool light_grad = EXTRA && g.glight != nullptr && g.shade_mode == 2;
+    constexpr bool BWD = MODE == 1 || MODE == 2 || MODE == 4 || MODE == 5;
+    constexpr bool from_ids = MODE == 2 || MODE == 3 || MODE == 4 || MODE == 7;
+    const bool light_grad = EXTRA && g.glight != nullptr && g.shade_mode >= 2;
     float *glacc = light_grad ? S.gl[tid] : nullptr;
     if (light_grad) glacc[0] = glacc[1] = glacc[2] = 0.f;
     if (!from_ids)
@@ -1124,7 +1283,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
 template <int MODE, int TT>
 constexpr int tile_min_ctas()
 {
-    return MODE == 0 || MODE == 3 ? 4 : (MODE == 2 || MODE == 4) ? 3 : (TT == 16 ? 4 : 3);
+    return MODE == 0 || MODE == 3 ? 4 : (MODE == 2 || MODE == 4 || MODE >= 6) ? 3 : (TT == 16 ? 4 : 3);
 }
 
 template <int K, int MODE, int TT>
@@ -1160,7 +1319,7 @@ constexpr size_t tile_smem_bytes()
 {
     // from stored ids: the first part of Smem; otherwise Smem, the K-lists,
     // the candidate queue, the two pair-block tables
-    return MODE == 2 || MODE == 3 || MODE == 4 ? offsetof(Smem, F)
+    return MODE == 2 || MODE == 3 || MODE == 4 || MODE == 7 ? offsetof(Smem, F)
                      : sizeof(Smem) + sizeof(unsigned long long) * TT * TT * K + sizeof(unsigned) * QN + 2 * NBLK;
 }
 // four forward CTAs of the default configuration (K = 3, 16 px tiles) per SM: 228 KB of
@@ -1206,8 +1365,9 @@ static void launch_k(const Globals &g, cudaStream_t s)
 }
 
 // the per-tile kernel of one mode (0 forward, 1 adjoint re-rasterizing, 2 adjoint from
-// stored layer ids, 3 forward from stored layer ids, 4 / 5: 2 / 1 with the light
-// gradient and the inverse UV); instantiated by that mode's translation unit
+// stored layer ids, 3 forward from stored layer ids, 4 / 5 / 6 / 7: 2 / 1 / 0 / 3 with the
+// normal map, the light gradient and the inverse UV); instantiated by that mode's
+// translation unit
 template <int MODE>
 void launch_tile_mode(const Globals &g, cudaStream_t s)
 {

@@ -5,10 +5,12 @@
 
 namespace dressi {
 template void launch_tile_mode<3>(const Globals &g, cudaStream_t s);
+extern template void launch_tile_mode<7>(const Globals &g, cudaStream_t s);
 
 void launch_tile_shade(const Globals &g, cudaStream_t s)
 {
-    launch_tile_mode<3>(g, s);
+    if (g.shade_mode == 3) launch_tile_mode<7>(g, s);
+    else launch_tile_mode<3>(g, s);
     count_launch(1);
 }
 }  // namespace dressi

@@ -34,12 +34,13 @@ class PackedScene:
 
     def __init__(self, meshes: Sequence, device="cuda", tex_dtype: Optional[torch.dtype] = None):
         self.device = torch.device(device)
-        pos, col, uv, faces, tex = [], [], [], [], []
+        pos, col, uv, faces, tex, ntex = [], [], [], [], [], []
         table = []
         vo = fo = to = 0
         has_col = all(getattr(m, "col", None) is not None for m in meshes)
         has_uv = all(getattr(m, "uv", None) is not None for m in meshes)
         has_tex = all(getattr(m, "tex", None) is not None for m in meshes)
+        has_ntex = has_tex and all(getattr(m, "ntex", None) is not None for m in meshes)
         if tex_dtype is None and has_tex:
             t0 = meshes[0].tex
             tex_dtype = torch.float16 if (str(getattr(t0, "dtype", "")) in ("float16", "torch.float16")) else torch.float32
@@ -58,6 +59,10 @@ class PackedScene:
                 tt = _t(m.tex, self.tex_dtype, self.device)
                 th, tw = int(tt.shape[0]), int(tt.shape[1])
                 tex.append(tt.reshape(-1, 4))
+                if has_ntex:
+                    nt = _t(m.ntex, self.tex_dtype, self.device)
+                    assert tuple(nt.shape) == tuple(tt.shape), "the normal map is sized like the texture"
+                    ntex.append(nt.reshape(-1, 4))
             table.append(B.DressiMesh(int(p.shape[0]), int(f.shape[0]), vo, fo, to, tw, th))
             vo += int(p.shape[0])
             fo += int(f.shape[0])
@@ -70,23 +75,26 @@ class PackedScene:
         self.col = torch.cat(col, 1).contiguous() if has_col else None
         self.uv = torch.cat(uv, 1).contiguous() if has_uv else None
         self.tex = torch.cat(tex, 0).contiguous() if has_tex else None
+        self.ntex = torch.cat(ntex, 0).contiguous() if has_ntex else None
         self.table = (B.DressiMesh * len(table))(*table)
         self.n_meshes = len(table)
 
-    def c_struct(self, pos=None, col=None, tex=None) -> B.DressiScene:
-        """C view of the scene; ``pos``/``col``/``tex`` override the stored tensors
-        (same shapes), e.g. with tensors that require grad."""
+    def c_struct(self, pos=None, col=None, tex=None, ntex=None) -> B.DressiScene:
+        """C view of the scene; ``pos``/``col``/``tex``/``ntex`` override the stored
+        tensors (same shapes), e.g. with tensors that require grad."""
         pos = self.pos if pos is None else pos
         col = self.col if col is None else col
         tex = self.tex if tex is None else tex
-        for t in (pos, col, tex):
+        ntex = self.ntex if ntex is None else ntex
+        for t in (pos, col, tex, ntex):
             if t is not None:
                 assert t.is_cuda and t.is_contiguous()
         return B.DressiScene(self.n_meshes, C.cast(self.table, C.POINTER(B.DressiMesh)), self.n_verts_total,
                              pos.data_ptr(), col.data_ptr() if col is not None else None,
                              self.uv.data_ptr() if self.uv is not None else None, self.faces.data_ptr(),
                              tex.data_ptr() if tex is not None else None,
-                             B.TEX_F16 if self.tex_dtype == torch.float16 else B.TEX_F32)
+                             B.TEX_F16 if self.tex_dtype == torch.float16 else B.TEX_F32,
+                             ntex.data_ptr() if ntex is not None else None)
 
 
 def make_views(views: Sequence) -> "C.Array":
@@ -231,9 +239,11 @@ class Renderer:
         return out
 
     def backward(self, grad_rgba: torch.Tensor, ids: Optional[torch.Tensor] = None, grad_pos=None, grad_col=None,
-                 grad_tex=None, pos=None, col=None, tex=None, camera: bool = False):
-        """Adjoint of ``forward``: ``(grad_pos, grad_col, grad_tex)``, and with ``camera``
-        also ``grad_mvp [n_views, 16]`` and ``grad_light [n_views, 3]``."""
+                 grad_tex=None, pos=None, col=None, tex=None, camera: bool = False, normal_map: bool = False,
+                 grad_ntex=None):
+        """Adjoint of ``forward``: ``(grad_pos, grad_col, grad_tex)``, with ``camera``
+        also ``grad_mvp [n_views, 16]`` and ``grad_light [n_views, 3]``, and with
+        ``normal_map`` (shade_mode 3) the normal-map texel gradient last."""
         dev = self.scene.device
         sc = self.scene.c_struct(pos, col, tex)
         grad_rgba = grad_rgba.contiguous()
@@ -243,6 +253,8 @@ class Renderer:
             grad_col = torch.empty(3, self.scene.n_verts_total, dtype=torch.float32, device=dev)
         if grad_tex is None and self.scene.tex is not None and self.params.shade_mode != 0:
             grad_tex = torch.empty(self.scene.n_texels, 4, dtype=torch.float32, device=dev)
+        if normal_map and grad_ntex is None:
+            grad_ntex = torch.empty(self.scene.n_texels, 4, dtype=torch.float32, device=dev)
         gm = torch.empty(self.n_views, 16, dtype=torch.float32, device=dev) if camera else None
         gl = torch.empty(self.n_views, 3, dtype=torch.float32, device=dev) if camera else None
         code = self.lib.dressi_backward_ex(C.byref(sc), self.views, self.n_views, C.byref(self.params),
@@ -252,11 +264,15 @@ class Renderer:
                                            grad_tex.data_ptr() if grad_tex is not None else None,
                                            gm.data_ptr() if gm is not None else None,
                                            gl.data_ptr() if gl is not None else None,
+                                           grad_ntex.data_ptr() if normal_map else None,
                                            self.ws.data_ptr(), self.ws_bytes, self.status.data_ptr(), self._stream())
         B.check(code, "dressi_backward_ex")
+        res = (grad_pos, grad_col, grad_tex)
         if camera:
-            return grad_pos, grad_col, grad_tex, gm, gl
-        return grad_pos, grad_col, grad_tex
+            res = res + (gm, gl)
+        if normal_map:
+            res = res + (grad_ntex,)
+        return res
 
     def l2_grad(self, out: torch.Tensor, target: torch.Tensor, grad: Optional[torch.Tensor] = None,
                 loss: Optional[torch.Tensor] = None):

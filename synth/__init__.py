@@ -333,6 +333,30 @@ def config2(seed: int = 1236, texgrad_mode: int = 0) -> Scene:
     return Scene("uvsphere5120_256px_lambert_tex512", [mesh], [view], p)
 
 
+def normal_map(g, side: int, amp: float = 0.25) -> np.ndarray:
+    """Tangent-space normal map [side, side, 4]: unit normals near +z (x, y smooth value
+    noise of amplitude amp), encoded t = (n + 1) / 2 as in a normal-map image."""
+    seed = int(g.integers(1 << 30))
+    uu, vv = np.meshgrid((np.arange(side) + 0.5) / side, (np.arange(side) + 0.5) / side)
+    pts = np.stack([np.cos(2 * np.pi * uu), np.sin(2 * np.pi * uu), 2 * vv - 1], -1).reshape(-1, 3)
+    nx = amp * value_noise(pts * 3.0, seed)
+    ny = amp * value_noise(pts * 3.0 + 17.0, seed + 1)
+    nz = np.sqrt(np.maximum(1.0 - nx * nx - ny * ny, 0.0))
+    t = np.zeros((side * side, 4), np.float32)
+    t[:, 0], t[:, 1], t[:, 2] = (nx + 1) / 2, (ny + 1) / 2, (nz + 1) / 2
+    return t.reshape(side, side, 4)
+
+
+def config2n(seed: int = 1236) -> Scene:
+    """config2 with a tangent-space normal map (shade_mode 3), 256^2 map and texture."""
+    g = rng(seed)
+    pos, faces, uv = _displaced_uv_sphere(64, 41, seed)
+    mesh = Mesh(_f32(pos), faces, uv=_f32(uv), tex=_tex(g, 256), ntex=normal_map(g, 256))
+    view = View(camera_mvp((0, 0, 3), 256, 256), 0, 256, 256)
+    p = soft_params_px(256, shade_mode=3)
+    return Scene("uvsphere5120_256px_normalmap256", [mesh], [view], p)
+
+
 def config3(seed: int = 1237, n_views: int = 64, res: int = 512) -> Scene:
     """Batched multi-view: 20,480-tri displaced UV sphere, 1024^2 texture, 64 views of 512^2."""
     g = rng(seed)

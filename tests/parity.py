@@ -84,24 +84,26 @@ class GpuRun:
             v = self.r.views[i]
             g[v.pix_off: v.pix_off + v.width * v.height] = torch.as_tensor(
                 np.asarray(gv, np.float32).reshape(-1, 4), device=self.ps.device)
-        res = self.r.backward(g, ids=self.ids if use_ids else None, camera=camera)
+        nmap = self.scene.params.shade_mode == 3
+        res = self.r.backward(g, ids=self.ids if use_ids else None, camera=camera, normal_map=nmap)
         torch.cuda.synchronize()
-        per_mesh = self.split(*res[:3])
+        per_mesh = self.split(*res[:3], gnt=res[-1] if nmap else None)
         if camera:
             return per_mesh, res[3].cpu().numpy().astype(np.float64), res[4].cpu().numpy().astype(np.float64)
         return per_mesh
 
-    def split(self, gp, gc, gt):
-        """Per-mesh numpy gradients [V,3], [V,3] or None, [Ht,Wt,4] or None."""
+    def split(self, gp, gc, gt, gnt=None):
+        """Per-mesh numpy gradients [V,3], [V,3] or None, [Ht,Wt,4] or None, and the
+        normal-map gradient [Ht,Wt,4] or None."""
         res = []
         for m, t in zip(self.scene.meshes, self.ps.table):
             a, n = t.vert_off, t.n_verts
             p = gp[:, a:a + n].t().cpu().numpy().astype(np.float64)
             c = gc[:, a:a + n].t().cpu().numpy().astype(np.float64) if gc is not None else None
-            x = None
-            if gt is not None:
-                x = gt[t.tex_off: t.tex_off + t.tex_w * t.tex_h].view(t.tex_h, t.tex_w, 4).cpu().numpy().astype(np.float64)
-            res.append((p, c, x))
+            texels = lambda q: q[t.tex_off: t.tex_off + t.tex_w * t.tex_h].view(t.tex_h, t.tex_w, 4).cpu().numpy().astype(np.float64)
+            x = texels(gt) if gt is not None else None
+            nx = texels(gnt) if gnt is not None else None
+            res.append((p, c, x, nx))
         return res
 
     def status(self):
@@ -161,18 +163,23 @@ def compare_scene(scene, windows=None, seed=0, grad_from_target=None, store_laye
             g_gpu, gm_gpu, gl_gpu = gpu.backward(grads, use_ids=store_layers, camera=True)
         else:
             g_gpu = gpu.backward(grads, use_ids=store_layers)
+        nmap = scene.params.shade_mode == 3
         res = [[np.zeros(m.pos.shape), None if m.col is None else np.zeros(m.col.shape),
-                None if m.tex is None else np.zeros(m.tex.shape)] for m in scene.meshes]
+                None if m.tex is None else np.zeros(m.tex.shape),
+                np.zeros(m.ntex.shape) if nmap else None] for m in scene.meshes]
         errs = {}
         for i, v in enumerate(scene.views):
             gv, win = stats["per_view"][i]
+            gnt = None
             if camera:
-                gp, gc, gt, gm, gl = oracle.backward(scene.meshes[v.mesh], v, scene.params, gv, window=win, camera=True)
+                gp, gc, gt, gm, gl, *rest = oracle.backward(scene.meshes[v.mesh], v, scene.params, gv, window=win,
+                                                            camera=True, want_ntex=nmap)
+                gnt = rest[0] if nmap else None
                 if np.any(gm):
                     e = rel_l2(gm_gpu[i], gm)
                     errs[f"mvp{i}"] = e
                     assert e <= GRAD_TOL, f"view {i} grad_mvp rel-L2 {e:.3e} > {GRAD_TOL}"
-                if scene.params.shade_mode == 2 and np.any(gl):
+                if scene.params.shade_mode >= 2 and np.any(gl):
                     e = rel_l2(gl_gpu[i], gl)
                     errs[f"light{i}"] = e
                     assert e <= GRAD_TOL, f"view {i} grad_light rel-L2 {e:.3e} > {GRAD_TOL}"
@@ -180,14 +187,19 @@ def compare_scene(scene, windows=None, seed=0, grad_from_target=None, store_laye
                     assert not np.any(gl) and not np.any(gl_gpu[i])
                 assert not np.any(gm_gpu[i][8:12])   # the depth row
             else:
-                gp, gc, gt = oracle.backward(scene.meshes[v.mesh], v, scene.params, gv, window=win)
+                gp, gc, gt, *rest = oracle.backward(scene.meshes[v.mesh], v, scene.params, gv, window=win,
+                                                    want_ntex=nmap)
+                gnt = rest[0] if nmap else None
             res[v.mesh][0] += gp
             if gc is not None:
                 res[v.mesh][1] += gc
             if gt is not None:
                 res[v.mesh][2] += gt
+            if gnt is not None:
+                res[v.mesh][3] += gnt
         for mi, (o_, g_) in enumerate(zip(res, g_gpu)):
-            for name, a, b in (("pos", g_[0], o_[0]), ("col", g_[1], o_[1]), ("tex", g_[2], o_[2])):
+            for name, a, b in (("pos", g_[0], o_[0]), ("col", g_[1], o_[1]), ("tex", g_[2], o_[2]),
+                               ("ntex", g_[3], o_[3])):
                 if a is None or b is None or not np.any(b):
                     continue
                 if name == "tex" and scene.params.shade_mode == 0:
