@@ -33,11 +33,11 @@ constexpr int TT_MAX = 32;             // tile edges: 16 (one pixel per thread) 
 constexpr int RHO_MAX = 8;             // largest supported edge-mask radius
 constexpr int HS_MAX = TT_MAX + 2 * RHO_MAX;
 constexpr float APPROX_EPS = 1e-3f;    // pixel slack of the tile-local (approximate) edge equations
-constexpr int CH = 128;                // faces staged per round (one per thread of the first half)
-constexpr int HASH = 2 * CH;           // face id -> staged slot, open addressing
+constexpr int CH = 96;                 // faces staged per round (one per thread)
+constexpr int HASH = 256;              // face id -> staged slot, open addressing (> 2 CH)
 constexpr unsigned long long EMPTY = ~0ULL;
 constexpr int QN = 4 * NT;             // queued candidate pairs per batch
-constexpr int NBLK = 2048;             // pair blocks of 32 with a table entry (65,536 pairs)
+constexpr int NBLK = 1024;             // pair blocks of 32 with a table entry (32,768 items)
 
 // conservative tile-local data of a staged face: edge equations in pixels relative to
 // the tile origin (FP32, a few 1e-6 px of error) and the smallest corner depth.  12 words:
@@ -698,7 +698,6 @@ struct Smem {
     int view, totals[2], next;
     int qn[2];           // queue fill of the current batch, by batch parity
     unsigned long long m0[HS_MAX], m1[HS_MAX];   // per halo row: columns with S^H = 0 / 1
-    float gl[NT][3];     // adjoint: each thread's share of dL/dlight
     unsigned char sh[HS_MAX * HS_MAX];
     // the raster (forward and re-rasterizing adjoint) only: the modes from stored layer
     // ids are launched with the shared memory up to F, leaving the rest of the SM's
@@ -964,6 +963,10 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
     unsigned *qbuf = reinterpret_cast<unsigned *>(kbuf + TT * TT * K);
     unsigned char *blk = reinterpret_cast<unsigned char *>(qbuf + QN);
     unsigned char *hblk = blk + NBLK;
+    // the adjoints with extras: each thread's share of dL/dlight, after the part of the
+    // shared memory the kernel uses (the header alone when it reads stored layers)
+    float(*gl_slots)[3] = reinterpret_cast<float(*)[3]>(
+        MODE == 4 ? reinterpret_cast<unsigned char *>(&S) + offsetof(Smem, F) : hblk + NBLK);
     if (threadIdx.x == 0) {
         S.view = view_of_tile(g, t);
         S.qn[0] = 0;
@@ -987,7 +990,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
     constexpr bool BWD = MODE == 1 || MODE == 2 || MODE == 4 || MODE == 5;
     constexpr bool from_ids = MODE == 2 || MODE == 3 || MODE == 4 || MODE == 7;
     const bool light_grad = EXTRA && g.glight != nullptr && g.shade_mode >= 2;
-    float *glacc = light_grad ? S.gl[tid] : nullptr;
+    float *glacc = light_grad ? gl_slots[tid] : nullptr;
     if (light_grad) glacc[0] = glacc[1] = glacc[2] = 0.f;
     if (!from_ids)
         for (int i = tid; i < TT * TT * K; i += NT) kbuf[i] = EMPTY;
@@ -1317,14 +1320,18 @@ __global__ void __launch_bounds__(NT, tile_min_ctas<MODE, TT>()) k_tile_persiste
 template <int K, int MODE, int TT>
 constexpr size_t tile_smem_bytes()
 {
-    // from stored ids: the first part of Smem; otherwise Smem, the K-lists,
-    // the candidate queue, the two pair-block tables
-    return MODE == 2 || MODE == 3 || MODE == 4 || MODE == 7 ? offsetof(Smem, F)
-                     : sizeof(Smem) + sizeof(unsigned long long) * TT * TT * K + sizeof(unsigned) * QN + 2 * NBLK;
+    // from stored ids: the first part of Smem; otherwise Smem, the K-lists, the
+    // candidate queue, the two pair-block tables; the adjoints with extras add the
+    // per-thread dL/dlight slots
+    return (MODE == 2 || MODE == 3 || MODE == 4 || MODE == 7
+                ? offsetof(Smem, F)
+                : sizeof(Smem) + sizeof(unsigned long long) * TT * TT * K + sizeof(unsigned) * QN + 2 * NBLK) +
+           (MODE == 4 || MODE == 5 ? sizeof(float) * 3 * NT : 0);
 }
 // four forward CTAs of the default configuration (K = 3, 16 px tiles) per SM: 228 KB of
 // shared memory per SM, 1 KB of it reserved per CTA
 static_assert(4 * (tile_smem_bytes<3, 0, 16>() + 1024) <= 228 * 1024, "K = 3 forward tiles no longer fit four CTAs per SM");
+static_assert(4 * (tile_smem_bytes<3, 0, 32>() + 1024) <= 228 * 1024, "K = 3, 32 px forward tiles no longer fit four CTAs per SM");
 
 template <int K, int MODE, int TT>
 static void launch_kk(const Globals &g, cudaStream_t s)
