@@ -40,7 +40,7 @@ static void launch_tile_profiled(const Globals &g, int pass, cudaStream_t s)
 }
 
 struct Layout {
-    size_t views, meshes, vrec, frec, tile_count, tile_off, tile_cursor, lists, nrm, adj_off, adj_cur, adj, scan_partial,
+    size_t views, meshes, vrec, frec, tile_view, tile_count, tile_off, tile_cursor, lists, nrm, adj_off, adj_cur, adj, scan_partial,
         sgrad, ngrad, queue,
         tile_order, lpt_hist, tg_keys, tg_pay0, tg_pay1, tg_scratch, inv_uv, total;
     long long tg_slots;   // texel-gather record slots (0 unless texgrad_mode 1 with a texture)
@@ -166,6 +166,7 @@ static bool make_plan(const dressi_scene *sc, const dressi_view *views, int n_vi
     L.meshes = o; o = align_up(o + sizeof(MeshK) * sc->n_meshes);
     L.vrec = o; o = align_up(o + sizeof(VRec) * (size_t)std::max<long long>(vrec, 1));
     L.frec = o; o = align_up(o + sizeof(FaceRec) * (size_t)std::max<long long>(view_faces, 1));
+    L.tile_view = o; o = align_up(o + sizeof(int) * (size_t)std::max(tiles, 1));
     L.tile_count = o; o = align_up(o + sizeof(int) * (size_t)tiles);
     L.tile_off = o; o = align_up(o + sizeof(int) * (size_t)(tiles + 1));
     L.tile_cursor = o; o = align_up(o + sizeof(int) * (size_t)tiles);
@@ -257,6 +258,7 @@ static Globals make_globals(const dressi_scene *sc, const dressi_params *p, cons
     g.ntex = sc->ntex;
     g.vrec = reinterpret_cast<VRec *>(ws + L.vrec);
     g.frec = reinterpret_cast<FaceRec *>(ws + L.frec);
+    g.tile_view = reinterpret_cast<int *>(ws + L.tile_view);
     g.tile_count = reinterpret_cast<int *>(ws + L.tile_count);
     g.tile_off = reinterpret_cast<int *>(ws + L.tile_off);
     g.tile_cursor = reinterpret_cast<int *>(ws + L.tile_cursor);
@@ -292,6 +294,7 @@ static void run_setup(const Globals &g, const Plan &P, char *ws, bool need_bins,
     upload(P.meshes.data(), sizeof(MeshK) * P.meshes.size(), ws + L.meshes, s);
     launch_vertex(g, (int)P.views.size(), P.max_nv_view, s);
     launch_face(g, (int)P.views.size(), P.max_nf_view, s);
+    launch_tile_view(g, (int)P.views.size(), s);
     if (g.shade_mode >= 2) {
         const size_t nv = (size_t)std::max<long long>(g.n_verts_total, 1);
         cudaMemsetAsync(ws + L.adj_off, 0, sizeof(int) * (nv + 1), s);

@@ -101,6 +101,7 @@ struct Globals {
     VRec *vrec;
     FaceRec *frec;        // per (view, face): the face's record, written by the setup
     int *tile_count, *tile_off, *tile_cursor, *lists;
+    int *tile_view;       // [total_tiles] the view owning each tile
     float4 *nrm;          // [n_verts_total] normalized vertex normals, w = |sum|
     int *adj_off;         // [n_verts_total + 1] vertex -> incident faces (CSR offsets)
     int *adj_cur;         // [n_verts_total] fill cursors
@@ -418,17 +419,6 @@ __device__ __forceinline__ bool hard_test(const FaceRec &R, float px, float py)
 __device__ __forceinline__ bool frag_less(float ka, int ia, float kb, int ib)
 {
     return ka < kb || (ka == kb && ia < ib);
-}
-
-// binary search of the view owning global tile t
-__device__ __forceinline__ int view_of_tile(const Globals &g, int t)
-{
-    int lo = 0, hi = g.n_views - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (g.views[mid].tile_base <= t) lo = mid; else hi = mid - 1;
-    }
-    return lo;
 }
 
 __device__ __forceinline__ float sigmoidf_stable(float x)

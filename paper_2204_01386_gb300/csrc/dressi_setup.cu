@@ -174,6 +174,16 @@ __global__ void k_normal_csr(Globals g)
 }
 
 // ---------------------------------------------------------------------------
+// tile -> view table: one load per tile instead of a search over the views
+// ---------------------------------------------------------------------------
+__global__ void k_tile_view(Globals g)
+{
+    const ViewK &V = g.views[blockIdx.x];
+    const int n = V.tiles_x * V.tiles_y;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) g.tile_view[V.tile_base + i] = blockIdx.x;
+}
+
+// ---------------------------------------------------------------------------
 // face table: the record of every (view, face) -- screen corners, canonical edges,
 // lengths, area, flags -- built once per call and read by binning, staging,
 // shading and the adjoint (112 bytes each)
@@ -430,6 +440,12 @@ void launch_normals(const Globals &g, int n_meshes, int max_nf, int max_nv, cuda
     k_adjacency<1><<<gf, 256, 0, s>>>(g);
     k_normal_csr<<<gv, 256, 0, s>>>(g);
     count_launch(3);
+}
+
+void launch_tile_view(const Globals &g, int n_views, cudaStream_t s)
+{
+    k_tile_view<<<n_views, 256, 0, s>>>(g);
+    count_launch(1);
 }
 
 void launch_face(const Globals &g, int n_views, int max_nf, cudaStream_t s)

@@ -968,7 +968,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
     float(*gl_slots)[3] = reinterpret_cast<float(*)[3]>(
         MODE == 4 ? reinterpret_cast<unsigned char *>(&S) + offsetof(Smem, F) : hblk + NBLK);
     if (threadIdx.x == 0) {
-        S.view = view_of_tile(g, t);
+        S.view = g.tile_view[t];
         S.qn[0] = 0;
         S.qn[1] = 0;
     }
@@ -992,8 +992,9 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
     const bool light_grad = EXTRA && g.glight != nullptr && g.shade_mode >= 2;
     float *glacc = light_grad ? gl_slots[tid] : nullptr;
     if (light_grad) glacc[0] = glacc[1] = glacc[2] = 0.f;
-    if (!from_ids)
-        for (int i = tid; i < TT * TT * K; i += NT) kbuf[i] = EMPTY;
+    if (!from_ids)   // 16-byte stores (TT^2 K is even; kbuf is 16-byte aligned)
+        for (int i = tid; i < TT * TT * K / 2; i += NT)
+            reinterpret_cast<ulonglong2 *>(kbuf)[i] = make_ulonglong2(EMPTY, EMPTY);
     bool single_chunk = false;
     unsigned n_pairs = 0, n_exact = 0, n_cand = 0, n_layers = 0;
     int batch = 0;   // candidate-queue batches so far (selects the queue counter)
