@@ -791,6 +791,90 @@ __device__ __forceinline__ bool kept_hard(const Globals &g, const ViewK &V, cons
            eval_face<false>(R, px, py, V.r_px, V.half_inv_S, fr) && fr.hard;
 }
 
+// edge mask (Sec. 3.4.3) of tile pixel (lx, ly): the window of radius rho sees both
+// S^H = 0 and 1 (S.m0 / S.m1 hold the columns of each halo row with either value)
+__device__ __forceinline__ bool edge_mask(const Globals &g, const Smem &S, int lx, int ly, int rho)
+{
+    if (g.edge_mode != 0) return g.edge_mode == 1;
+    unsigned long long a0 = 0ull, a1 = 0ull;
+    for (int wy = 0; wy <= 2 * rho; ++wy) { a0 |= S.m0[ly + wy]; a1 |= S.m1[ly + wy]; }
+    const unsigned long long wm = (2ull << (2 * rho)) - 1ull;   // columns lx .. lx + 2 rho
+    return ((a0 >> lx) & wm) && ((a1 >> lx) & wm);
+}
+
+// the adjoint of the edge-mask blend (Sec. 3.4.3) at one pixel: the colour
+// sum_k D_k C_k / sum_k D_k and the silhouette 1 - prod_k (1 - D_k), from the nl layers'
+// D_k and C_k and the incoming dL/d(RGBA) gi4; adds into gCk / gDk (zero on entry)
+template <int K>
+__device__ __forceinline__ void blend_weights(const float (&Dk)[K], const float (&Ck)[K][3], int nl, float4 gi4,
+                                              float (&gCk)[K][3], float (&gDk)[K])
+{
+    const float gc[3] = {gi4.x, gi4.y, gi4.z};
+    float Ds = 0.f, Ie[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        Ds += Dk[k];
+        Ie[0] = fmaf(Dk[k], Ck[k][0], Ie[0]);
+        Ie[1] = fmaf(Dk[k], Ck[k][1], Ie[1]);
+        Ie[2] = fmaf(Dk[k], Ck[k][2], Ie[2]);
+    }
+    if (Ds > 0.f) {
+        const float iD = 1.f / Ds;
+        Ie[0] *= iD; Ie[1] *= iD; Ie[2] *= iD;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            gCk[k][0] = Dk[k] * iD * gc[0];
+            gCk[k][1] = Dk[k] * iD * gc[1];
+            gCk[k][2] = Dk[k] * iD * gc[2];
+            gDk[k] = (gc[0] * (Ck[k][0] - Ie[0]) + gc[1] * (Ck[k][1] - Ie[1]) + gc[2] * (Ck[k][2] - Ie[2])) * iD;
+        }
+    }
+    // silhouette 1 - prod_k (1 - D_k)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float others = 1.f;
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (j != k && j < nl) others *= 1.f - Dk[j];
+        if (k < nl) gDk[k] += gi4.w * others;
+    }
+}
+
+// dL/dC_k and dL/dD_k of the K layers of one pixel (the adjoint of the blend, Sec.
+// 3.4.3): E and SH as the forward decided them; returns false when nothing flows back
+// (no layer, or a zero incoming gradient unless every sample is wanted)
+template <int K, bool EXTRA>
+__device__ __forceinline__ bool pixel_weights(const Globals &g, const ViewK &V, const MeshK &M, long long pix,
+                                              float px, float py, const int (&ids)[K], int nl, bool E, bool SH,
+                                              bool inv, float (&gCk)[K][3], float (&gDk)[K])
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k) { gDk[k] = 0.f; gCk[k][0] = gCk[k][1] = gCk[k][2] = 0.f; }
+    if (nl == 0) return false;
+    const float4 gi4 = __ldg(reinterpret_cast<const float4 *>(g.gin) + pix);
+    const float gc[3] = {gi4.x, gi4.y, gi4.z};
+    if (!inv && gc[0] == 0.f && gc[1] == 0.f && gc[2] == 0.f && gi4.w == 0.f) return false;
+    if (E) {
+        // pass 1: D_k and C_k of every layer
+        float Dk[K], Ck[K][3];
+#pragma unroll
+        for (int k = 0; k < K; ++k) { Dk[k] = 0.f; Ck[k][0] = Ck[k][1] = Ck[k][2] = 0.f; }
+        // rolled loop: one inlined copy of the layer code keeps the kernel small
+#pragma unroll 1
+        for (int k = 0; k < nl; ++k) {
+            Layer L;
+            if (layer_build<EXTRA>(g, V, M, ids[k], px, py, L)) {
+                Dk[k] = L.S.D;
+                Ck[k][0] = L.S.C[0]; Ck[k][1] = L.S.C[1]; Ck[k][2] = L.S.C[2];
+            }
+        }
+        blend_weights<K>(Dk, Ck, nl, gi4, gCk, gDk);
+    } else if (SH) {
+        gCk[0][0] = gc[0]; gCk[0][1] = gc[1]; gCk[0][2] = gc[2];
+    }
+    return true;
+}
+
 // S^H, edge mask, shading and blend (forward) or the adjoint (BWD) of one pixel
 // whose K layer ids are known; S.sh holds the tile's S^H with its ring.
 template <int K, bool BWD, int TT, bool EXTRA>
@@ -807,15 +891,7 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
 #pragma unroll
     for (int k = 0; k < K; ++k) nl += (ids[k] != 0x7fffffff) ? 1 : 0;
     const bool SH = S.sh[(ly + rho) * hs + (lx + rho)] == 1;
-
-    // edge mask (Sec. 3.4.3): the window of radius rho sees both S^H = 0 and 1
-    bool E = g.edge_mode == 1;
-    if (g.edge_mode == 0) {
-        unsigned long long a0 = 0ull, a1 = 0ull;
-        for (int wy = 0; wy <= 2 * rho; ++wy) { a0 |= S.m0[ly + wy]; a1 |= S.m1[ly + wy]; }
-        const unsigned long long wm = (2ull << (2 * rho)) - 1ull;   // columns lx .. lx + 2 rho
-        E = ((a0 >> lx) & wm) && ((a1 >> lx) & wm);
-    }
+    const bool E = edge_mask(g, S, lx, ly, rho);
 
     unsigned layers = 0;
     if (!BWD) {
@@ -868,60 +944,9 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
         }
         reinterpret_cast<float4 *>(g.out)[pix] = o;
     } else {
-        if (nl == 0) return 0;
-        // the inverse UV needs every shaded sample, also those without a gradient
         const bool inv = EXTRA && g.texgrad_mode == 2;
-        const float4 gi4 = __ldg(reinterpret_cast<const float4 *>(g.gin) + pix);
-        const float gc[3] = {gi4.x, gi4.y, gi4.z};
-        if (!inv && gc[0] == 0.f && gc[1] == 0.f && gc[2] == 0.f && gi4.w == 0.f) return 0;
         float gCk[K][3], gDk[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) { gDk[k] = 0.f; gCk[k][0] = gCk[k][1] = gCk[k][2] = 0.f; }
-        if (E) {
-            // pass 1: D_k and C_k of every layer
-            float Dk[K], Ck[K][3];
-#pragma unroll
-            for (int k = 0; k < K; ++k) { Dk[k] = 0.f; Ck[k][0] = Ck[k][1] = Ck[k][2] = 0.f; }
-            // rolled loop: one inlined copy of the layer code keeps the kernel small
-#pragma unroll 1
-            for (int k = 0; k < nl; ++k) {
-                Layer L;
-                if (layer_build<EXTRA>(g, V, M, ids[k], px, py, L)) {
-                    Dk[k] = L.S.D;
-                    Ck[k][0] = L.S.C[0]; Ck[k][1] = L.S.C[1]; Ck[k][2] = L.S.C[2];
-                }
-            }
-            float Ds = 0.f, Ie[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                Ds += Dk[k];
-                Ie[0] = fmaf(Dk[k], Ck[k][0], Ie[0]);
-                Ie[1] = fmaf(Dk[k], Ck[k][1], Ie[1]);
-                Ie[2] = fmaf(Dk[k], Ck[k][2], Ie[2]);
-            }
-            if (Ds > 0.f) {
-                const float iD = 1.f / Ds;
-                Ie[0] *= iD; Ie[1] *= iD; Ie[2] *= iD;
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    gCk[k][0] = Dk[k] * iD * gc[0];
-                    gCk[k][1] = Dk[k] * iD * gc[1];
-                    gCk[k][2] = Dk[k] * iD * gc[2];
-                    gDk[k] = (gc[0] * (Ck[k][0] - Ie[0]) + gc[1] * (Ck[k][1] - Ie[1]) + gc[2] * (Ck[k][2] - Ie[2])) * iD;
-                }
-            }
-            // silhouette 1 - prod_k (1 - D_k)
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                float others = 1.f;
-#pragma unroll
-                for (int j = 0; j < K; ++j)
-                    if (j != k && j < nl) others *= 1.f - Dk[j];
-                if (k < nl) gDk[k] += gi4.w * others;
-            }
-        } else if (SH) {
-            gCk[0][0] = gc[0]; gCk[0][1] = gc[1]; gCk[0][2] = gc[2];
-        }
+        if (!pixel_weights<K, EXTRA>(g, V, M, pix, px, py, ids, nl, E, SH, inv, gCk, gDk)) return 0;
         // pass 2: per-layer adjoint
         unsigned stored = 0u;
 #pragma unroll 1
@@ -947,6 +972,168 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
                 inv_uv_write(g, V, M, ids[k], fadd(px, g.uv_jx), fadd(py, g.uv_jy), (int)slot);
             }
         }
+    }
+    return layers;
+}
+
+// The adjoint from stored layer ids, by layer rather than by pixel.  A layer rebuilt
+// from its face id (record, distance, barycentrics, shading) is the costliest step, and
+// by pixel it would run with the lanes of background, single-layer and gradient-free
+// pixels idle.  Each round of NT pixels (one per thread) instead
+//   1. queues, for an edge-masked pixel, each of its layers for the blend (D_k, C_k);
+//      a pixel outside the mask queues its front layer's adjoint directly
+//      (dL/dC = dL/dRGB when S^H = 1);
+//   2. rebuilds the queued layers with all threads into a (pixel, layer) table;
+//   3. forms each edge-masked pixel's dL/dC_k, dL/dD_k from the table (blend_weights)
+//      and queues its layers with a gradient;
+//   4. rebuilds and back-propagates the queued adjoints, whole multiples of NT at a
+//      time (the rest waits for the next round; the last round takes all).
+// Steps 2 and 3 are skipped in a round without edge-masked pixels.  The adjoint ring
+// holds fewer than NT leftovers plus one round's K NT items.
+template <int K>
+__host__ __device__ constexpr int adj_ring() { return NT * (K + 1); }
+__host__ __device__ constexpr size_t adj_ring_off() { return (offsetof(Smem, F) + 15) / 16 * 16; }
+template <int K>
+__host__ __device__ constexpr size_t adj_smem_bytes()
+{
+    // adjoint ring (dL/dC, dL/dD | face id, pixel and layer), blend table, blend queue
+    return adj_ring_off() + (sizeof(float4) + sizeof(int2)) * adj_ring<K>() + sizeof(float4) * NT * K +
+           sizeof(unsigned short) * NT * K;
+}
+
+template <int K, int TT>
+__device__ __forceinline__ unsigned adjoint_queued(const Globals &g, Smem &S, const ViewK &V, const MeshK &M,
+                                                   int X0, int Y0, int rho, int wlim, int hlim)
+{
+    constexpr int PPT = TT * TT / NT;
+    constexpr int QC = adj_ring<K>();
+    float4 *qg = reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(&S) + adj_ring_off());
+    int2 *qi = reinterpret_cast<int2 *>(qg + QC);        // (face id, pixel | layer << 10)
+    float4 *dc = reinterpret_cast<float4 *>(qi + QC);    // [thread][layer]: (C_k, D_k)
+    unsigned short *bq = reinterpret_cast<unsigned short *>(dc + NT * K);   // thread | layer << 8
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int hs = TT + 2 * rho;
+    unsigned layers = 0;
+    // S.qn[0]: adjoint items queued, S.qn[1]: taken (both zero at the tile's start);
+    // S.totals[0]: blend items of the round
+    if (tid == 0) S.totals[0] = 0;
+    __syncthreads();
+
+    // warp-aggregated reservation of c slots on counter *ctr: returns this lane's first slot
+    auto reserve = [&](int *ctr, int c) {
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int base = 0;
+        if (lane == 31 && incl > 0) base = atomicAdd(ctr, incl);
+        return __shfl_sync(0xffffffffu, base, 31) + incl - c;
+    };
+    auto push_adj = [&](int base, int id, int p, int k, float c0, float c1, float c2, float d) {
+        const int q = base % QC;
+        qg[q] = make_float4(c0, c1, c2, d);
+        qi[q] = make_int2(id, p | (k << 10));
+    };
+
+    for (int j = 0; j < PPT; ++j) {
+        const int p = tid + j * NT;
+        const int lx = p % TT, ly = p / TT;
+        const int X = X0 + lx, Y = Y0 + ly;
+        const long long pix = V.pix_off + (long long)Y * V.W + X;
+        const bool in = lx < wlim && ly < hlim;
+        // step 1
+        int nl = 0, id0 = 0;
+        bool E = false, front = false;
+        float4 gi4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (in) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) nl += __ldg(g.ids_in + (long long)k * g.n_pix + pix) != -1 ? 1 : 0;
+            if (nl > 0) {
+                gi4 = __ldg(reinterpret_cast<const float4 *>(g.gin) + pix);
+                if (gi4.x != 0.f || gi4.y != 0.f || gi4.z != 0.f || gi4.w != 0.f) {
+                    E = edge_mask(g, S, lx, ly, rho);
+                    // outside the mask the pixel is its front layer's colour where S^H = 1
+                    front = !E && S.sh[(ly + rho) * hs + (lx + rho)] == 1 &&
+                            (gi4.x != 0.f || gi4.y != 0.f || gi4.z != 0.f);
+                    if (front) id0 = __ldg(g.ids_in + pix) & 0x7fffffff;
+                }
+            }
+        }
+        {
+            const int b = reserve(&S.totals[0], E ? nl : 0);
+            for (int k = 0; k < (E ? nl : 0); ++k) bq[b + k] = (unsigned short)(tid | (k << 8));
+            const int a = reserve(&S.qn[0], front ? 1 : 0);
+            if (front) push_adj(a, id0, p, 0, gi4.x, gi4.y, gi4.z, 0.f);
+        }
+        __syncthreads();
+        const int nb = S.totals[0];
+        if (nb > 0) {
+            // step 2: the blend table
+            for (int i = tid; i < nb; i += NT) {
+                const int it = bq[i];
+                const int o = it & 255, k = it >> 8;
+                const int po = o + j * NT;
+                const int Xo = X0 + po % TT, Yo = Y0 + po / TT;
+                const long long pixo = V.pix_off + (long long)Yo * V.W + Xo;
+                const int id = __ldg(g.ids_in + (long long)k * g.n_pix + pixo) & 0x7fffffff;
+                Layer L;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (layer_build<false>(g, V, M, id, (float)Xo + 0.5f, (float)Yo + 0.5f, L))
+                    v = make_float4(L.S.C[0], L.S.C[1], L.S.C[2], L.S.D);
+                dc[o * K + k] = v;
+            }
+            __syncthreads();
+            // every thread has read the blend count; the next round's reservations
+            // come after this round's last barrier
+            if (tid == 0) S.totals[0] = 0;
+            // step 3
+            float gCk[K][3], gDk[K];
+            unsigned want = 0u;
+            int ids[K];
+            if (E) {
+                float Dk[K], Ck[K][3];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    gDk[k] = 0.f; gCk[k][0] = gCk[k][1] = gCk[k][2] = 0.f;
+                    const float4 v = k < nl ? dc[tid * K + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    Ck[k][0] = v.x; Ck[k][1] = v.y; Ck[k][2] = v.z; Dk[k] = v.w;
+                }
+                blend_weights<K>(Dk, Ck, nl, gi4, gCk, gDk);
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    ids[k] = k < nl ? __ldg(g.ids_in + (long long)k * g.n_pix + pix) & 0x7fffffff : 0;
+                    if (k < nl && (gDk[k] != 0.f || gCk[k][0] != 0.f || gCk[k][1] != 0.f || gCk[k][2] != 0.f))
+                        want |= 1u << k;
+                }
+            }
+            int a = reserve(&S.qn[0], __popc(want));
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if ((want >> k) & 1u) push_adj(a++, ids[k], p, k, gCk[k][0], gCk[k][1], gCk[k][2], gDk[k]);
+            __syncthreads();
+        }
+        // step 4
+        const int head = S.qn[1], n = S.qn[0] - head;
+        const int m = (j == PPT - 1) ? n : n / NT * NT;
+        for (int i = tid; i < m; i += NT) {
+            const int q = (head + i) % QC;
+            const float4 gg = qg[q];
+            const int2 it = qi[q];
+            const int pp = it.y & 1023, k = it.y >> 10;
+            const int Xq = X0 + pp % TT, Yq = Y0 + pp / TT;
+            const float px = (float)Xq + 0.5f, py = (float)Yq + 0.5f;
+            const float gCl[3] = {gg.x, gg.y, gg.z};
+            const long long slot = (V.slot_base + (long long)Yq * V.W + Xq) * K + k;
+            Layer L;
+            if (layer_build<false>(g, V, M, it.x, px, py, L)) {
+                ++layers;
+                layer_adjoint<false>(g, V, M, L, px, py, gCl, gg.w, slot, nullptr);
+            }
+        }
+        __syncthreads();   // the items taken are free and every thread has read the counters
+        if (tid == 0) S.qn[1] = head + m;
     }
     return layers;
 }
@@ -1226,7 +1413,9 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
         __syncthreads();
     }
 
-    for (int j = 0; j < PPT; ++j) {
+    if constexpr (MODE == 2) {
+        n_layers = adjoint_queued<K, TT>(g, S, V, M, X0, Y0, rho, wlim, hlim);
+    } else for (int j = 0; j < PPT; ++j) {
         const int p = tid + j * NT;
         const int lx = p % TT, ly = p / TT;
         if (lx >= wlim || ly >= hlim) continue;
@@ -1324,7 +1513,8 @@ constexpr size_t tile_smem_bytes()
     // from stored ids: the first part of Smem; otherwise Smem, the K-lists, the
     // candidate queue, the two pair-block tables; the adjoints with extras add the
     // per-thread dL/dlight slots
-    return (MODE == 2 || MODE == 3 || MODE == 4 || MODE == 7
+    return (MODE == 2   ? adj_smem_bytes<K>()
+            : MODE == 3 || MODE == 4 || MODE == 7
                 ? offsetof(Smem, F)
                 : sizeof(Smem) + sizeof(unsigned long long) * TT * TT * K + sizeof(unsigned) * QN + 2 * NBLK) +
            (MODE == 4 || MODE == 5 ? sizeof(float) * 3 * NT : 0);
