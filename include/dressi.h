@@ -49,8 +49,8 @@ extern "C" {
 #define DRESSI_API
 #endif
 
-#define DRESSI_ABI_VERSION 2   /* 2: layer ids carry the soft flag; dressi_forward_from_layers,
-                                  dressi_backward_ex */
+#define DRESSI_ABI_VERSION 3   /* 2: layer ids carry the soft flag; dressi_forward_from_layers,
+                                  dressi_backward_ex; 3: dressi_params.reuse_setup */
 #define DRESSI_MAX_K 5          /* the paper keeps K at most five (Sec. 3.4.2) */
 #define DRESSI_MAX_VIEWS 65535
 #define DRESSI_MAX_MESHES 4096
@@ -134,6 +134,14 @@ typedef struct {
     float uv_jitter[2]; /* texgrad_mode 2: offset (pixels) of every sample from its pixel
                            centre for the inverse-UV lookup; the paper draws a Sobol point per
                            frame (the caller supplies it; [-0.5, 0.5)^2 keeps it in the pixel) */
+    int32_t reuse_setup; /* dressi_backward(_ex) only: 1 = the workspace still holds what the
+                            last dressi_forward on it built for the same scene (positions
+                            unchanged), views and params -- vertex transform, face table,
+                            normals and, for layer_ids == NULL, the tile lists -- and the
+                            backward takes it instead of rebuilding it (with layer_ids == NULL
+                            it still re-rasterizes: layers and barycentrics are recomputed).
+                            0 = rebuild.  The caller guarantees the precondition; a workspace
+                            written by another call since gives wrong gradients. */
 } dressi_params;
 
 /* Size in bytes of the workspace that dressi_forward / dressi_backward need for
@@ -230,8 +238,8 @@ DRESSI_API int dressi_forward_static_scratch(const dressi_scene *scene, const dr
                                              const dressi_params *params, float *out_rgba, int32_t *layer_ids,
                                              int64_t n_pix, int32_t *dev_status, void *stream);
 
-/* Autotuner (no counterpart in the paper): times one forward + adjoint pass for
-   every execution choice (tile edge 16 / 32, schedule 1 / 2) whose workspace fits in
+/* Autotuner (no counterpart in the paper): times one forward + adjoint pass (the
+   adjoint with reuse_setup = 1, as in a training step) for every execution choice (tile edge 16 / 32, schedule 1 / 2) whose workspace fits in
    ws_bytes, keeps the fastest in params->tile / params->schedule, and sets
    params->list_cap to the tile-list entries this scene actually needs plus 25 %
    headroom (so the workspace of later calls can shrink).  The method parameters

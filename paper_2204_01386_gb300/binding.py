@@ -40,11 +40,11 @@ class DressiParams(C.Structure):
     _fields_ = [("K", C.c_int32), ("r", C.c_float), ("sigma", C.c_float), ("delta", C.c_float),
                 ("gamma", C.c_float), ("edge_mode", C.c_int32), ("shade_mode", C.c_int32),
                 ("texgrad_mode", C.c_int32), ("tile", C.c_int32), ("schedule", C.c_int32),
-                ("list_cap", C.c_int64), ("uv_jitter", C.c_float * 2)]
+                ("list_cap", C.c_int64), ("uv_jitter", C.c_float * 2), ("reuse_setup", C.c_int32)]
 
 
 # every symbol declared in include/dressi.h, with its ctypes signature
-ABI_VERSION = 2   # DRESSI_ABI_VERSION of include/dressi.h
+ABI_VERSION = 3   # DRESSI_ABI_VERSION of include/dressi.h
 
 SIGNATURES = {
     "dressi_workspace_size": (C.c_size_t, [C.POINTER(DressiScene), C.POINTER(DressiView), C.c_int32,

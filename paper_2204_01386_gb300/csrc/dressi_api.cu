@@ -71,6 +71,7 @@ static bool check_params(const dressi_params *p)
     if (p->tile != 0 && p->tile != 16 && p->tile != 32) return false;
     if (p->schedule < 0 || p->schedule > 2) return false;
     if (p->list_cap < 0) return false;
+    if (p->reuse_setup != 0 && p->reuse_setup != 1) return false;
     return true;
 }
 
@@ -292,8 +293,12 @@ static void run_setup(const Globals &g, const Plan &P, char *ws, bool need_bins,
     const Layout &L = P.lay;
     upload(P.views.data(), sizeof(ViewK) * P.views.size(), ws + L.views, s);
     upload(P.meshes.data(), sizeof(MeshK) * P.meshes.size(), ws + L.meshes, s);
+    if (need_bins) {
+        cudaMemsetAsync(ws + L.tile_count, 0, sizeof(int) * (size_t)L.total_tiles, s);
+        cudaMemsetAsync(ws + L.tile_cursor, 0, sizeof(int) * (size_t)L.total_tiles, s);
+    }
     launch_vertex(g, (int)P.views.size(), P.max_nv_view, s);
-    launch_face(g, (int)P.views.size(), P.max_nf_view, s);
+    launch_face(g, (int)P.views.size(), P.max_nf_view, need_bins, s);
     launch_tile_view(g, (int)P.views.size(), s);
     if (g.shade_mode >= 2) {
         const size_t nv = (size_t)std::max<long long>(g.n_verts_total, 1);
@@ -301,11 +306,7 @@ static void run_setup(const Globals &g, const Plan &P, char *ws, bool need_bins,
         cudaMemsetAsync(ws + L.adj_cur, 0, sizeof(int) * nv, s);
         launch_normals(g, (int)P.meshes.size(), P.max_nf, P.max_nv, s);
     }
-    if (need_bins) {
-        cudaMemsetAsync(ws + L.tile_count, 0, sizeof(int) * (size_t)L.total_tiles, s);
-        cudaMemsetAsync(ws + L.tile_cursor, 0, sizeof(int) * (size_t)L.total_tiles, s);
-        launch_bin(g, (int)P.views.size(), P.max_nf_view, s);
-    }
+    if (need_bins) launch_bin(g, (int)P.views.size(), P.max_nf_view, s);
 }
 
 // the per-tile kernel, persistent (longest face list first when the lists exist) or
@@ -509,7 +510,7 @@ int dressi_backward_ex(const dressi_scene *scene, const dressi_view *views, int3
     if (!tex_records) g.texgrad_mode = 0;
     if (gather) cudaMemsetAsync(w + P.lay.tg_keys, 0xff, sizeof(unsigned) * (size_t)P.lay.tg_slots, s);
     if (inv_uv) cudaMemsetAsync(w + P.lay.inv_uv, 0xff, sizeof(int) * (size_t)P.n_texels, s);
-    run_setup(g, P, w, layer_ids == nullptr, s);
+    if (!params->reuse_setup) run_setup(g, P, w, layer_ids == nullptr, s);
     run_tiles(g, P, w, layer_ids == nullptr, 1, s);
     if (gather)
         launch_tex_gather(g, P.lay.tg_slots, P.n_texels, (int)P.meshes.size(), P.max_texels, w + P.lay.tg_scratch,
@@ -546,12 +547,15 @@ int dressi_autotune(const dressi_scene *scene, const dressi_view *views, int32_t
             Plan P;
             if (!make_plan(scene, views, n_views, &p, n_pix, P)) { rc = DRESSI_ERR_ARG; goto done; }
             if (P.lay.total > ws_bytes) continue;
+            // the backward takes the forward's setup, as a training step does
+            dressi_params pb = p;
+            pb.reuse_setup = 1;
             float ms = 0.f;
             for (int rep = 0; rep < 5; ++rep) {   // two runs warm up, the best of the others counts
                 cudaEventRecord(e0, s);
                 int r1 = dressi_forward(scene, views, n_views, &p, out_rgba, layer_ids, n_pix, ws, ws_bytes,
                                         dev_status, stream);
-                int r2 = r1 == DRESSI_OK ? dressi_backward(scene, views, n_views, &p, out_rgba, layer_ids, n_pix,
+                int r2 = r1 == DRESSI_OK ? dressi_backward(scene, views, n_views, &pb, out_rgba, layer_ids, n_pix,
                                                            grad_pos, grad_col, grad_tex, ws, ws_bytes, dev_status,
                                                            stream)
                                          : r1;

@@ -184,75 +184,119 @@ __global__ void k_tile_view(Globals g)
 }
 
 // ---------------------------------------------------------------------------
+// tile binning: every live face goes into the list of each tile that its
+// bounding box, grown by bin_R pixels (r plus the edge-mask halo plus a guard),
+// touches.  The face table kernel counts, k_bin fills.  Order inside a list is
+// irrelevant: the peel keeps the K smallest (key, id) pairs.
+// ---------------------------------------------------------------------------
+// the tiles [tx0, tx1] x [ty0, ty1] that the grown box of screen corners (xh, yh)
+// touches; false when it misses the view
+__device__ __forceinline__ bool bin_rect(const Globals &g, const ViewK &V, const float (&xh)[3], const float (&yh)[3],
+                                         int &tx0, int &tx1, int &ty0, int &ty1)
+{
+    const float Tinv = 1.f / (float)g.tile;
+    const float x0 = fminf(xh[0], fminf(xh[1], xh[2])) - V.bin_R;
+    const float x1 = fmaxf(xh[0], fmaxf(xh[1], xh[2])) + V.bin_R;
+    const float y0 = fminf(yh[0], fminf(yh[1], yh[2])) - V.bin_R;
+    const float y1 = fmaxf(yh[0], fmaxf(yh[1], yh[2])) + V.bin_R;
+    if (x1 < 0.f || y1 < 0.f || x0 > (float)V.W || y0 > (float)V.H) return false;
+    tx0 = max(0, (int)floorf(x0 * Tinv));
+    tx1 = min(V.tiles_x - 1, (int)floorf(x1 * Tinv));
+    ty0 = max(0, (int)floorf(y0 * Tinv));
+    ty1 = min(V.tiles_y - 1, (int)floorf(y1 * Tinv));
+    return tx0 <= tx1 && ty0 <= ty1;
+}
+
+// the (face, tile) pairs of a warp's faces, one step per tile of each lane's box: the
+// lanes at the same tile in a step share one atomic (consecutive faces of a mesh are
+// mostly neighbours), and PASS 1 gives them consecutive list slots.  All 32 lanes call it.
+template <int PASS>
+__device__ __forceinline__ void bin_walk(const Globals &g, const ViewK &V, int f, bool any, int tx0, int tx1,
+                                         int ty0, int ty1)
+{
+    const int lane = threadIdx.x & 31;
+    int tx = tx0, ty = ty0;
+    bool more = any;
+    while (__any_sync(0xffffffffu, more)) {
+        const int t = more ? V.tile_base + ty * V.tiles_x + tx : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, t);
+        if (more) {
+            const int leader = __ffs(grp) - 1;
+            if (PASS == 0) {
+                if (lane == leader) atomicAdd(g.tile_count + t, __popc(grp));
+            } else {
+                int base = 0;
+                if (lane == leader) base = atomicAdd(g.tile_cursor + t, __popc(grp));
+                base = __shfl_sync(grp, base, leader) + __popc(grp & ((1u << lane) - 1u));
+                const long long idx = (long long)g.tile_off[t] + base;
+                if (idx < g.list_cap) g.lists[idx] = f;
+            }
+            if (++tx > tx1) {
+                tx = tx0;
+                if (++ty > ty1) more = false;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // face table: the record of every (view, face) -- screen corners, canonical edges,
 // lengths, area, flags -- built once per call and read by binning, staging,
-// shading and the adjoint (112 bytes each)
+// shading and the adjoint (112 bytes each).  COUNT: also the tile counts of the
+// binning (the lists' lengths).
 // ---------------------------------------------------------------------------
+template <bool COUNT>
 __global__ void k_face(Globals g)
 {
     const ViewK &V = g.views[blockIdx.y];
     const MeshK &M = g.meshes[V.mesh];
     const VRec *vr = g.vrec + V.vrec_off;
-    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < M.nF; f += gridDim.x * blockDim.x) {
+    bool bad = false;
+    // block-uniform trip count: every lane of a warp takes part in the binning steps
+    for (int f0 = blockIdx.x * blockDim.x; f0 < M.nF; f0 += gridDim.x * blockDim.x) {
+        const int f = f0 + threadIdx.x;
+        bool live = false;
         FaceRec R;
-        face_load(g, M, vr, f, R);
-        if (R.flags & FLAG_RANGE) {
-            // out of range: nothing else of the record is meaningful
+        if (f < M.nF) {
+            face_load(g, M, vr, f, R);
+            if (R.flags & FLAG_RANGE) {
+                // out of range: nothing else of the record is meaningful
+                bad = true;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) { R.vi[i] = 0; R.xh[i] = R.xl[i] = R.yh[i] = R.yl[i] = 0.f; }
+                for (int i = 0; i < 3; ++i) { R.vi[i] = 0; R.xh[i] = R.xl[i] = R.yh[i] = R.yl[i] = 0.f; }
+            }
+            live = (R.flags & FLAG_LIVE) != 0;
+            float4 *dst = reinterpret_cast<float4 *>(g.frec + V.frec_off + f);
+            dst[0] = make_float4(R.xh[0], R.xh[1], R.xh[2], R.xl[0]);
+            dst[1] = make_float4(R.xl[1], R.xl[2], R.yh[0], R.yh[1]);
+            dst[2] = make_float4(R.yh[2], R.yl[0], R.yl[1], R.yl[2]);
+            dst[3] = make_float4(R.invL[0], R.invL[1], R.invL[2], R.z[0]);
+            dst[4] = make_float4(R.z[1], R.z[2], R.invA, __int_as_float(R.flags));
+            dst[5] = make_float4(__int_as_float(R.id), __int_as_float(R.vi[0]), __int_as_float(R.vi[1]),
+                                 __int_as_float(R.vi[2]));
+            dst[6] = make_float4(R.iw[0], R.iw[1], R.iw[2], 0.f);
         }
-        float4 *dst = reinterpret_cast<float4 *>(g.frec + V.frec_off + f);
-        dst[0] = make_float4(R.xh[0], R.xh[1], R.xh[2], R.xl[0]);
-        dst[1] = make_float4(R.xl[1], R.xl[2], R.yh[0], R.yh[1]);
-        dst[2] = make_float4(R.yh[2], R.yl[0], R.yl[1], R.yl[2]);
-        dst[3] = make_float4(R.invL[0], R.invL[1], R.invL[2], R.z[0]);
-        dst[4] = make_float4(R.z[1], R.z[2], R.invA, __int_as_float(R.flags));
-        dst[5] = make_float4(__int_as_float(R.id), __int_as_float(R.vi[0]), __int_as_float(R.vi[1]),
-                             __int_as_float(R.vi[2]));
-        dst[6] = make_float4(R.iw[0], R.iw[1], R.iw[2], 0.f);
+        if (COUNT) {
+            int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+            const bool any = live && bin_rect(g, V, R.xh, R.yh, tx0, tx1, ty0, ty1);
+            bin_walk<0>(g, V, f, any, tx0, tx1, ty0, ty1);
+        }
     }
+    if (bad) atomicOr(g.status, DRESSI_DEV_FACE_RANGE);
 }
 
-// ---------------------------------------------------------------------------
-// tile binning: every live face goes into the list of each tile that its
-// bounding box, grown by bin_R pixels (r plus the edge-mask halo plus a guard),
-// touches.  pass 0 counts, pass 1 fills.  Order inside a list is irrelevant:
-// the peel keeps the K smallest (key, id) pairs.
-// ---------------------------------------------------------------------------
-template <int PASS>
+// the list entries of every (face, tile) pair, into the slots the counts' prefix gives
 __global__ void k_bin(Globals g)
 {
     const ViewK &V = g.views[blockIdx.y];
     const MeshK &M = g.meshes[V.mesh];
-    const int T = g.tile;
-    const float Tinv = 1.f / (float)T;
-    bool bad = false;
-    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < M.nF; f += gridDim.x * blockDim.x) {
+    for (int f0 = blockIdx.x * blockDim.x; f0 < M.nF; f0 += gridDim.x * blockDim.x) {
+        const int f = f0 + threadIdx.x;
+        int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
         FaceRec R;
-        if (!face_get(g, V, M, f, R)) {
-            if (R.flags & FLAG_RANGE) bad = true;
-            continue;
-        }
-        float x0 = fminf(R.xh[0], fminf(R.xh[1], R.xh[2])) - V.bin_R;
-        float x1 = fmaxf(R.xh[0], fmaxf(R.xh[1], R.xh[2])) + V.bin_R;
-        float y0 = fminf(R.yh[0], fminf(R.yh[1], R.yh[2])) - V.bin_R;
-        float y1 = fmaxf(R.yh[0], fmaxf(R.yh[1], R.yh[2])) + V.bin_R;
-        if (x1 < 0.f || y1 < 0.f || x0 > (float)V.W || y0 > (float)V.H) continue;
-        int tx0 = max(0, (int)floorf(x0 * Tinv)), tx1 = min(V.tiles_x - 1, (int)floorf(x1 * Tinv));
-        int ty0 = max(0, (int)floorf(y0 * Tinv)), ty1 = min(V.tiles_y - 1, (int)floorf(y1 * Tinv));
-        for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx) {
-                const int t = V.tile_base + ty * V.tiles_x + tx;
-                if (PASS == 0) {
-                    atomicAdd(g.tile_count + t, 1);
-                } else {
-                    const int slot = atomicAdd(g.tile_cursor + t, 1);
-                    const long long idx = (long long)g.tile_off[t] + slot;
-                    if (idx < g.list_cap) g.lists[idx] = f;
-                }
-            }
+        const bool any = f < M.nF && face_get(g, V, M, f, R) && bin_rect(g, V, R.xh, R.yh, tx0, tx1, ty0, ty1);
+        bin_walk<1>(g, V, f, any, tx0, tx1, ty0, ty1);
     }
-    if (PASS == 0 && bad) atomicOr(g.status, DRESSI_DEV_FACE_RANGE);
 }
 
 // ---------------------------------------------------------------------------
@@ -448,23 +492,24 @@ void launch_tile_view(const Globals &g, int n_views, cudaStream_t s)
     count_launch(1);
 }
 
-void launch_face(const Globals &g, int n_views, int max_nf, cudaStream_t s)
+void launch_face(const Globals &g, int n_views, int max_nf, bool count, cudaStream_t s)
 {
     dim3 grid(grid_x(max_nf, 256, 2048), n_views);
-    k_face<<<grid, 256, 0, s>>>(g);
+    if (count) k_face<true><<<grid, 256, 0, s>>>(g);
+    else k_face<false><<<grid, 256, 0, s>>>(g);
     count_launch(1);
 }
 
+// after launch_face(count = true): the counts' prefix and the lists
 void launch_bin(const Globals &g, int n_views, int max_nf, cudaStream_t s)
 {
     dim3 grid(grid_x(max_nf, 256, 2048), n_views);
-    k_bin<0><<<grid, 256, 0, s>>>(g);
     // exclusive prefix of the tile counts: tile_off[n] = total list entries
     cudaMemcpyAsync(g.tile_off, g.tile_count, sizeof(int) * (size_t)g.total_tiles, cudaMemcpyDeviceToDevice, s);
     cudaMemsetAsync(g.tile_off + g.total_tiles, 0, sizeof(int), s);
     launch_scan_inplace(g.tile_off, g.total_tiles + 1, g.scan_partial, s);
-    k_bin<1><<<grid, 256, 0, s>>>(g);
-    count_launch(2);
+    k_bin<<<grid, 256, 0, s>>>(g);
+    count_launch(1);
 }
 
 void launch_lpt_order(const Globals &g, cudaStream_t s)

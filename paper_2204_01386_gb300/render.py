@@ -136,6 +136,25 @@ class Renderer:
         dev = scene.device
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        # what the workspace holds from the last setup: (key, tile lists built) or None
+        self._setup = None
+
+    def _setup_key(self, pos):
+        """The inputs the setup (vertex transform, face table, normals, tile lists)
+        depends on: the positions (storage and version), the parameters, the workspace."""
+        t = self.scene.pos if pos is None else pos
+        self.params.reuse_setup = 0
+        return (t.data_ptr(), t._version, bytes(self.params), self.ws.data_ptr())
+
+    def _begin_setup(self):
+        """Before a call that rebuilds the setup: the workspace holds nothing
+        reusable until it returns."""
+        old, self._setup = self._setup, None
+        return old
+
+    def _end_setup(self, old, key, bins: bool):
+        # the tile lists survive a setup without them when the key is unchanged
+        self._setup = (key, bins or (old is not None and old[0] == key and old[1]))
 
     def _stream(self):
         return C.c_void_p(torch.cuda.current_stream(self.scene.device).cuda_stream)
@@ -205,6 +224,7 @@ class Renderer:
         sc = self.scene.c_struct()
         self.ws_bytes = int(self.lib.dressi_workspace_size(C.byref(sc), self.views, self.n_views, C.byref(self.params)))
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.scene.device)
+        self._setup = None
         return dict(choice)
 
     def forward(self, store_layers: bool = True, out: Optional[torch.Tensor] = None,
@@ -217,10 +237,13 @@ class Renderer:
         if not store_layers:
             ids = None
         sc = self.scene.c_struct(pos, col, tex)
+        key = self._setup_key(pos)
+        old = self._begin_setup()
         code = self.lib.dressi_forward(C.byref(sc), self.views, self.n_views, C.byref(self.params), out.data_ptr(),
                                        ids.data_ptr() if ids is not None else None, self.n_pix, self.ws.data_ptr(),
                                        self.ws_bytes, self.status.data_ptr(), self._stream())
         B.check(code, "dressi_forward")
+        self._end_setup(old, key, True)
         return out, ids
 
     def forward_from_layers(self, ids: torch.Tensor, out: Optional[torch.Tensor] = None, pos=None, col=None,
@@ -232,18 +255,26 @@ class Renderer:
         if out is None:
             out = torch.empty(self.n_pix, 4, dtype=torch.float32, device=dev)
         sc = self.scene.c_struct(pos, col, tex)
+        key = self._setup_key(pos)
+        old = self._begin_setup()
         code = self.lib.dressi_forward_from_layers(C.byref(sc), self.views, self.n_views, C.byref(self.params),
                                                    ids.data_ptr(), out.data_ptr(), self.n_pix, self.ws.data_ptr(),
                                                    self.ws_bytes, self.status.data_ptr(), self._stream())
         B.check(code, "dressi_forward_from_layers")
+        self._end_setup(old, key, False)
         return out
 
     def backward(self, grad_rgba: torch.Tensor, ids: Optional[torch.Tensor] = None, grad_pos=None, grad_col=None,
                  grad_tex=None, pos=None, col=None, tex=None, camera: bool = False, normal_map: bool = False,
-                 grad_ntex=None):
+                 grad_ntex=None, reuse_setup: Optional[bool] = None):
         """Adjoint of ``forward``: ``(grad_pos, grad_col, grad_tex)``, with ``camera``
         also ``grad_mvp [n_views, 16]`` and ``grad_light [n_views, 3]``, and with
-        ``normal_map`` (shade_mode 3) the normal-map texel gradient last."""
+        ``normal_map`` (shade_mode 3) the normal-map texel gradient last.
+
+        ``reuse_setup``: None takes the setup (vertex transform, face table, normals,
+        tile lists) the last ``forward`` left in the workspace when it was built from
+        the same positions (same storage and version) and parameters, else rebuilds
+        it; False always rebuilds."""
         dev = self.scene.device
         sc = self.scene.c_struct(pos, col, tex)
         grad_rgba = grad_rgba.contiguous()
@@ -257,6 +288,11 @@ class Renderer:
             grad_ntex = torch.empty(self.scene.n_texels, 4, dtype=torch.float32, device=dev)
         gm = torch.empty(self.n_views, 16, dtype=torch.float32, device=dev) if camera else None
         gl = torch.empty(self.n_views, 3, dtype=torch.float32, device=dev) if camera else None
+        key = self._setup_key(pos)
+        reuse = (reuse_setup is not False and self._setup is not None and self._setup[0] == key
+                 and (ids is not None or self._setup[1]))
+        self.params.reuse_setup = 1 if reuse else 0
+        old = self._setup if reuse else self._begin_setup()
         code = self.lib.dressi_backward_ex(C.byref(sc), self.views, self.n_views, C.byref(self.params),
                                            grad_rgba.data_ptr(), ids.data_ptr() if ids is not None else None,
                                            self.n_pix, grad_pos.data_ptr(),
@@ -266,7 +302,10 @@ class Renderer:
                                            gl.data_ptr() if gl is not None else None,
                                            grad_ntex.data_ptr() if normal_map else None,
                                            self.ws.data_ptr(), self.ws_bytes, self.status.data_ptr(), self._stream())
+        self.params.reuse_setup = 0
         B.check(code, "dressi_backward_ex")
+        if not reuse:
+            self._end_setup(old, key, ids is None)
         res = (grad_pos, grad_col, grad_tex)
         if camera:
             res = res + (gm, gl)

@@ -43,16 +43,16 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_layout_matches_header(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "dressi.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(dressi_mesh), sizeof(dressi_scene),'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(dressi_mesh), sizeof(dressi_scene),'
                     ' sizeof(dressi_view), sizeof(dressi_params), offsetof(dressi_view, pix_off),'
                     ' offsetof(dressi_params, list_cap), offsetof(dressi_params, schedule),'
-                    ' offsetof(dressi_params, uv_jitter));return 0;}\n')
+                    ' offsetof(dressi_params, uv_jitter), offsetof(dressi_params, reuse_setup));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [C.sizeof(B.DressiMesh), C.sizeof(B.DressiScene), C.sizeof(B.DressiView), C.sizeof(B.DressiParams),
             B.DressiView.pix_off.offset, B.DressiParams.list_cap.offset, B.DressiParams.schedule.offset,
-            B.DressiParams.uv_jitter.offset]
+            B.DressiParams.uv_jitter.offset, B.DressiParams.reuse_setup.offset]
     assert got == want
 
 
@@ -137,7 +137,7 @@ def test_status_strings(lib):
         assert lib.dressi_status_string(c)
     for b in (0, 1, 2, 4):
         assert lib.dressi_dev_status_string(b)
-    assert lib.dressi_abi_version() == B.ABI_VERSION == 2
+    assert lib.dressi_abi_version() == B.ABI_VERSION == 3
 
 
 def test_product_has_no_fallback(monkeypatch, tmp_path):
