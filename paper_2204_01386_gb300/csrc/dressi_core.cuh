@@ -244,6 +244,12 @@ __device__ __forceinline__ bool face_get(const Globals &g, const ViewK &V, const
     return (R.flags & FLAG_LIVE) != 0;
 }
 
+// a hint that the line holding address a will be read soon: fetch it into L2
+__device__ __forceinline__ void prefetch_l2(const void *a)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 // face_get into shared memory: seven 16-byte copies
 __device__ __forceinline__ bool face_stage(const Globals &g, const ViewK &V, const MeshK &m, int f, FaceRec &dst)
 {

@@ -1191,11 +1191,20 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
         const int n = fallback ? M.nF : (int)(le - lb);
         if (fallback && tid == 0) atomicOr(g.status, DRESSI_DEV_TILE_OVERFLOW);
         single_chunk = n <= CH;
+        // the id -> slot hash serves the forward's shading of a tile staged in one chunk
+        const bool use_hash = !BWD && single_chunk;
         for (int c0 = 0; c0 < n; c0 += CH) {
             const int nch = min(CH, n - c0);
+            // the next chunk's face ids, loaded under this chunk's staging: their records
+            // are prefetched into L2 once this chunk is staged
+            const int nnext = min(CH, n - c0 - CH);
+            int fnext = -1;
+            if (tid < nnext) fnext = fallback ? c0 + CH + tid : g.lists[lb + c0 + CH + tid];
             __syncthreads();   // previous chunk consumed
-            for (int i = tid; i < HASH; i += NT) S.hash[i] = make_int2(-1, -1);
-            __syncthreads();
+            if (use_hash) {
+                for (int i = tid; i < HASH; i += NT) S.hash[i] = make_int2(-1, -1);
+                __syncthreads();
+            }
             int cnt = 0, hcnt = 0;
             if (tid < nch) {
                 const int f = fallback ? c0 + tid : g.lists[lb + c0 + tid];
@@ -1230,13 +1239,21 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                         }
                     }
                     // id -> slot for the shading phase
-                    unsigned hsh = ((unsigned)R.id * 2654435761u) & (HASH - 1);
-                    for (int probe = 0; probe < HASH; ++probe) {
-                        const int prev = atomicCAS(&S.hash[hsh].x, -1, R.id);
-                        if (prev == -1 || prev == R.id) { S.hash[hsh].y = tid; break; }
-                        hsh = (hsh + 1) & (HASH - 1);
+                    if (use_hash) {
+                        unsigned hsh = ((unsigned)R.id * 2654435761u) & (HASH - 1);
+                        for (int probe = 0; probe < HASH; ++probe) {
+                            const int prev = atomicCAS(&S.hash[hsh].x, -1, R.id);
+                            if (prev == -1 || prev == R.id) { S.hash[hsh].y = tid; break; }
+                            hsh = (hsh + 1) & (HASH - 1);
+                        }
                     }
                 }
+            }
+            if ((unsigned)fnext < (unsigned)M.nF) {
+                // both 128-byte lines a 112-byte record can touch
+                const char *a = reinterpret_cast<const char *>(g.frec + V.frec_off + fnext);
+                prefetch_l2(a);
+                prefetch_l2(a + sizeof(FaceRec) - 1);
             }
             // exclusive prefix of the two pair counts over the chunk
             {

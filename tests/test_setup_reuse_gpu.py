@@ -33,8 +33,9 @@ def _backward(r, grad, ids, reuse):
 def _close(a, b):
     if a is None:
         return b is None
-    # float atomics accumulate in any order
-    return torch.allclose(a, b, rtol=1e-5, atol=1e-7 * max(1.0, b.abs().max().item()))
+    # float atomics accumulate in any order: equal up to summation order, far inside
+    # the gradient tolerance against the oracle (relative L2 1e-4)
+    return (a - b).norm().item() <= 1e-6 * max(b.norm().item(), 1e-30)
 
 
 @pytest.mark.parametrize("cfg,store", [("config1", True), ("config1", False), ("config2", True),
