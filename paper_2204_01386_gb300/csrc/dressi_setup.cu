@@ -447,8 +447,25 @@ __global__ void k_normal_bwd(Globals g)
 __global__ void k_l2(const float *out, const float *tgt, long long n, float *grad, float *loss)
 {
     float acc = 0.f;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float d = out[i] - tgt[i];
+    const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long done = 0;
+    if (((reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(tgt) | reinterpret_cast<uintptr_t>(grad)) &
+         15) == 0) {
+        // 16-byte accesses over the whole float4s, then the scalar tail
+        const long long n4 = n >> 2;
+        const float4 *o4 = reinterpret_cast<const float4 *>(out), *t4 = reinterpret_cast<const float4 *>(tgt);
+        float4 *g4 = reinterpret_cast<float4 *>(grad);
+        for (long long i = i0; i < n4; i += stride) {
+            const float4 a = __ldg(o4 + i), b = __ldg(t4 + i);
+            const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
+            g4[i] = make_float4(2.f * dx, 2.f * dy, 2.f * dz, 2.f * dw);
+            acc += dx * dx + dy * dy + dz * dz + dw * dw;
+        }
+        done = n4 << 2;
+    }
+    for (long long i = done + i0; i < n; i += stride) {
+        const float d = out[i] - tgt[i];
         grad[i] = 2.f * d;
         acc += d * d;
     }

@@ -976,6 +976,128 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
     return layers;
 }
 
+// S^H, edge mask, shading and blend of one round of pixels (one per thread; lanes
+// outside the image take part with no layer).  A warp shades the layers its pixels
+// blend -- all of a pixel's layers inside the edge mask, else the front one where
+// S^H = 1 -- as one list, 32 at a time, so pixels with three layers, one or none
+// share full warps; each pixel then takes its layers' colours and coverages back by
+// shuffles and blends them in layer order.
+template <int K, int TT, bool EXTRA>
+__device__ __forceinline__ unsigned finish_forward(const Globals &g, const Smem &S, const ViewK &V, const MeshK &M,
+                                                   int X0, int Y0, int p, int rho, bool in, const int (&ids)[K],
+                                                   unsigned hardbits, bool single_chunk)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int lx = p % TT, ly = p / TT;
+    const int hs = TT + 2 * rho;
+    int nl = 0;
+    bool SH = false, E = false;
+    long long pix = 0;
+    if (in) {
+        pix = V.pix_off + (long long)(Y0 + ly) * V.W + (X0 + lx);
+#pragma unroll
+        for (int k = 0; k < K; ++k) nl += (ids[k] != 0x7fffffff) ? 1 : 0;
+        SH = S.sh[(ly + rho) * hs + (lx + rho)] == 1;
+        E = edge_mask(g, S, lx, ly, rho);
+        if (g.ids) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                // stored layer: the face index, with bit 31 set for a soft fragment
+                const unsigned soft = ((hardbits >> k) & 1u) ? 0u : 0x80000000u;
+                g.ids[(long long)k * g.n_pix + pix] = (k < nl) ? (int)((unsigned)ids[k] | soft) : -1;
+            }
+        }
+    }
+    // the layers blended (outside the edge mask only the front one is seen), and their
+    // place in the warp's list
+    const int cnt = E ? nl : (SH && nl > 0 ? 1 : 0);
+    int off = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, off, o);
+        if (lane >= o) off += y;
+    }
+    const int tot = __shfl_sync(FULL, off, 31);
+    off -= cnt;
+
+    float Cs[3] = {0.f, 0.f, 0.f}, C1[3] = {0.f, 0.f, 0.f};
+    float Ds = 0.f, prod = 1.f;
+    unsigned layers = 0;
+    for (int w = 0; w * 32 < tot; ++w) {
+        const int i = w * 32 + lane;
+        // the pixel (lane) whose layers include list entry i: the last one starting at or before it
+        int o = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1)
+            if (__shfl_sync(FULL, off, o + st) <= i) o += st;
+        const int k = i - __shfl_sync(FULL, off, o);
+        int id = 0x7fffffff;
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            const int v = __shfl_sync(FULL, ids[kk], o);
+            if (kk == k) id = v;
+        }
+        float C[3] = {0.f, 0.f, 0.f}, D = 0.f;
+        int live = 0;
+        if (i < tot) {
+            // re-evaluate the layer at its pixel (from shared memory when the whole tile
+            // list was staged at once): distance and barycentrics, then the shading
+            const int po = p - lane + o;
+            const float px = (float)(X0 + po % TT) + 0.5f, py = (float)(Y0 + po / TT) + 0.5f;
+            const int slot = single_chunk ? find_slot(S, id) : -1;
+            FaceRec R;
+            bool ok;
+            if (slot >= 0) {
+                R = S.F[slot];
+                ok = (R.flags & FLAG_LIVE) != 0;
+            } else {
+                ok = face_get(g, V, M, id, R);
+            }
+            Frag fr;
+            if (ok && eval_face(R, px, py, V.r_px, V.half_inv_S, fr)) {
+                Shade Sh;
+                frag_lambda(R, fr, Sh.lam);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) { Sh.vi[q] = R.vi[q]; Sh.iw[q] = R.iw[q]; }
+                shade<EXTRA>(g, V, M, fr.dist, Sh);
+                C[0] = Sh.C[0]; C[1] = Sh.C[1]; C[2] = Sh.C[2];
+                D = Sh.D;
+                live = 1;
+                ++layers;
+            }
+        }
+        // this pixel's layers among the entries of this pass, in layer order
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            const int src = off + kk - w * 32;
+            const int sl = src & 31;
+            const float c0 = __shfl_sync(FULL, C[0], sl), c1 = __shfl_sync(FULL, C[1], sl),
+                        c2 = __shfl_sync(FULL, C[2], sl), d = __shfl_sync(FULL, D, sl);
+            const int lv = __shfl_sync(FULL, live, sl);
+            if (kk < cnt && src >= 0 && src < 32 && lv) {
+                Cs[0] = ffma(d, c0, Cs[0]);
+                Cs[1] = ffma(d, c1, Cs[1]);
+                Cs[2] = ffma(d, c2, Cs[2]);
+                Ds = fadd(Ds, d);
+                prod = fmul(prod, fsub(1.f, d));
+                if (kk == 0) { C1[0] = c0; C1[1] = c1; C1[2] = c2; }
+            }
+        }
+    }
+    if (in) {
+        float4 o;
+        if (E) {
+            const float iD = Ds > 0.f ? __fdiv_rn(1.f, Ds) : 0.f;
+            o = make_float4(fmul(Cs[0], iD), fmul(Cs[1], iD), fmul(Cs[2], iD), fsub(1.f, prod));
+        } else {
+            o = SH ? make_float4(C1[0], C1[1], C1[2], 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        reinterpret_cast<float4 *>(g.out)[pix] = o;
+    }
+    return layers;
+}
+
 // The adjoint from stored layer ids, by layer rather than by pixel.  A layer rebuilt
 // from its face id (record, distance, barycentrics, shading) is the costliest step, and
 // by pixel it would run with the lanes of background, single-layer and gradient-free
@@ -1435,10 +1557,15 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
     } else for (int j = 0; j < PPT; ++j) {
         const int p = tid + j * NT;
         const int lx = p % TT, ly = p / TT;
-        if (lx >= wlim || ly >= hlim) continue;
+        const bool in = lx < wlim && ly < hlim;
+        // the forward's shading is warp-collective: every lane takes part
+        if (BWD && !in) continue;
         int ids[K];
         unsigned hardbits = 0u;
-        if (!from_ids) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) ids[k] = 0x7fffffff;
+        if (!in) {
+        } else if (!from_ids) {
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const unsigned long long v = kbuf[p * K + k];
@@ -1462,7 +1589,11 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                 ids[k] = id == -1 ? 0x7fffffff : (id & 0x7fffffff);
             }
         }
-        n_layers += finish_pixel<K, BWD, TT, EXTRA>(g, S, V, M, X0, Y0, lx, ly, rho, ids, hardbits, single_chunk, glacc);
+        if constexpr (BWD)
+            n_layers += finish_pixel<K, true, TT, EXTRA>(g, S, V, M, X0, Y0, lx, ly, rho, ids, hardbits, single_chunk,
+                                                         glacc);
+        else
+            n_layers += finish_forward<K, TT, EXTRA>(g, S, V, M, X0, Y0, p, rho, in, ids, hardbits, single_chunk);
     }
     if (light_grad) {
         // this tile's dL/dlight: warp sums, one atomic per warp and component
