@@ -1098,6 +1098,149 @@ __device__ __forceinline__ unsigned finish_forward(const Globals &g, const Smem 
     return layers;
 }
 
+// The re-rasterizing adjoint of one round of pixels (one per thread; lanes outside the
+// image take part with no layer), warp-collective like the forward's shading: a warp
+// rebuilds the layers its edge-masked pixels blend (for D_k, C_k) as one list, each
+// pixel forms dL/dC_k, dL/dD_k (blend_weights), and the warp then rebuilds and
+// back-propagates the layers with a gradient as a second list.
+template <int K, int TT>
+__device__ __forceinline__ unsigned adjoint_warp(const Globals &g, const Smem &S, const ViewK &V, const MeshK &M,
+                                                 int X0, int Y0, int p, int rho, bool in, const int (&ids)[K])
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int lx = p % TT, ly = p / TT;
+    const int hs = TT + 2 * rho;
+    int nl = 0;
+    bool E = false, SH = false, active = false;
+    float4 gi4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (in) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) nl += (ids[k] != 0x7fffffff) ? 1 : 0;
+        if (nl > 0) {
+            gi4 = __ldg(reinterpret_cast<const float4 *>(g.gin) + V.pix_off + (long long)(Y0 + ly) * V.W + (X0 + lx));
+            active = gi4.x != 0.f || gi4.y != 0.f || gi4.z != 0.f || gi4.w != 0.f;
+            if (active) {
+                SH = S.sh[(ly + rho) * hs + (lx + rho)] == 1;
+                E = edge_mask(g, S, lx, ly, rho);
+            }
+        }
+    }
+    // list entry i of a warp list with per-lane counts cnt (exclusive offsets off):
+    // the owning lane
+    auto owner = [&](int off, int i) {
+        int o = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1)
+            if (__shfl_sync(FULL, off, o + st) <= i) o += st;
+        return o;
+    };
+    auto scan = [&](int cnt, int &tot) {
+        int off = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, off, o);
+            if (lane >= o) off += y;
+        }
+        tot = __shfl_sync(FULL, off, 31);
+        return off - cnt;
+    };
+
+    // pass 1: D_k and C_k of every layer of an edge-masked pixel
+    float Dk[K], Ck[K][3];
+#pragma unroll
+    for (int k = 0; k < K; ++k) { Dk[k] = 0.f; Ck[k][0] = Ck[k][1] = Ck[k][2] = 0.f; }
+    {
+        const int cnt = (active && E) ? nl : 0;
+        int tot;
+        const int off = scan(cnt, tot);
+        for (int w = 0; w * 32 < tot; ++w) {
+            const int i = w * 32 + lane;
+            const int o = owner(off, i);
+            const int k = i - __shfl_sync(FULL, off, o);
+            int id = 0x7fffffff;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                const int v = __shfl_sync(FULL, ids[kk], o);
+                if (kk == k) id = v;
+            }
+            float C[3] = {0.f, 0.f, 0.f}, D = 0.f;
+            if (i < tot) {
+                const int po = p - lane + o;
+                Layer L;
+                if (layer_build<false>(g, V, M, id, (float)(X0 + po % TT) + 0.5f, (float)(Y0 + po / TT) + 0.5f, L)) {
+                    C[0] = L.S.C[0]; C[1] = L.S.C[1]; C[2] = L.S.C[2];
+                    D = L.S.D;
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                const int src = off + kk - w * 32;
+                const int sl = src & 31;
+                const float c0 = __shfl_sync(FULL, C[0], sl), c1 = __shfl_sync(FULL, C[1], sl),
+                            c2 = __shfl_sync(FULL, C[2], sl), d = __shfl_sync(FULL, D, sl);
+                if (kk < cnt && src >= 0 && src < 32) {
+                    Dk[kk] = d;
+                    Ck[kk][0] = c0; Ck[kk][1] = c1; Ck[kk][2] = c2;
+                }
+            }
+        }
+    }
+    // the blend's adjoint per pixel
+    float gCk[K][3], gDk[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) { gDk[k] = 0.f; gCk[k][0] = gCk[k][1] = gCk[k][2] = 0.f; }
+    if (active) {
+        if (E) blend_weights<K>(Dk, Ck, nl, gi4, gCk, gDk);
+        else if (SH) { gCk[0][0] = gi4.x; gCk[0][1] = gi4.y; gCk[0][2] = gi4.z; }
+    }
+    unsigned want = 0u;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        if (k < nl && (gDk[k] != 0.f || gCk[k][0] != 0.f || gCk[k][1] != 0.f || gCk[k][2] != 0.f)) want |= 1u << k;
+
+    // pass 2: the adjoints of the layers with a gradient
+    unsigned layers = 0;
+    {
+        int tot;
+        const int off = scan(__popc(want), tot);
+        for (int w = 0; w * 32 < tot; ++w) {
+            const int i = w * 32 + lane;
+            const int o = owner(off, i);
+            const int j = i - __shfl_sync(FULL, off, o);   // the owner's j-th layer with a gradient
+            const unsigned wm = __shfl_sync(FULL, want, o);
+            int k = 0;
+#pragma unroll
+            for (int kk = 0, seen = 0; kk < K; ++kk)
+                if ((wm >> kk) & 1u) {
+                    if (seen == j) k = kk;
+                    ++seen;
+                }
+            int id = 0x7fffffff;
+            float gC[3] = {0.f, 0.f, 0.f}, gD = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                const int v = __shfl_sync(FULL, ids[kk], o);
+                const float a0 = __shfl_sync(FULL, gCk[kk][0], o), a1 = __shfl_sync(FULL, gCk[kk][1], o),
+                            a2 = __shfl_sync(FULL, gCk[kk][2], o), b = __shfl_sync(FULL, gDk[kk], o);
+                if (kk == k) { id = v; gC[0] = a0; gC[1] = a1; gC[2] = a2; gD = b; }
+            }
+            if (i < tot) {
+                const int po = p - lane + o;
+                const int Xo = X0 + po % TT, Yo = Y0 + po / TT;
+                const float px = (float)Xo + 0.5f, py = (float)Yo + 0.5f;
+                const long long slot = (V.slot_base + (long long)Yo * V.W + Xo) * K + k;
+                Layer L;
+                if (layer_build<false>(g, V, M, id, px, py, L)) {
+                    ++layers;
+                    layer_adjoint<false>(g, V, M, L, px, py, gC, gD, slot, nullptr);
+                }
+            }
+        }
+    }
+    return layers;
+}
+
 // The adjoint from stored layer ids, by layer rather than by pixel.  A layer rebuilt
 // from its face id (record, distance, barycentrics, shading) is the costliest step, and
 // by pixel it would run with the lanes of background, single-layer and gradient-free
@@ -1558,8 +1701,9 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
         const int p = tid + j * NT;
         const int lx = p % TT, ly = p / TT;
         const bool in = lx < wlim && ly < hlim;
-        // the forward's shading is warp-collective: every lane takes part
-        if (BWD && !in) continue;
+        // the forward's shading and the re-rasterizing adjoint are warp-collective: every
+        // lane takes part
+        if (BWD && MODE != 1 && !in) continue;
         int ids[K];
         unsigned hardbits = 0u;
 #pragma unroll
@@ -1589,7 +1733,9 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                 ids[k] = id == -1 ? 0x7fffffff : (id & 0x7fffffff);
             }
         }
-        if constexpr (BWD)
+        if constexpr (MODE == 1)
+            n_layers += adjoint_warp<K, TT>(g, S, V, M, X0, Y0, p, rho, in, ids);
+        else if constexpr (BWD)
             n_layers += finish_pixel<K, true, TT, EXTRA>(g, S, V, M, X0, Y0, lx, ly, rho, ids, hardbits, single_chunk,
                                                          glacc);
         else
