@@ -256,9 +256,9 @@ def ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        r.forward(store_layers=store, out=out, ids=ids)
+        # forward with the L2 loss fused in (out, dL/dout, loss), then the adjoint
         loss.zero_()
-        r.l2_grad(out, target, grad, loss)
+        r.forward(store_layers=store, out=out, ids=ids, target=target, grad=grad, loss=loss)
         r.backward(grad, ids=ids, grad_pos=gp, grad_tex=gt)
         if world > 1:
             dist.all_reduce(gp)
@@ -379,8 +379,7 @@ def ours(args, rank, world, local_rank):
         def plain_step():
             for i, (rr, v) in enumerate(zip(rv, s.views)):
                 sl = slice(offs[i], offs[i] + v.width * v.height)
-                rr.forward(store_layers=store, out=out[sl], ids=idv[i])
-                rr.l2_grad(out[sl], target[sl], grad[sl], loss)
+                rr.forward(store_layers=store, out=out[sl], ids=idv[i], target=target[sl], grad=grad[sl], loss=loss)
                 rr.backward(grad[sl], ids=idv[i], grad_pos=gp, grad_tex=gt)
 
         for _ in range(2):
@@ -457,9 +456,8 @@ def ours(args, rank, world, local_rank):
 
         def make_step(pos, tex, tgt):
             def f():
-                r.forward(store_layers=store, out=out, ids=ids, pos=pos, tex=tex)
                 loss.zero_()
-                r.l2_grad(out, tgt, grad, loss)
+                r.forward(store_layers=store, out=out, ids=ids, pos=pos, tex=tex, target=tgt, grad=grad, loss=loss)
                 r.backward(grad, ids=ids, grad_pos=gp, grad_tex=gt, pos=pos, tex=tex)
                 if world > 1:
                     dist.all_reduce(gp)

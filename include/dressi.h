@@ -50,7 +50,8 @@ extern "C" {
 #endif
 
 #define DRESSI_ABI_VERSION 3   /* 2: layer ids carry the soft flag; dressi_forward_from_layers,
-                                  dressi_backward_ex; 3: dressi_params.reuse_setup */
+                                  dressi_backward_ex; 3: dressi_params.reuse_setup,
+                                  dressi_forward_l2 */
 #define DRESSI_MAX_K 5          /* the paper keeps K at most five (Sec. 3.4.2) */
 #define DRESSI_MAX_VIEWS 65535
 #define DRESSI_MAX_MESHES 4096
@@ -165,6 +166,21 @@ DRESSI_API size_t dressi_workspace_size(const dressi_scene *scene, const dressi_
 DRESSI_API int dressi_forward(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
                    const dressi_params *params, float *out_rgba, int32_t *layer_ids, int64_t n_pix,
                    void *ws, size_t ws_bytes, int32_t *dev_status, void *stream);
+
+/* dressi_forward fused with an L2 image loss L = sum (out_rgba - target)^2 (no counterpart
+   in the paper; the loss of a fit to target images): besides out_rgba it writes
+   grad_rgba = dL/d(out_rgba) = 2 (out_rgba - target), the input of dressi_backward, and
+   adds L to *loss_accum.  grad_rgba equals dressi_forward followed by
+   dressi_l2_loss_grad bit for bit; the loss is summed in another order.
+     target     DEVICE [n_pix][4] float (16-byte aligned).
+     grad_rgba  DEVICE [n_pix][4] float, written for the pixels of the views (the pixels
+                of the packed buffers outside every view are left as they are).
+     loss_accum DEVICE float or NULL; not cleared.
+   All other arguments as for dressi_forward. */
+DRESSI_API int dressi_forward_l2(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
+                                 const dressi_params *params, const float *target, float *out_rgba,
+                                 float *grad_rgba, float *loss_accum, int32_t *layer_ids, int64_t n_pix,
+                                 void *ws, size_t ws_bytes, int32_t *dev_status, void *stream);
 
 /* Forward from stored layers: the cached-rasterization counterpart of the reactive cache
    of Sec. 3.3.3 (Stage Packing), which skips passes whose inputs did not change -- here,

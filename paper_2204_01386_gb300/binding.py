@@ -51,6 +51,9 @@ SIGNATURES = {
                                            C.POINTER(DressiParams)]),
     "dressi_forward": (C.c_int, [C.POINTER(DressiScene), C.POINTER(DressiView), C.c_int32, C.POINTER(DressiParams),
                                  C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
+    "dressi_forward_l2": (C.c_int, [C.POINTER(DressiScene), C.POINTER(DressiView), C.c_int32,
+                                    C.POINTER(DressiParams), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_int64, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
     "dressi_backward": (C.c_int, [C.POINTER(DressiScene), C.POINTER(DressiView), C.c_int32, C.POINTER(DressiParams),
                                   C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),

@@ -430,6 +430,32 @@ int dressi_forward(const dressi_scene *scene, const dressi_view *views, int32_t 
     return cudaGetLastError() == cudaSuccess ? DRESSI_OK : DRESSI_ERR_LAUNCH;
 }
 
+int dressi_forward_l2(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
+                      const dressi_params *params, const float *target, float *out_rgba, float *grad_rgba,
+                      float *loss_accum, int32_t *layer_ids, int64_t n_pix, void *ws, size_t ws_bytes,
+                      int32_t *dev_status, void *stream)
+{
+    Plan P;
+    if (!target || !out_rgba || !grad_rgba || !dev_status || n_pix < 1) return DRESSI_ERR_ARG;
+    if (((reinterpret_cast<uintptr_t>(target) | reinterpret_cast<uintptr_t>(out_rgba) |
+          reinterpret_cast<uintptr_t>(grad_rgba)) & 15) != 0)
+        return DRESSI_ERR_ARG;
+    if (!make_plan(scene, views, n_views, params, n_pix, P)) return DRESSI_ERR_ARG;
+    if (!ws || ws_bytes < P.lay.total) return DRESSI_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaGetLastError();
+    char *w = static_cast<char *>(ws);
+    Globals g = make_globals(scene, params, P, w, n_pix, dev_status);
+    g.out = out_rgba;
+    g.ids = layer_ids;
+    g.l2_target = target;
+    g.l2_grad = grad_rgba;
+    g.l2_loss = loss_accum;
+    run_setup(g, P, w, true, s);
+    run_tiles(g, P, w, true, 0, s);
+    return cudaGetLastError() == cudaSuccess ? DRESSI_OK : DRESSI_ERR_LAUNCH;
+}
+
 int dressi_forward_static_scratch(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
                                   const dressi_params *params, float *out_rgba, int32_t *layer_ids, int64_t n_pix,
                                   int32_t *dev_status, void *stream)

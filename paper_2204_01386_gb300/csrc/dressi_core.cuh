@@ -117,6 +117,9 @@ struct Globals {
     // forward
     float *out;
     int *ids;             // [K][n_pix] or nullptr
+    const float *l2_target;   // fused L2 loss: [n_pix][4] target, or nullptr
+    float *l2_grad;       // [n_pix][4] 2 (out - target)
+    float *l2_loss;       // sum of (out - target)^2 added here, or nullptr
     // backward
     const float *gin;
     const int *ids_in;    // [K][n_pix] or nullptr (recompute)

@@ -875,15 +875,15 @@ __device__ __forceinline__ bool pixel_weights(const Globals &g, const ViewK &V, 
     return true;
 }
 
-// S^H, edge mask, shading and blend (forward) or the adjoint (BWD) of one pixel
-// whose K layer ids are known; S.sh holds the tile's S^H with its ring.
-template <int K, bool BWD, int TT, bool EXTRA>
-__device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S, const ViewK &V, const MeshK &M,
-                                             int X0, int Y0, int lx, int ly, int rho,
-                                             const int (&ids)[K], unsigned hardbits, bool single_chunk, float *gl)
+// The adjoint of one pixel whose K layer ids are known, by pixel: the adjoints with
+// the extras (light gradient, inverse UV, normal map); S.sh holds the tile's S^H with its
+// ring.
+template <int K, int TT, bool EXTRA>
+__device__ __forceinline__ unsigned adjoint_pixel(const Globals &g, const Smem &S, const ViewK &V, const MeshK &M,
+                                                  int X0, int Y0, int lx, int ly, int rho, const int (&ids)[K],
+                                                  float *gl)
 {
-    const int X = X0 + lx, Y = Y0 + ly;
-    const int lx_g = X, ly_g = Y;   // view-local pixel coordinates
+    const int X = X0 + lx, Y = Y0 + ly;   // view-local pixel coordinates
     const float px = (float)X + 0.5f, py = (float)Y + 0.5f;
     const int hs = TT + 2 * rho;
     const long long pix = V.pix_off + (long long)Y * V.W + X;
@@ -894,83 +894,32 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
     const bool E = edge_mask(g, S, lx, ly, rho);
 
     unsigned layers = 0;
-    if (!BWD) {
-        if (g.ids) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                // stored layer: the face index, with bit 31 set for a soft fragment
-                const unsigned soft = ((hardbits >> k) & 1u) ? 0u : 0x80000000u;
-                g.ids[(long long)k * g.n_pix + pix] = (k < nl) ? (int)((unsigned)ids[k] | soft) : -1;
-            }
-        }
-        float Cs[3] = {0.f, 0.f, 0.f}, C1[3] = {0.f, 0.f, 0.f};
-        float Ds = 0.f, prod = 1.f;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            // outside the edge mask only the front layer is seen
-            if (!(k < nl && (E || k == 0))) continue;
-            // re-evaluate the layer at this pixel (from shared memory when the whole tile
-            // list was staged at once): distance and barycentrics
-            const int slot = single_chunk ? find_slot(S, ids[k]) : -1;
-            FaceRec R;
-            bool live;
-            if (slot >= 0) {
-                R = S.F[slot];
-                live = (R.flags & FLAG_LIVE) != 0;
-            } else {
-                live = face_get(g, V, M, ids[k], R);
-            }
-            Frag fr;
-            if (!live || !eval_face(R, px, py, V.r_px, V.half_inv_S, fr)) continue;
-            Shade Sh;
+    const bool inv = EXTRA && g.texgrad_mode == 2;
+    float gCk[K][3], gDk[K];
+    if (!pixel_weights<K, EXTRA>(g, V, M, pix, px, py, ids, nl, E, SH, inv, gCk, gDk)) return 0;
+    // the adjoint of each layer with a gradient
+    unsigned stored = 0u;
+#pragma unroll 1
+    for (int k = 0; k < nl; ++k) {
+        const float gCl[3] = {gCk[k][0], gCk[k][1], gCk[k][2]};
+        const float gDl = gDk[k];
+        const bool any = gDl != 0.f || gCl[0] != 0.f || gCl[1] != 0.f || gCl[2] != 0.f;
+        Layer L;
+        const long long slot = (V.slot_base + (long long)Y * V.W + X) * K + k;
+        if (any && layer_build<EXTRA>(g, V, M, ids[k], px, py, L)) {
             ++layers;
-            frag_lambda(R, fr, Sh.lam);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) { Sh.vi[i] = R.vi[i]; Sh.iw[i] = R.iw[i]; }
-            shade<EXTRA>(g, V, M, fr.dist, Sh);
-            Cs[0] = ffma(Sh.D, Sh.C[0], Cs[0]);
-            Cs[1] = ffma(Sh.D, Sh.C[1], Cs[1]);
-            Cs[2] = ffma(Sh.D, Sh.C[2], Cs[2]);
-            Ds = fadd(Ds, Sh.D);
-            prod = fmul(prod, fsub(1.f, Sh.D));
-            if (k == 0) { C1[0] = Sh.C[0]; C1[1] = Sh.C[1]; C1[2] = Sh.C[2]; }
+            if (layer_adjoint<EXTRA>(g, V, M, L, px, py, gCl, gDl, slot, gl)) stored |= 1u << k;
         }
-        float4 o;
-        if (E) {
-            const float iD = Ds > 0.f ? __fdiv_rn(1.f, Ds) : 0.f;
-            o = make_float4(fmul(Cs[0], iD), fmul(Cs[1], iD), fmul(Cs[2], iD), fsub(1.f, prod));
-        } else {
-            o = SH ? make_float4(C1[0], C1[1], C1[2], 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        reinterpret_cast<float4 *>(g.out)[pix] = o;
-    } else {
-        const bool inv = EXTRA && g.texgrad_mode == 2;
-        float gCk[K][3], gDk[K];
-        if (!pixel_weights<K, EXTRA>(g, V, M, pix, px, py, ids, nl, E, SH, inv, gCk, gDk)) return 0;
-        // pass 2: per-layer adjoint
-        unsigned stored = 0u;
+    }
+    if (inv) {
+        // every shaded sample (the layers the forward blends) claims its texel; a sample
+        // without a texture gradient offers dL/dA = 0
 #pragma unroll 1
         for (int k = 0; k < nl; ++k) {
-            const float gCl[3] = {gCk[k][0], gCk[k][1], gCk[k][2]};
-            const float gDl = gDk[k];
-            const bool any = gDl != 0.f || gCl[0] != 0.f || gCl[1] != 0.f || gCl[2] != 0.f;
-            Layer L;
-            const long long slot = (V.slot_base + (long long)ly_g * V.W + lx_g) * K + k;
-            if (any && layer_build<EXTRA>(g, V, M, ids[k], px, py, L)) {
-                ++layers;
-                if (layer_adjoint<EXTRA>(g, V, M, L, px, py, gCl, gDl, slot, gl)) stored |= 1u << k;
-            }
-        }
-        if (inv) {
-            // pass 3: every shaded sample (the layers the forward blends) claims its texel;
-            // a sample without a texture gradient offers dL/dA = 0
-#pragma unroll 1
-            for (int k = 0; k < nl; ++k) {
-                if (!(E || k == 0)) continue;
-                const long long slot = (V.slot_base + (long long)ly_g * V.W + lx_g) * K + k;
-                if (!((stored >> k) & 1u)) g.tg_pay0[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
-                inv_uv_write(g, V, M, ids[k], fadd(px, g.uv_jx), fadd(py, g.uv_jy), (int)slot);
-            }
+            if (!(E || k == 0)) continue;
+            const long long slot = (V.slot_base + (long long)Y * V.W + X) * K + k;
+            if (!((stored >> k) & 1u)) g.tg_pay0[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+            inv_uv_write(g, V, M, ids[k], fadd(px, g.uv_jx), fadd(py, g.uv_jy), (int)slot);
         }
     }
     return layers;
@@ -985,7 +934,7 @@ __device__ __forceinline__ unsigned finish_pixel(const Globals &g, const Smem &S
 template <int K, int TT, bool EXTRA>
 __device__ __forceinline__ unsigned finish_forward(const Globals &g, const Smem &S, const ViewK &V, const MeshK &M,
                                                    int X0, int Y0, int p, int rho, bool in, const int (&ids)[K],
-                                                   unsigned hardbits, bool single_chunk)
+                                                   unsigned hardbits, bool single_chunk, float &l2acc)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -1094,6 +1043,13 @@ __device__ __forceinline__ unsigned finish_forward(const Globals &g, const Smem 
             o = SH ? make_float4(C1[0], C1[1], C1[2], 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         reinterpret_cast<float4 *>(g.out)[pix] = o;
+        if (g.l2_target) {
+            // the L2 loss's gradient 2 (out - target) and its sum of squares
+            const float4 t = __ldg(reinterpret_cast<const float4 *>(g.l2_target) + pix);
+            const float dx = o.x - t.x, dy = o.y - t.y, dz = o.z - t.z, dw = o.w - t.w;
+            reinterpret_cast<float4 *>(g.l2_grad)[pix] = make_float4(2.f * dx, 2.f * dy, 2.f * dz, 2.f * dw);
+            l2acc += dx * dx + dy * dy + dz * dz + dw * dw;
+        }
     }
     return layers;
 }
@@ -1449,6 +1405,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
             reinterpret_cast<ulonglong2 *>(kbuf)[i] = make_ulonglong2(EMPTY, EMPTY);
     bool single_chunk = false;
     unsigned n_pairs = 0, n_exact = 0, n_cand = 0, n_layers = 0;
+    float l2acc = 0.f;   // the fused L2 loss: this thread's sum of squares
     int batch = 0;   // candidate-queue batches so far (selects the queue counter)
     if (!from_ids) {
         const long long lb = g.tile_off[t], le = g.tile_off[t + 1];
@@ -1736,10 +1693,15 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
         if constexpr (MODE == 1)
             n_layers += adjoint_warp<K, TT>(g, S, V, M, X0, Y0, p, rho, in, ids);
         else if constexpr (BWD)
-            n_layers += finish_pixel<K, true, TT, EXTRA>(g, S, V, M, X0, Y0, lx, ly, rho, ids, hardbits, single_chunk,
-                                                         glacc);
+            n_layers += adjoint_pixel<K, TT, EXTRA>(g, S, V, M, X0, Y0, lx, ly, rho, ids, glacc);
         else
-            n_layers += finish_forward<K, TT, EXTRA>(g, S, V, M, X0, Y0, p, rho, in, ids, hardbits, single_chunk);
+            n_layers += finish_forward<K, TT, EXTRA>(g, S, V, M, X0, Y0, p, rho, in, ids, hardbits, single_chunk, l2acc);
+    }
+    if (!BWD && g.l2_loss) {
+        // this tile's share of the fused L2 loss: warp sums, one atomic per warp
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l2acc += __shfl_xor_sync(0xffffffffu, l2acc, o);
+        if ((tid & 31) == 0 && l2acc != 0.f) atomicAdd(g.l2_loss, l2acc);
     }
     if (light_grad) {
         // this tile's dL/dlight: warp sums, one atomic per warp and component

@@ -228,7 +228,12 @@ class Renderer:
         return dict(choice)
 
     def forward(self, store_layers: bool = True, out: Optional[torch.Tensor] = None,
-                ids: Optional[torch.Tensor] = None, pos=None, col=None, tex=None):
+                ids: Optional[torch.Tensor] = None, pos=None, col=None, tex=None,
+                target: Optional[torch.Tensor] = None, grad: Optional[torch.Tensor] = None,
+                loss: Optional[torch.Tensor] = None):
+        """Renders ``out [n_pix, 4]`` (and the layer ids with ``store_layers``).  With
+        ``target`` the L2 loss is fused in: ``grad`` receives 2 (out - target) and
+        ``loss`` (if given) accumulates sum (out - target)^2; returns (out, ids, grad)."""
         dev = self.scene.device
         if out is None:
             out = torch.empty(self.n_pix, 4, dtype=torch.float32, device=dev)
@@ -239,6 +244,19 @@ class Renderer:
         sc = self.scene.c_struct(pos, col, tex)
         key = self._setup_key(pos)
         old = self._begin_setup()
+        if target is not None:
+            target = target.contiguous()
+            if grad is None:
+                grad = torch.empty_like(out)
+            code = self.lib.dressi_forward_l2(C.byref(sc), self.views, self.n_views, C.byref(self.params),
+                                              target.data_ptr(), out.data_ptr(), grad.data_ptr(),
+                                              loss.data_ptr() if loss is not None else None,
+                                              ids.data_ptr() if ids is not None else None, self.n_pix,
+                                              self.ws.data_ptr(), self.ws_bytes, self.status.data_ptr(),
+                                              self._stream())
+            B.check(code, "dressi_forward_l2")
+            self._end_setup(old, key, True)
+            return out, ids, grad
         code = self.lib.dressi_forward(C.byref(sc), self.views, self.n_views, C.byref(self.params), out.data_ptr(),
                                        ids.data_ptr() if ids is not None else None, self.n_pix, self.ws.data_ptr(),
                                        self.ws_bytes, self.status.data_ptr(), self._stream())
