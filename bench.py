@@ -166,9 +166,10 @@ def reference_arm(args, rank, world):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
-def algorithmic_bytes(scene, K, backward, store_layers=True):
+def algorithmic_bytes(scene, K, backward, store_layers=True, fused_loss=True):
     """Bytes one launch of the per-tile kernel must move at minimum:
-    forward: RGBA out 16 B (+ K layer ids 4 B when stored) per pixel; per view the vertex
+    forward: RGBA out 16 B (+ K layer ids 4 B when stored) per pixel, with the fused L2
+    loss also the target read and dL/dout written (2 x 16 B); per view the vertex
     records (32 B) and faces (12 B) of its mesh; every texture once (texel bytes).
     adjoint: dL/dI 16 B (+ K ids 4 B when stored) per pixel; per view vertex records,
     faces and the screen-gradient accumulators (16 B read + 16 B written per vertex);
@@ -180,7 +181,7 @@ def algorithmic_bytes(scene, K, backward, store_layers=True):
     texels = sum(m.tex.shape[0] * m.tex.shape[1] for m in scene.meshes if m.tex is not None)
     ids = 4 * K if store_layers else 0
     if not backward:
-        return px * (16 + ids) + per_view + tex_bytes
+        return px * (16 + ids + (32 if fused_loss else 0)) + per_view + tex_bytes
     acc = sum(32 * scene.meshes[v.mesh].pos.shape[0] for v in scene.views)
     return px * (16 + ids) + per_view + acc + tex_bytes + 2 * 16 * texels
 
