@@ -1780,6 +1780,8 @@ constexpr size_t tile_smem_bytes()
 // shared memory per SM, 1 KB of it reserved per CTA
 static_assert(4 * (tile_smem_bytes<3, 0, 16>() + 1024) <= 228 * 1024, "K = 3 forward tiles no longer fit four CTAs per SM");
 static_assert(4 * (tile_smem_bytes<3, 0, 32>() + 1024) <= 228 * 1024, "K = 3, 32 px forward tiles no longer fit four CTAs per SM");
+static_assert(4 * (tile_smem_bytes<3, 2, 32>() + 1024) <= 228 * 1024,
+              "K = 3 adjoint from stored ids no longer fits four CTAs per SM");
 
 template <int K, int MODE, int TT>
 static void launch_kk(const Globals &g, cudaStream_t s)
