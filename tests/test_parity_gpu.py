@@ -86,8 +86,11 @@ def test_fp16_texture_error_against_fp32_oracle():
     assert worst > 1e-6   # the storage rounding is visible: the comparison is not vacuous
 
 
+@pytest.mark.parametrize("store_layers", [True, False])
 @pytest.mark.parametrize("tile", [16, 32])
-def test_ragged_multi_mesh_multi_view(tile):
+def test_ragged_multi_mesh_multi_view(tile, store_layers):
+    """Meshes and views of uneven sizes (tiles cut by the image edge), from stored layer ids
+    and re-rasterizing."""
     g = synth.rng(3)
     meshes, views = [], []
     for m, (sl, st_, res) in enumerate([(12, 7, 40), (30, 17, 96), (8, 5, 23)]):
@@ -102,7 +105,7 @@ def test_ragged_multi_mesh_multi_view(tile):
         views.append(synth.View(synth.camera_mvp(2.8 * d, res, res), m, res, res))
     views.append(synth.View(synth.camera_mvp((0, 0, 3), 50, 31), 1, 50, 31))
     s = synth.Scene("ragged", meshes, views, synth.soft_params_px(64, shade_mode=2))
-    compare_scene(s, tile=tile)
+    compare_scene(s, tile=tile, store_layers=store_layers)
 
 
 @pytest.mark.parametrize("tile", [16, 32])
