@@ -83,7 +83,7 @@ def test_workspace_size_host_only(lib):
 
 
 @pytest.mark.parametrize("bad", ["K0", "K6", "sigma0", "edge3", "shade_tex_missing", "mesh_idx", "pix_off", "tile",
-                                 "rho_too_big", "nan_mvp", "schedule"])
+                                 "rho_too_big", "nan_mvp", "schedule", "reuse2"])
 def test_invalid_arguments_rejected_on_host(lib, bad):
     sc, keep = _scene()
     v = _views(1)
@@ -111,6 +111,8 @@ def test_invalid_arguments_rejected_on_host(lib, bad):
         v[0].mvp[3] = float("nan")
     elif bad == "schedule":
         p.schedule = 3
+    elif bad == "reuse2":
+        p.reuse_setup = 2
     if bad != "pix_off":   # the image size is only known to the passes
         assert lib.dressi_workspace_size(C.byref(sc), v, 1, C.byref(p)) == 0
     # the entry points reject before touching the device
@@ -119,6 +121,21 @@ def test_invalid_arguments_rejected_on_host(lib, bad):
     code = lib.dressi_backward(C.byref(sc), v, 1, C.byref(p), 0x1000, None, n_pix, 0x1000, None, None, 0x1000,
                                1 << 40, 0x1000, None)
     assert code == B.DRESSI_ERR_ARG
+
+
+def test_fused_loss_arguments_rejected_on_host(lib):
+    """dressi_forward_l2 wants a target and a gradient buffer, 16-byte aligned like the
+    image; it rejects them before touching the device."""
+    sc, keep = _scene()
+    v = _views(1)
+    p = B.DressiParams(3, 0.01, 0.01 / 7, 0.01, 0.0, 0, 0, 0, 0, 0, 0)
+    n = lib.dressi_workspace_size(C.byref(sc), v, 1, C.byref(p))
+    args = dict(target=0x1000, out=0x1000, grad=0x2000)
+    for key, bad in (("target", None), ("grad", None), ("target", 0x1004), ("grad", 0x2008), ("out", 0x1002)):
+        a = dict(args, **{key: bad})
+        code = lib.dressi_forward_l2(C.byref(sc), v, 1, C.byref(p), a["target"], a["out"], a["grad"], None, None,
+                                     64 * 48, 0x1000, n, 0x1000, None)
+        assert code == B.DRESSI_ERR_ARG, (key, bad)
 
 
 def test_workspace_too_small_rejected(lib):
