@@ -146,6 +146,11 @@ class Renderer:
         self.params.reuse_setup = 0
         return (t.data_ptr(), t._version, bytes(self.params), self.ws.data_ptr())
 
+    def _setup_reusable(self, key, have_ids: bool) -> bool:
+        """Whether the workspace holds the setup for ``key``, with the tile lists when
+        the backward re-rasterizes (no stored layer ids)."""
+        return self._setup is not None and self._setup[0] == key and (have_ids or self._setup[1])
+
     def _begin_setup(self):
         """Before a call that rebuilds the setup: the workspace holds nothing
         reusable until it returns."""
@@ -307,8 +312,7 @@ class Renderer:
         gm = torch.empty(self.n_views, 16, dtype=torch.float32, device=dev) if camera else None
         gl = torch.empty(self.n_views, 3, dtype=torch.float32, device=dev) if camera else None
         key = self._setup_key(pos)
-        reuse = (reuse_setup is not False and self._setup is not None and self._setup[0] == key
-                 and (ids is not None or self._setup[1]))
+        reuse = reuse_setup is not False and self._setup_reusable(key, ids is not None)
         self.params.reuse_setup = 1 if reuse else 0
         old = self._setup if reuse else self._begin_setup()
         code = self.lib.dressi_backward_ex(C.byref(sc), self.views, self.n_views, C.byref(self.params),
