@@ -47,7 +47,7 @@ def masks(o, params, view):
     return ~unstable, ~(unstable | sh_bad)
 
 
-class GpuRun:
+class CudaPath:
     def __init__(self, scene, device="cuda", list_cap=0, tile=0):
         self.scene = scene
         self.ps = PackedScene(scene.meshes, device)
@@ -123,7 +123,7 @@ def compare_scene(scene, windows=None, seed=0, grad_from_target=None, store_laye
                   check_grads=True, report=None, tile=0, camera=False):
     """Runs both paths on every view (restricted to ``windows``) and asserts parity.
     Returns a dict of the measured errors."""
-    gpu = GpuRun(scene, list_cap=list_cap, tile=tile)
+    gpu = CudaPath(scene, list_cap=list_cap, tile=tile)
     gpu.forward(store_layers=store_layers)
     rng = np.random.default_rng(seed)
     stats = dict(ids_checked=0, ids_unstable=0, fwd_err=0.0, fwd_checked=0)

@@ -5,7 +5,7 @@ import torch
 
 import oracle
 import synth
-from parity import GpuRun, compare_scene, masks, rel_l2
+from parity import CudaPath, compare_scene, masks, rel_l2
 from scenes_small import grid_mesh, pixel_mesh, pixel_scene
 
 pytestmark = pytest.mark.gpu
@@ -74,7 +74,7 @@ def test_fp16_texture_error_against_fp32_oracle():
     s32 = synth.config5(subdiv=4, n_views=2, res=128, tex_side=256, tex_dtype=np.float32)
     s16 = synth.config5(subdiv=4, n_views=2, res=128, tex_side=256, tex_dtype=np.float16)
     np.testing.assert_array_equal(s16.meshes[0].tex, s32.meshes[0].tex.astype(np.float16))
-    gpu = GpuRun(s16)
+    gpu = CudaPath(s16)
     gpu.forward()
     worst = 0.0
     for i, v in enumerate(s32.views):
@@ -111,9 +111,9 @@ def test_ragged_multi_mesh_multi_view(tile, store_layers):
 @pytest.mark.parametrize("tile", [16, 32])
 def test_tile_list_overflow_falls_back_exactly(tile):
     s = synth.config1()
-    full = GpuRun(s, tile=tile)
+    full = CudaPath(s, tile=tile)
     out_a, _ = full.forward()
-    tiny = GpuRun(s, list_cap=16, tile=tile)
+    tiny = CudaPath(s, list_cap=16, tile=tile)
     out_b, _ = tiny.forward()
     assert tiny.status() & 1
     assert torch.equal(out_a, out_b)
@@ -126,7 +126,7 @@ def test_face_index_out_of_range_is_skipped():
     f = s.meshes[0].faces.copy()
     f[7] = (0, 1, 10 ** 6)
     s.meshes[0].faces = f
-    gpu = GpuRun(s)
+    gpu = CudaPath(s)
     gpu.forward()
     assert gpu.status() & 2
     o = oracle.render(s.meshes[0], s.views[0], s.params)
@@ -141,7 +141,7 @@ def test_nonfinite_vertex_skips_its_faces():
     p = s.meshes[0].pos.copy()
     p[5, 1] = np.nan
     s.meshes[0].pos = p
-    gpu = GpuRun(s)
+    gpu = CudaPath(s)
     gpu.forward()
     assert gpu.status() & 4
     o = oracle.render(s.meshes[0], s.views[0], s.params)
@@ -155,7 +155,7 @@ def test_empty_view_renders_nothing():
     s = synth.config1()
     m = s.meshes[0]
     s.meshes = [synth.Mesh(m.pos + np.float32(100.0), m.faces, col=m.col)]
-    gpu = GpuRun(s)
+    gpu = CudaPath(s)
     out, ids = gpu.forward()
     assert torch.count_nonzero(out) == 0
     assert (ids == -1).all()
@@ -170,7 +170,7 @@ def test_exact_fill_rule_on_gpu():
     V, F = grid_mesh(9, W, H)
     V = np.round(V)
     s = pixel_scene(pixel_mesh(V, F, W, H), W, H, K=2, r=1 / 64, sigma=0.3 / 64, delta=1 / 64)
-    gpu = GpuRun(s)
+    gpu = CudaPath(s)
     gpu.forward()
     o = oracle.render(s.meshes[0], s.views[0], s.params)
     assert (gpu.view_ids(0)[0] == o["ids"][0]).all()      # the owning face, everywhere
@@ -182,7 +182,7 @@ def test_exact_fill_rule_on_gpu():
 
 def test_store_and_recompute_backward_agree():
     s = synth.config2()
-    gpu = GpuRun(s)
+    gpu = CudaPath(s)
     gpu.forward(store_layers=True)
     g = [np.random.default_rng(1).normal(size=(256, 256, 4))]
     a = gpu.backward(g, use_ids=True)
@@ -221,9 +221,9 @@ def test_autotune_choice_gives_identical_images(tmp_path):
     tolerance (vertex normals are summed with float atomics, so Lambert images of two
     runs may differ in the last bits); the choice is cached."""
     s = synth.config2()
-    ref = GpuRun(s)
+    ref = CudaPath(s)
     out_a, ids_a = ref.forward()
-    tuned = GpuRun(s)
+    tuned = CudaPath(s)
     cache = str(tmp_path / "tune.json")
     ch = tuned.r.autotune(cache_path=cache)
     assert ch["tile"] in (16, 32) and ch["schedule"] in (1, 2) and ch["list_cap"] > 0 and ch["ms"] > 0
@@ -231,7 +231,7 @@ def test_autotune_choice_gives_identical_images(tmp_path):
     assert tuned.status() == 0
     assert torch.equal(ids_a, ids_b)
     assert (out_a - out_b).abs().max().item() <= 1e-5
-    again = GpuRun(s)
+    again = CudaPath(s)
     assert again.r.autotune(cache_path=cache) == ch   # served from the cache
 
 
@@ -246,13 +246,13 @@ def test_texel_gather_mode_matches_oracle(store_layers):
 def test_texel_gather_is_bitwise_reproducible_and_agrees_with_atomics():
     s = synth.config2(texgrad_mode=1)
     g = [np.random.default_rng(4).normal(size=(256, 256, 4))]
-    a = GpuRun(s)
+    a = CudaPath(s)
     a.forward()
     t1 = a.backward(g)[0][2]
     t2 = a.backward(g)[0][2]
     np.testing.assert_array_equal(t1, t2)            # no atomics: identical bits every run
     s0 = synth.config2(texgrad_mode=0)
-    b = GpuRun(s0)
+    b = CudaPath(s0)
     b.forward()
     t0 = b.backward(g)[0][2]
     assert rel_l2(t1, t0) < 1e-6
