@@ -136,13 +136,15 @@ typedef struct {
                            centre for the inverse-UV lookup; the paper draws a Sobol point per
                            frame (the caller supplies it; [-0.5, 0.5)^2 keeps it in the pixel) */
     int32_t reuse_setup; /* dressi_backward(_ex) only: 1 = the workspace still holds what the
-                            last dressi_forward on it built for the same scene (positions
-                            unchanged), views and params -- vertex transform, face table,
-                            normals and, for layer_ids == NULL, the tile lists -- and the
-                            backward takes it instead of rebuilding it (with layer_ids == NULL
-                            it still re-rasterizes: layers and barycentrics are recomputed).
-                            0 = rebuild.  The caller guarantees the precondition; a workspace
-                            written by another call since gives wrong gradients. */
+                            last forward call on it (dressi_forward, dressi_forward_l2, or
+                            dressi_forward_from_layers, which builds no tile lists) built for
+                            the same scene (positions unchanged), views and params -- vertex
+                            transform, face table, normals and, for layer_ids == NULL, the
+                            tile lists -- and the backward takes it instead of rebuilding it
+                            (with layer_ids == NULL it still re-rasterizes: layers and
+                            barycentrics are recomputed).  0 = rebuild.  The caller
+                            guarantees the precondition; a workspace written by another call
+                            since gives wrong gradients. */
 } dressi_params;
 
 /* Size in bytes of the workspace that dressi_forward / dressi_backward need for
