@@ -1,10 +1,11 @@
 // dressi_tile.cuh -- the per-tile hot kernel of HardSoftRas, forward and adjoint
-// (included by one translation unit per mode: dressi_tile_fwd.cu, _bwd.cu, _ids.cu).
+// (included by one translation unit per mode: dressi_tile_fwd.cu, _bwd.cu, _ids.cu,
+// _cached.cu, _extra_ids.cu, _extra_bwd.cu, _nmap_fwd.cu, _nmap_cached.cu).
 //
 // One CTA owns one TT x TT pixel tile of one view (TT = 16 or 32; 256 threads).  Per CTA:
 //   1. the tile's face list is staged in shared memory, CH faces at a time, from the
 //      per-(view, face) record table, with tile-local edge equations for a cheap
-//      conservative pretest;
+//      conservative pretest; the next round's records are prefetched into L2;
 //   2. every (face, pixel) pair of the faces' r-grown bounding boxes is enumerated
 //      (pair -> face through a per-32-pair table); pairs passing the pretest and the
 //      key lower bound are queued, and the queue gets the exact SignedDist, hard test
@@ -13,12 +14,14 @@
 //   3. the hard stencil S^H of a ring of rho pixels around the tile is built from the
 //      same staged faces (hard test only), so the edge mask E of every tile pixel is
 //      known without a second pass over the image;
-//   4. forward: each layer is re-evaluated, shaded (perspective-correct
-//      interpolation, bilinear texture, Lambert) and blended (D_k = sigmoid(dist/sigma),
-//      colour and silhouette equations of Sec. 3.4.3); adjoint: the same values are
-//      rebuilt and dL/dI is pushed back to the screen-space corners, vertex colours,
-//      vertex normals and texels.
-// With layer ids stored by the forward (mode 2), the adjoint skips steps 1-3: S^H of
+//   4. forward: each warp re-evaluates and shades (perspective-correct interpolation,
+//      bilinear texture, Lambert or normal map) the layers its pixels blend as one list,
+//      and each pixel blends them (D_k = sigmoid(dist/sigma), colour and silhouette
+//      equations of Sec. 3.4.3), optionally with the L2 loss; adjoint: the same values are
+//      rebuilt, by warp lists (re-rasterizing) or a CTA-wide layer queue (stored ids), and
+//      dL/dI is pushed back to the screen-space corners, vertex colours, vertex normals,
+//      texels, the camera and the light.
+// With layer ids stored by the forward (modes 2, 3, 4, 7), steps 1-3 are skipped: S^H of
 // the tile and its ring is the stored front layer's hard flag.
 #pragma once
 #include "dressi_core.cuh"
