@@ -699,12 +699,14 @@ __device__ __forceinline__ void inv_uv_write(const Globals &g, const ViewK &V, c
 struct Smem {
     // every mode
     int view, totals[2], next;
-    int qn[2];           // queue fill of the current batch, by batch parity
+    int qn[2];           // queue fill of the current batch, by batch parity (the stored-ids
+                         // adjoint: its layer ring's items queued / taken)
     unsigned long long m0[HS_MAX], m1[HS_MAX];   // per halo row: columns with S^H = 0 / 1
     unsigned char sh[HS_MAX * HS_MAX];
     // the raster (forward and re-rasterizing adjoint) only: the modes from stored layer
-    // ids are launched with the shared memory up to F, leaving the rest of the SM's
-    // unified L1 / shared storage to the L1 cache
+    // ids are launched with the shared memory up to F (the stored-ids adjoint adds its
+    // layer queues there, adj_smem_bytes), leaving the rest of the SM's unified L1 / shared storage
+    // to the L1 cache
     FaceRec F[CH];
     Pre P[CH];
     int rect[CH];        // tile pairs: x0 | y0 << 8 | w << 16 | h << 24 (tile-local, x0/y0 >= 0)
