@@ -39,6 +39,13 @@
  * and the reverse-mode adjoint of 8-16 back to positions, colours, texels.
  * Distances handed to sigmoid and Shift are in normalised screen units:
  * pixel distance / max(W, H).
+ *
+ * Parity unpinned (the paper fixes no value for them, so no pin can): the width rule
+ * of E (rho = max(1, round(delta max(W, H))) pixels, a Chebyshev window), perspective-
+ * correct rather than screen-linear barycentrics, the colour blend's normalisation by
+ * the sum of D_k, and Enlarge read as dist >= -r instead of the paper's grown polygons.
+ * These steps follow the readings above; everything else is pinned by closed forms,
+ * brute force, a ray-cast renderer and finite differences in the tests.
  */
 #include <math.h>
 #include <stdint.h>
