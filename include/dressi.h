@@ -78,7 +78,7 @@ typedef struct {
     int64_t vert_off;     /* first vertex in the packed vertex planes */
     int64_t face_off;     /* first face in the packed face array */
     int64_t tex_off;      /* first texel in the packed texture buffer (ignored without texture) */
-    int32_t tex_w, tex_h; /* texture size in texels (0 without texture) */
+    int32_t tex_w, tex_h; /* texture size in texels (0 without texture); tex_w * tex_h < 2^31 */
 } dressi_mesh;
 
 /* Packed ragged scene.  The struct and `meshes` live in HOST memory; the data

@@ -99,6 +99,7 @@ static bool make_plan(const dressi_scene *sc, const dressi_view *views, int n_vi
         k.tex_h = dm.tex_h;
         if (textured) {
             if (dm.tex_w <= 0 || dm.tex_h <= 0 || dm.tex_off < 0) return false;
+            if ((long long)dm.tex_w * dm.tex_h > 0x7fffffffLL) return false;   // texel counts are int32
             P.n_texels = std::max(P.n_texels, (long long)dm.tex_off + (long long)dm.tex_w * dm.tex_h);
             P.max_texels = std::max(P.max_texels, dm.tex_w * dm.tex_h);
         }

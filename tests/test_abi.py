@@ -123,6 +123,16 @@ def test_invalid_arguments_rejected_on_host(lib, bad):
     assert code == B.DRESSI_ERR_ARG
 
 
+def test_texture_with_too_many_texels_rejected(lib):
+    """Texel counts are int32 on the device: a texture of 2^31 texels or more is refused."""
+    sc, meshes = _scene(tex=True)
+    v = _views(1)
+    p = B.DressiParams(3, 0.01, 0.01 / 7, 0.01, 0.0, 0, 1, 0, 0, 0, 0)
+    assert lib.dressi_workspace_size(C.byref(sc), v, 1, C.byref(p)) > 0
+    meshes[0].tex_w, meshes[0].tex_h = 65536, 32768
+    assert lib.dressi_workspace_size(C.byref(sc), v, 1, C.byref(p)) == 0
+
+
 def test_fused_loss_arguments_rejected_on_host(lib):
     """dressi_forward_l2 wants a target and a gradient buffer, 16-byte aligned like the
     image; it rejects them before touching the device."""
