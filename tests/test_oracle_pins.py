@@ -560,3 +560,103 @@ def test_brute_force_equals_bbox(cfg):
     b = oracle.render(s.meshes[0], s.views[0], s.params, window=win, brute_force=True)
     for k in ("rgba", "ids", "hard", "dist", "key", "sh", "edge", "margin_hard", "margin_cand", "n_hard"):
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+# ----------------------------------------------------------------------------
+# K >= 2 blend (Sec. 3.4.3): I_c^e = sum D_k C_k / sum D_k, I_s^e = 1 - prod (1 - D_k)
+# ----------------------------------------------------------------------------
+
+def _blend_scene(K):
+    """Three nested right triangles with legs on the pixel axes (w = 1, constant depths,
+    one uniform colour per face, so C_k is the face colour whatever the barycentrics):
+    id 0 red at depth 0.6, id 1 blue at depth 0.3, id 2 green at depth 0.45."""
+    W = H = 32
+    V = [(2, 2), (30, 2), (2, 30), (6, 6), (30, 6), (6, 30), (4, 4), (30, 4), (4, 30)]
+    z = [0.6] * 3 + [0.3] * 3 + [0.45] * 3
+    col = [(1, 0, 0)] * 3 + [(0, 0, 1)] * 3 + [(0, 1, 0)] * 3
+    return pixel_scene(pixel_mesh(V, [(0, 1, 2), (3, 4, 5), (6, 7, 8)], W, H, z=z, col=col), W, H, K=K,
+                       r=8 / 32, sigma=4 / 32, delta=8 / 32, edge_mode=1)
+
+
+# per pixel: (face id, signed pixel distance) in Shift order, distances read off the
+# geometry by hand (legs x = a, y = a and hypotenuse x + y = 32 + a of the face at a)
+_BLEND_PIXELS = {
+    # (10.5, 10.5): inside all three; nearest feature of each face is a leg
+    (10, 10): [(1, 4.5), (2, 6.5), (0, (32 - 21) / math.sqrt(2))],
+    # (4.5, 10.5): inside faces 2 (leg x = 4 at 0.5 px) and 0 (leg x = 2 at 2.5 px); face 1
+    # is soft, 1.5 px left of its leg x = 6 (foot (6, 10.5) inside the leg)
+    (4, 10): [(2, 0.5), (0, 2.5), (1, -1.5)],
+    # (1.5, 1.5): outside all three; each nearest feature is the corner (a, a)
+    (1, 1): [(0, -math.sqrt(0.5)), (2, -2.5 * math.sqrt(2)), (1, -4.5 * math.sqrt(2))],
+}
+_BLEND_COLOUR = {0: (1.0, 0.0, 0.0), 1: (0.0, 0.0, 1.0), 2: (0.0, 1.0, 0.0)}
+
+
+@pytest.mark.parametrize("K", [2, 3])
+def test_multi_layer_blend_equations(K):
+    """With E = 1 the pixel is the D-weighted mean of its K layers' colours and the
+    silhouette is 1 - prod_k (1 - D_k), D_k = sigmoid(d_k / sigma) (the colour and
+    silhouette blend equations of Sec. 3.4.3), from hand-computed distances; with
+    K = 2 the farthest of the three layers is dropped."""
+    s = _blend_scene(K)
+    r = _render(s)
+    sig_px = 4.0
+    for (x, y), layers in _BLEND_PIXELS.items():
+        kept = layers[:K]
+        assert [int(i) for i in r["ids"][:, y, x]] == [i for i, _ in kept]
+        D = np.array([1.0 / (1.0 + math.exp(-d / sig_px)) for _, d in kept])
+        C = np.array([_BLEND_COLOUR[i] for i, _ in kept])
+        rgb = (D[:, None] * C).sum(0) / D.sum()
+        alpha = 1.0 - np.prod(1.0 - D)
+        np.testing.assert_allclose(r["rgba"][y, x, :3], rgb, rtol=0, atol=1e-12)
+        assert r["rgba"][y, x, 3] == pytest.approx(alpha, abs=1e-12)
+        np.testing.assert_allclose(r["dist"][:K, y, x] * 32, [d for _, d in kept], atol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# culling (reading: a face with a corner at w <= 1e-6 or depth outside [0, 1] is dropped)
+# ----------------------------------------------------------------------------
+
+def _cull_scene(bad_corner, mvp):
+    """A quad of two faces (ids 0, 1) over the whole image at depth 1/2 and, in front of
+    it, face 2 whose first corner is ``bad_corner`` = (x, y, z) in object space (the other
+    two corners are ordinary)."""
+    W = H = 24
+    pos = np.array([[-1.2, -1.2, 1.0], [1.2, -1.2, 1.0], [1.2, 1.2, 1.0], [-1.2, 1.2, 1.0],
+                    bad_corner, [0.6, -0.5, 1.0], [-0.3, 0.7, 1.0]], np.float32)
+    faces = np.array([[0, 1, 2], [0, 2, 3], [4, 5, 6]], np.int32)
+    col = synth.rng(4).random((7, 3)).astype(np.float32)
+    mesh = synth.Mesh(pos, faces, col=col)
+    view = synth.View(np.asarray(mvp, np.float32).reshape(16), 0, W, H)
+    return synth.Scene("cull", [mesh], [view], synth.Params(K=3, r=2 / 24, sigma=1 / 24, delta=2 / 24))
+
+
+# clip = (x, y, z_depth, w): depth from the z row; the w row either 1 (depth = the z row)
+# or the object z (so w follows the corner's z while depth stays 1/2 wherever w != 0)
+_MVP_DEPTH = [[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0.5, 0], [0, 0, 0, 1]]
+_MVP_W = [[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0.5, 0], [0, 0, 1, 0]]
+
+
+@pytest.mark.parametrize("mvp,bad,kept", [
+    (_MVP_DEPTH, (-0.5, -0.4, 2.5), False),    # depth 1.25 > 1
+    (_MVP_DEPTH, (-0.5, -0.4, -0.5), False),   # depth -0.25 < 0
+    (_MVP_DEPTH, (-0.5, -0.4, 2.0), True),     # depth exactly 1: kept
+    (_MVP_DEPTH, (-0.5, -0.4, 0.0), True),     # depth exactly 0: kept
+    (_MVP_W, (-0.5, -0.4, -0.5), False),       # w = -0.5 (depth 1/2)
+    (_MVP_W, (-0.5, -0.4, 1e-7), False),       # 0 < w <= 1e-6 (depth 1/2)
+    (_MVP_W, (-0.5, -0.4, 0.5), True),         # w = 1/2: kept
+])
+def test_culling_near_and_far(mvp, bad, kept):
+    """A culled face is absent from every layer and the other faces' layers, keys and
+    image are exactly those of the scene without it; a face at the limits is kept."""
+    s = _cull_scene(bad, mvp)
+    r = _render(s)
+    m = s.meshes[0]
+    without = synth.Scene("cull2", [synth.Mesh(m.pos, m.faces[:2], col=m.col)], s.views, s.params)
+    r2 = _render(without)
+    if kept:
+        assert (r["ids"] == 2).any()
+        return
+    assert not (r["ids"] == 2).any()
+    for k in ("ids", "hard", "key", "rgba", "dist", "sh", "edge"):
+        np.testing.assert_array_equal(r[k], r2[k], err_msg=k)
