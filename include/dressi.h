@@ -149,7 +149,8 @@ typedef struct {
 
 /* Size in bytes of the workspace that dressi_forward / dressi_backward need for
    this scene, view set and parameters (host-only computation; views is a host
-   array).  Returns 0 on invalid arguments. */
+   array).  Returns 0 on invalid arguments, among them a packed texel count of
+   2^32 - 1 or more with texgrad_mode 1 (the gather sorts 32-bit texel keys). */
 DRESSI_API size_t dressi_workspace_size(const dressi_scene *scene, const dressi_view *views, int32_t n_views,
                              const dressi_params *params);
 
@@ -246,7 +247,9 @@ DRESSI_API int dressi_backward_ex(const dressi_scene *scene, const dressi_view *
      - Scenes whose dressi_workspace_size() exceeds DRESSI_STATIC_SCRATCH_BYTES are
        rejected with DRESSI_ERR_WORKSPACE before anything is enqueued.
      - The first call on a device looks up the array's device address on the current
-       device (once per device); make that first call before any stream capture.
+       device (once per device); make that first call before any stream capture.  The
+       address stays cached for the life of the process: after a cudaDeviceReset of that
+       device this entry point must not be called again.
      - The library allocates nothing here (no cudaMalloc / cudaFree); the counters the
        pass needs zeroed are cleared on `stream` at every call.
      - All calls on a device share the one array, which keeps the last call's
@@ -307,6 +310,14 @@ DRESSI_API int dressi_set_stats_buffer(void *dev_counters);
    -1 -- into this DEVICE int32 [sum texels] buffer.  NULL disables.  Process-wide
    setting, not thread safe. */
 DRESSI_API int dressi_set_inverse_uv_buffer(int32_t *dev_buffer);
+
+/* Inspection hook of the persistent schedule (no counterpart in the paper): when set,
+   each pass with schedule 2 that builds tile lists copies the order in which its CTAs
+   take the tiles (global tile numbers, views' tiles counted in view order, row-major
+   inside a view) into dev_order and each tile's face-list length (indexed by tile)
+   into dev_lengths (DEVICE int32 [total tiles] each, either may be NULL).  NULL, NULL
+   disables.  Process-wide setting, not thread safe. */
+DRESSI_API int dressi_set_tile_order_buffer(int32_t *dev_order, int32_t *dev_lengths);
 
 /* Number of kernels this library has launched since it was loaded (process-wide). */
 DRESSI_API unsigned long long dressi_launch_count(void);

@@ -78,6 +78,7 @@ SIGNATURES = {
     "dressi_launch_count": (C.c_ulonglong, []),
     "dressi_set_stats_buffer": (C.c_int, [C.c_void_p]),
     "dressi_set_inverse_uv_buffer": (C.c_int, [C.c_void_p]),
+    "dressi_set_tile_order_buffer": (C.c_int, [C.c_void_p, C.c_void_p]),
 }
 
 _lock = threading.Lock()

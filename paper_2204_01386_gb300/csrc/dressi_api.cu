@@ -27,6 +27,8 @@ static cudaEvent_t g_prof[4] = {nullptr, nullptr, nullptr, nullptr};
 // optional device work counters of the per-tile kernel (statistics hook)
 static unsigned long long *g_stats = nullptr;
 static int *g_inv_uv_out = nullptr;
+// optional copies of the persistent schedule's tile order and the tiles' face-list lengths
+static int *g_order_out = nullptr, *g_lengths_out = nullptr;
 
 // pass: 0 forward, 1 adjoint, 2 forward from stored layer ids (timed as a forward)
 static void launch_tile_profiled(const Globals &g, int pass, cudaStream_t s)
@@ -186,6 +188,9 @@ static bool make_plan(const dressi_scene *sc, const dressi_view *views, int n_vi
     L.tile_order = o; o = align_up(o + sizeof(int) * (size_t)std::max(tiles, 1));
     L.lpt_hist = o; o = align_up(o + sizeof(int) * LPT_BINS);
     L.tg_slots = (p->texgrad_mode != 0 && textured) ? view_pixels * p->K : 0;
+    // the texel gather sorts 32-bit texel keys with 0xffffffff marking an empty slot: every
+    // packed texel index must stay below it
+    if (p->texgrad_mode == 1 && textured && P.n_texels >= 0xffffffffLL) return false;
     // the inverse UV stores sample numbers as int32 (atomicMax)
     if (p->texgrad_mode == 2 && L.tg_slots > 0x7fffffffLL) return false;
     L.inv_uv = o; o = align_up(o + sizeof(int) * (size_t)((p->texgrad_mode == 2 && textured) ? std::max<long long>(P.n_texels, 1) : 1));
@@ -320,6 +325,9 @@ static void run_tiles(Globals &g, const Plan &P, char *ws, bool bins_built, int 
             cudaMemsetAsync(ws + P.lay.lpt_hist, 0, sizeof(int) * LPT_BINS, s);
             g.tile_order = reinterpret_cast<const int *>(ws + P.lay.tile_order);
             launch_lpt_order(g, s);
+            const size_t n = sizeof(int) * (size_t)P.lay.total_tiles;
+            if (g_order_out) cudaMemcpyAsync(g_order_out, g.tile_order, n, cudaMemcpyDeviceToDevice, s);
+            if (g_lengths_out) cudaMemcpyAsync(g_lengths_out, g.tile_count, n, cudaMemcpyDeviceToDevice, s);
         }
     }
     launch_tile_profiled(g, pass, s);
@@ -337,15 +345,24 @@ constexpr int MAX_DEVICES = 64;
 static void *g_static_scratch_addr[MAX_DEVICES] = {};
 static std::mutex g_static_scratch_mu;
 
-// device address of g_static_scratch on the current device, or nullptr on failure
+// device address of g_static_scratch on the current device, or nullptr on failure (the
+// CUDA error of a failed lookup is cleared, so it does not surface in the caller's next
+// CUDA call).  The address is cached per device ordinal: a cudaDeviceReset in the caller's
+// process invalidates it (documented in dressi.h).
 static void *static_scratch_address()
 {
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return nullptr;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+        cudaGetLastError();
+        return nullptr;
+    }
     std::lock_guard<std::mutex> lock(g_static_scratch_mu);
     if (!g_static_scratch_addr[dev]) {
         void *ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) return nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return nullptr;
+        }
         g_static_scratch_addr[dev] = ptr;
     }
     return g_static_scratch_addr[dev];
@@ -373,6 +390,13 @@ unsigned long long dressi_launch_count(void) { return g_launches.load(); }
 int dressi_set_inverse_uv_buffer(int32_t *dev_buffer)
 {
     g_inv_uv_out = dev_buffer;
+    return DRESSI_OK;
+}
+
+int dressi_set_tile_order_buffer(int32_t *dev_order, int32_t *dev_lengths)
+{
+    g_order_out = dev_order;
+    g_lengths_out = dev_lengths;
     return DRESSI_OK;
 }
 

@@ -28,6 +28,8 @@
 #include "dressi_launch.h"
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 
 namespace dressi {
 
@@ -1788,23 +1790,39 @@ static_assert(4 * (tile_smem_bytes<3, 0, 32>() + 1024) <= 228 * 1024, "K = 3, 32
 static_assert(4 * (tile_smem_bytes<3, 2, 32>() + 1024) <= 228 * 1024,
               "K = 3 adjoint from stored ids no longer fits four CTAs per SM");
 
+constexpr int LAUNCH_MAX_DEVICES = 64;
+
 template <int K, int MODE, int TT>
 static void launch_kk(const Globals &g, cudaStream_t s)
 {
-    // per process: the attributes are per function, the SM count per device
-    static bool configured = false;
-    static int per_sm = 1, sms = 1;
+    // per device (the caller's current one): the shared-memory attribute above 48 KB is a
+    // property of the function in each device's context, and the persistent grid follows
+    // that device's SM count and occupancy.  Devices past LAUNCH_MAX_DEVICES are configured
+    // on every launch.
+    static std::atomic<bool> ready[LAUNCH_MAX_DEVICES];
+    static int per_sm_of[LAUNCH_MAX_DEVICES], sms_of[LAUNCH_MAX_DEVICES];
+    static std::mutex mu;
     const size_t smem = tile_smem_bytes<K, MODE, TT>();
-    if (!configured) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    const bool cached = dev >= 0 && dev < LAUNCH_MAX_DEVICES;
+    int per_sm = 1, sms = 1;
+    if (cached && ready[dev].load(std::memory_order_acquire)) {
+        per_sm = per_sm_of[dev];
+        sms = sms_of[dev];
+    } else {
+        std::lock_guard<std::mutex> lock(mu);
         cudaFuncSetAttribute(k_tile<K, MODE, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_tile_persistent<K, MODE, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev < 0 ? 0 : dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_persistent<K, MODE, TT>, NT, smem);
         if (per_sm < 1) per_sm = 1;
         if (sms < 1) sms = 1;
-        configured = true;
+        if (cached) {
+            per_sm_of[dev] = per_sm;
+            sms_of[dev] = sms;
+            ready[dev].store(true, std::memory_order_release);
+        }
     }
     if (g.persistent) {
         const int grid = std::min(g.total_tiles, per_sm * sms);

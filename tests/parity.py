@@ -48,10 +48,14 @@ def masks(o, params, view):
 
 
 class CudaPath:
-    def __init__(self, scene, device="cuda", list_cap=0, tile=0):
+    """The CUDA path of one scene; ``tile`` (16, 32; 0 = library default) and ``schedule``
+    (1 one CTA per tile, 2 persistent CTAs over the longest-first tile order; 0 = library
+    default) choose the per-tile kernel that runs."""
+
+    def __init__(self, scene, device="cuda", list_cap=0, tile=0, schedule=0):
         self.scene = scene
         self.ps = PackedScene(scene.meshes, device)
-        self.r = Renderer(self.ps, scene.views, scene.params, list_cap=list_cap, tile=tile)
+        self.r = Renderer(self.ps, scene.views, scene.params, list_cap=list_cap, tile=tile, schedule=schedule)
 
     def forward(self, store_layers=True):
         # layer ids are always kept here so they can be compared; whether the
@@ -120,10 +124,10 @@ def window_of(view, win):
 
 
 def compare_scene(scene, windows=None, seed=0, grad_from_target=None, store_layers=True, list_cap=0,
-                  check_grads=True, report=None, tile=0, camera=False):
+                  check_grads=True, report=None, tile=0, camera=False, schedule=0):
     """Runs both paths on every view (restricted to ``windows``) and asserts parity.
     Returns a dict of the measured errors."""
-    gpu = CudaPath(scene, list_cap=list_cap, tile=tile)
+    gpu = CudaPath(scene, list_cap=list_cap, tile=tile, schedule=schedule)
     gpu.forward(store_layers=store_layers)
     rng = np.random.default_rng(seed)
     stats = dict(ids_checked=0, ids_unstable=0, fwd_err=0.0, fwd_checked=0)

@@ -133,6 +133,25 @@ def test_texture_with_too_many_texels_rejected(lib):
     assert lib.dressi_workspace_size(C.byref(sc), v, 1, C.byref(p)) == 0
 
 
+def test_texel_gather_refuses_texel_indices_past_32_bits(lib):
+    """The texel gather (texgrad_mode 1) sorts 32-bit texel keys, 0xffffffff marking an
+    empty slot: a packed texel buffer of 2^32 - 1 texels or more is refused for it, while
+    the atomics mode (64-bit texel offsets) takes it."""
+    sc, meshes = _scene(tex=True)
+    v = _views(1)
+    p = B.DressiParams(3, 0.01, 0.01 / 7, 0.01, 0.0, 0, 1, 1, 0, 0, 0)
+    assert lib.dressi_workspace_size(C.byref(sc), v, 1, C.byref(p)) > 0
+    for off, ok in ((2 ** 32 - 18, True), (2 ** 32 - 17, False), (2 ** 32 - 8, False), (2 ** 40, False)):
+        meshes[0].tex_off = off           # 16 texels: the last index is off + 15
+        assert (lib.dressi_workspace_size(C.byref(sc), v, 1, C.byref(p)) > 0) == ok, off
+        code = lib.dressi_backward(C.byref(sc), v, 1, C.byref(p), 0x1000, None, 64 * 48, 0x1000, None, 0x1000,
+                                   0x1000, 0 if ok else 1 << 40, 0x1000, None)
+        assert code == (B.DRESSI_ERR_WORKSPACE if ok else B.DRESSI_ERR_ARG), off
+        p.texgrad_mode = 0
+        assert lib.dressi_workspace_size(C.byref(sc), v, 1, C.byref(p)) > 0, off
+        p.texgrad_mode = 1
+
+
 def test_fused_loss_arguments_rejected_on_host(lib):
     """dressi_forward_l2 wants a target and a gradient buffer, 16-byte aligned like the
     image; it rejects them before touching the device."""

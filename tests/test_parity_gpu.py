@@ -37,12 +37,14 @@ def test_config2_textured_lambert(store_layers, tile):
     assert st["ids_checked"] > 60000
 
 
+@pytest.mark.parametrize("schedule", [1, 2])
 @pytest.mark.parametrize("K", [1, 2, 4, 5])
 @pytest.mark.parametrize("edge_mode", [0, 1, 2])
-def test_layers_and_edge_modes(K, edge_mode):
+def test_layers_and_edge_modes(K, edge_mode, schedule):
     s = synth.config1()
     s.params = synth.Params(K=K, r=3 / 64, sigma=3 / 64 / 7, delta=2 / 64, edge_mode=edge_mode, shade_mode=0)
-    compare_scene(s, seed=K * 10 + edge_mode, tile=32 if K % 2 else 16)
+    compare_scene(s, seed=K * 10 + edge_mode, tile=32 if K % 2 else 16, schedule=schedule,
+                  store_layers=(K + edge_mode) % 2 == 0)
 
 
 @pytest.mark.parametrize("shade_mode", [1, 2])
@@ -86,9 +88,10 @@ def test_fp16_texture_error_against_fp32_oracle():
     assert worst > 1e-6   # the storage rounding is visible: the comparison is not vacuous
 
 
+@pytest.mark.parametrize("schedule", [1, 2])
 @pytest.mark.parametrize("store_layers", [True, False])
 @pytest.mark.parametrize("tile", [16, 32])
-def test_ragged_multi_mesh_multi_view(tile, store_layers):
+def test_ragged_multi_mesh_multi_view(tile, store_layers, schedule):
     """Meshes and views of uneven sizes (tiles cut by the image edge), from stored layer ids
     and re-rasterizing."""
     g = synth.rng(3)
@@ -105,7 +108,7 @@ def test_ragged_multi_mesh_multi_view(tile, store_layers):
         views.append(synth.View(synth.camera_mvp(2.8 * d, res, res), m, res, res))
     views.append(synth.View(synth.camera_mvp((0, 0, 3), 50, 31), 1, 50, 31))
     s = synth.Scene("ragged", meshes, views, synth.soft_params_px(64, shade_mode=2))
-    compare_scene(s, tile=tile, store_layers=store_layers)
+    compare_scene(s, tile=tile, store_layers=store_layers, schedule=schedule)
 
 
 @pytest.mark.parametrize("tile", [16, 32])
@@ -192,27 +195,120 @@ def test_store_and_recompute_backward_agree():
             assert rel_l2(x, y) < 1e-6
 
 
-@pytest.mark.parametrize("views", [[0, 37]])
-def test_config3_full_size_sampled(views):
-    """64 views x 512^2, 20,480 tris, 1024^2 texture, run in full on the GPU;
-    checked on 48 x 48 crops of two views (gradients with dL/dI zero elsewhere)."""
+# crops of the 512^2 views of the multi-view workload: the interior, the left and right
+# silhouette, the top-left corner and the bottom border (whole tiles up to the image edge)
+_C3_CROPS = {0: (232, 200, 48, 48), 37: (20, 232, 40, 48), 12: (0, 0, 40, 40), 50: (452, 210, 60, 40),
+             63: (200, 464, 48, 48)}
+
+
+@pytest.mark.parametrize("store_layers", [True, False])
+@pytest.mark.parametrize("tile,schedule", [(16, 1), (16, 2), (32, 1), (32, 2)])
+def test_config3_full_size_sampled(tile, schedule, store_layers):
+    """64 views x 512^2, 20,480 tris, 1024^2 texture, run in full on the GPU (with the
+    persistent longest-first schedule every CTA takes about 27 tiles in turn); checked on
+    crops of five views (gradients with dL/dI zero elsewhere)."""
     s = synth.config3()
+    # views outside the sample get zero-size windows (no pixels compared, zero gradient)
+    wins = [_C3_CROPS.get(i, (0, 0, 0, 0)) for i in range(len(s.views))]
+    st = compare_scene(s, windows=wins, tile=tile, schedule=schedule, store_layers=store_layers)
+    assert st["ids_checked"] > 4000
+
+
+@pytest.mark.parametrize("tile,schedule", [(32, 2), (16, 1)])
+def test_config3_cut_tiles_at_the_image_edge(tile, schedule):
+    """The multi-view workload at 500^2 (500 = 15 x 32 + 20 = 31 x 16 + 4): the last tile
+    column and row are cut by the image edge; crops on both cut borders and their corner."""
+    s = synth.config3(n_views=16, res=500)
+    crops = {3: (452, 226, 48, 40), 9: (226, 456, 40, 44), 14: (440, 440, 60, 60)}
+    wins = [crops.get(i, (0, 0, 0, 0)) for i in range(len(s.views))]
+    compare_scene(s, windows=wins, tile=tile, schedule=schedule, store_layers=schedule == 1)
+
+
+@pytest.mark.parametrize("tile,schedule", [(16, 1), (16, 2), (32, 1), (32, 2)])
+def test_config5_full_size_crop(tile, schedule):
+    """1.31M tris, 4096^2 FP16 texture, 8 views at 2048^2, recompute backward;
+    checked on a 64 x 64 crop of view 0 and one across the silhouette of view 5."""
+    s = synth.config5()
+    wins = [(0, 0, 0, 0)] * len(s.views)
+    wins[0] = (992, 1000, 64, 64)
+    wins[5] = (150, 1000, 64, 64)
+    st = compare_scene(s, windows=wins, store_layers=False, tile=tile, schedule=schedule)
+    assert st["ids_checked"] > 5000
+
+
+@pytest.mark.parametrize("tile,schedule", [(32, 2), (16, 1)])
+def test_config4_sampled(tile, schedule):
+    """The full ragged batch (32 meshes of 1k..200k tris, 128^2..1024^2 views, 512^2..2048^2
+    textures) in one call; checked against the oracle on the views of the four smallest
+    meshes in full and on a 64 x 64 crop of every other view (seeded position within the
+    middle half of the view, so crops straddle silhouettes; the two largest meshes' crops
+    are centred)."""
+    s = synth.config4()
+    nf = [int(m.faces.shape[0]) for m in s.meshes]
+    order = np.argsort(nf)
+    g = np.random.default_rng(44)
     wins = []
     for i, v in enumerate(s.views):
-        wins.append((232, 200, 48, 48) if i in views else (0, 0, 0, 0))
-    # views outside the sample get zero-size windows (no pixels compared, zero gradient)
-    st = compare_scene(s, windows=wins)
-    assert st["ids_checked"] > 2000
+        if v.mesh in order[:4]:
+            wins.append(None)
+        elif v.mesh in order[-2:]:
+            wins.append((v.width // 2 - 32, v.height // 2 - 32, 64, 64))
+        else:
+            x0 = int(g.integers(v.width // 4 - 32, 3 * v.width // 4 - 32 + 1))
+            y0 = int(g.integers(v.height // 4 - 32, 3 * v.height // 4 - 32 + 1))
+            wins.append((max(0, x0), max(0, y0), 64, 64))
+    st = compare_scene(s, windows=wins, tile=tile, schedule=schedule)
+    assert st["ids_checked"] > 500000
 
 
-@pytest.mark.parametrize("tile", [16, 32])
-def test_config5_full_size_crop(tile):
-    """1.31M tris, 4096^2 FP16 texture, 8 views at 2048^2, recompute backward;
-    checked on a 64 x 64 crop of one view."""
-    s = synth.config5()
-    wins = [(992, 1000, 64, 64)] + [(0, 0, 0, 0)] * (len(s.views) - 1)
-    st = compare_scene(s, windows=wins, store_layers=False, tile=tile)
-    assert st["ids_checked"] > 3000
+def test_persistent_schedule_equals_one_cta_per_tile():
+    """Two hundred 64^2 views of the icosphere (3,200 tiles of 16 px, several per persistent
+    CTA): the persistent longest-first kernel stores the same layer ids and image bit for
+    bit as one CTA per tile (no state of one tile leaks into the next, no tile is lost or
+    taken twice), and the adjoints agree up to the order of the float atomics."""
+    base = synth.config1()
+    g = np.random.default_rng(8)
+    views = []
+    for i in range(200):
+        d = g.normal(size=3)
+        views.append(synth.View(synth.camera_mvp(3.0 * d / np.linalg.norm(d), 64, 64), 0, 64, 64))
+    s = synth.Scene("many", base.meshes, views, base.params)
+    a, b = CudaPath(s, tile=16, schedule=1), CudaPath(s, tile=16, schedule=2)
+    out_a, ids_a = a.forward()
+    out_b, ids_b = b.forward()
+    assert torch.equal(ids_a, ids_b)
+    assert torch.equal(out_a, out_b)
+    grads = [np.random.default_rng(i).normal(size=(64, 64, 4)) for i in range(len(views))]
+    for use_ids in (True, False):
+        ga, gb = a.backward(grads, use_ids=use_ids)[0], b.backward(grads, use_ids=use_ids)[0]
+        for x, y in zip(ga, gb):
+            if x is not None:
+                assert rel_l2(x, y) < 1e-6
+    assert a.status() == 0 and b.status() == 0
+
+
+def test_longest_first_order_is_a_permutation():
+    """The persistent schedule's tile order (inspection hook): every tile exactly once,
+    face-list lengths non-increasing (in the order's 1,024 length buckets)."""
+    from paper_2204_01386_gb300 import binding as B
+    import ctypes as C
+    s = synth.config3(n_views=8)
+    gpu = CudaPath(s, tile=32, schedule=2)
+    n_tiles = sum(((v.width + 31) // 32) * ((v.height + 31) // 32) for v in s.views)
+    order = torch.full((n_tiles,), -1, dtype=torch.int32, device="cuda")
+    lengths = torch.full((n_tiles,), -1, dtype=torch.int32, device="cuda")
+    lib = B.load()
+    lib.dressi_set_tile_order_buffer(C.c_void_p(order.data_ptr()), C.c_void_p(lengths.data_ptr()))
+    try:
+        gpu.forward()
+    finally:
+        lib.dressi_set_tile_order_buffer(None, None)
+    o = order.cpu().numpy()
+    ln = lengths.cpu().numpy()
+    assert sorted(o.tolist()) == list(range(n_tiles))
+    assert (ln >= 0).all() and ln.max() > 0
+    bucket = np.minimum(ln[o], 1023)
+    assert (np.diff(bucket) <= 0).all()
 
 
 def test_autotune_choice_gives_identical_images(tmp_path):

@@ -49,13 +49,15 @@ def _forward_static(lib, sc, views, nv, prm, n_pix, K, dev):
 def test_static_scratch_forward_matches_workspace_forward():
     lib = B.load()
     dev = torch.device("cuda", 0)
-    # textured Lambert scene, then the vertex-colour scene, then the textured one again:
-    # every call must give the workspace path's result whatever the array held before
-    scenes = [synth.config2(), synth.config1(), synth.config2()]
-    for s in scenes:
+    # textured Lambert scene, then the vertex-colour scene, then the textured one with
+    # 32 px tiles and the persistent longest-first schedule (tile counts, queue head and
+    # the tile order live in the array), then the first again: every call must give the
+    # workspace path's result whatever the array held before
+    scenes = [(synth.config2(), 0, 0), (synth.config1(), 0, 0), (synth.config2(), 32, 2), (synth.config2(), 0, 0)]
+    for s, tile, schedule in scenes:
         ps = PackedScene(s.meshes, dev)
         views, n_pix = make_views(s.views)
-        prm = make_params(s.params)
+        prm = make_params(s.params, tile=tile, schedule=schedule)
         sc = ps.c_struct()
         K = s.params.K
         ref_out, ref_ids, ref_st, ws_bytes = _forward_with_workspace(lib, sc, views, len(s.views), prm, n_pix, K, dev)
