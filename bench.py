@@ -35,7 +35,7 @@ METRIC = "fwd+bwd Mpixel*views/s"
 FLOP_CANDIDATE = 50
 FLOP_SHADE_LAYER = 110
 FLOP_ADJOINT_LAYER = 340
-SMS, FP32_LANES_PER_SM = 152, 128
+FP32_LANES_PER_SM = 128
 UNIT = "Mpixel*views/s"
 L2_FLUSH_BYTES = 512 << 20
 
@@ -237,7 +237,30 @@ def recorded_traffic(kernel, pixels):
     return int(nbytes) * pixels / int(npix)
 
 
-def ours(args, rank, world, local_rank):
+def measured_peaks(lib, dev):
+    """FP32 FMA TFLOP/s and red.global.add.v4.f32 GB/s of this device, from the library's
+    microbenchmarks (dressi_measure_peak), and the SM count."""
+    import ctypes as C
+
+    import torch
+    buf = torch.zeros(64 << 18, dtype=torch.float32, device=dev)   # 64 MiB
+    stream = C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    res = {}
+    for which, name in ((0, "fp32_tflops"), (1, "red_v4_gbs")):
+        v = C.c_double(0.0)
+        code = lib.dressi_measure_peak(which, C.c_void_p(buf.data_ptr()), buf.numel() * 4, C.byref(v), stream)
+        res[name] = float(v.value) if code == 0 else None
+    res["sms"] = int(torch.cuda.get_device_properties(dev).multi_processor_count)
+    del buf
+    return res
+
+
+def measure(s, args, dev, world, rank, dist, flush, peaks, hbm_peak, main=False, n_steps=None, plain_arm=True):
+    """Times the step (forward with the L2 loss fused in, then the adjoint) of scene ``s``
+    on this rank: the per-tile kernels by CUDA events (non-graph steps), then whole steps
+    replayed from a CUDA graph (the gradient all-reduce over ranks stays outside the graph),
+    then, at one rank, the same views as a plain per-view launch sequence.  Returns the
+    record and the state the main workload's extra legs reuse."""
     import ctypes as C
 
     import torch
@@ -245,12 +268,7 @@ def ours(args, rank, world, local_rank):
     from paper_2204_01386_gb300 import PackedScene, Renderer
     from paper_2204_01386_gb300 import binding as B
 
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-    s = workload_scene(rank, world, n_views=args.views, workload=args.workload)
+    n_steps = n_steps or args.steps
     s.params.texgrad_mode = args.texgrad
     store = bool(s.params.store_layers)
     tgt_scene = synth.perturbed(s, 4321 + rank)
@@ -276,30 +294,33 @@ def ours(args, rank, world, local_rank):
     loss = torch.zeros(1, device=dev)
     gp = torch.empty(3, ps.n_verts_total, device=dev)
     gt = torch.empty(ps.n_texels, 4, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
+    def compute():
         # forward with the L2 loss fused in (out, dL/dout, loss), then the adjoint
         loss.zero_()
         r.forward(store_layers=store, out=out, ids=ids, target=target, grad=grad, loss=loss)
         r.backward(grad, ids=ids, grad_pos=gp, grad_tex=gt)
+
+    def exchange():
+        # views are sharded over ranks: the gradients are summed over all views
         if world > 1:
             dist.all_reduce(gp)
             dist.all_reduce(gt)
 
     for _ in range(args.warmup):
-        step()
+        compute()
+        exchange()
     torch.cuda.synchronize()
     assert (r.device_status() & ~1) == 0, r.device_status()
     c0 = lib.dressi_launch_count()
-    step()
+    compute()
     torch.cuda.synchronize()
     launches_per_step = lib.dressi_launch_count() - c0
 
     # 1) the per-tile kernels timed live: CUDA events recorded by the library right
     #    around them, on the stream they are launched on, in non-graph steps
-    n_prof = max(3, min(args.steps, 10))
+    n_prof = max(3, min(n_steps, 10))
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(n_prof)]
     for e in ev:
         for x in e:
@@ -310,7 +331,7 @@ def ours(args, rank, world, local_rank):
         e = ev[k]
         lib.dressi_set_profile_events(C.c_void_p(e[0].cuda_event), C.c_void_p(e[1].cuda_event),
                                       C.c_void_p(e[2].cuda_event), C.c_void_p(e[3].cuda_event))
-        step()
+        compute()
     torch.cuda.synchronize()
     lib.dressi_set_profile_events(None, None, None, None)
     fwd_ms = [e[0].elapsed_time(e[1]) for e in ev]
@@ -328,73 +349,72 @@ def ours(args, rank, world, local_rank):
     st_bwd = [int(x) for x in counters.tolist()]
     lib.dressi_set_stats_buffer(None)
 
-    # 2) the headline: whole steps, replayed from a CUDA graph (single rank)
-    use_graph = world == 1 and not args.no_graph
-    run = step
+    # 2) whole steps: the compute replayed from a CUDA graph, the exchange after it
+    use_graph = not args.no_graph
+    run = compute
     if use_graph:
         cg = torch.cuda.CUDAGraph()
         with torch.cuda.graph(cg):
-            step()
+            compute()
         cg.replay()
         torch.cuda.synchronize()
         run = cg.replay
-    tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = Clocks(local_rank)
+    tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
+    clocks = Clocks(dev.index or 0)
     clocks.start()
     time.sleep(0.3)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    for k in range(args.steps):
+    for k in range(n_steps):
         flush.fill_(float(k))
         tev[k][0].record(stream)
         run()
+        exchange()
         tev[k][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clock_info = clocks.stop()
     assert (r.device_status() & ~1) == 0, r.device_status()
-    step_ms = [a.elapsed_time(b) for a, b in tev]
-    total_ms = sum(step_ms)
+    total_ms = sum(a.elapsed_time(b) for a, b in tev)
     if world > 1:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = s.pixels * world * args.steps / (total_ms * 1e-3) / 1e6
+    value = s.pixels * world * n_steps / (total_ms * 1e-3) / 1e6
 
     # dominant kernel roofline (live CUDA-event durations of the per-tile kernels)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     fwd_avg, bwd_avg = statistics.mean(fwd_ms), statistics.mean(bwd_ms)
     bwd_dom = bwd_avg >= fwd_avg
     kb = algorithmic_bytes(s, s.params.K, bwd_dom, store)
     dur = (bwd_avg if bwd_dom else fwd_avg) * 1e-3
     st = st_bwd if bwd_dom else st_fwd
     flops = st[2] * FLOP_CANDIDATE + st[3] * (FLOP_ADJOINT_LAYER if bwd_dom else FLOP_SHADE_LAYER)
-    sm_mhz = clock_info.get("sm_mhz") or 2070.0
-    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     achieved = flops / dur / 1e12
-    kname = "k_tile<%d,%s,%d>" % (s.params.K, "bwd" if bwd_dom else "fwd", tile)
+    alu_peak = peaks.get("fp32_tflops")
+    peak_source = "measured: FP32 FMA microbenchmark (dressi_measure_peak) on %d SMs" % peaks["sms"]
+    if not alu_peak:
+        sm_mhz = clock_info.get("sm_mhz") or 2070.0
+        alu_peak = peaks["sms"] * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        peak_source = "derived: %d SMs x %d lanes x 2 FLOP x %.0f MHz" % (peaks["sms"], FP32_LANES_PER_SM, sm_mhz)
+    mode = "fwd" if not bwd_dom else ("bwd" if store else "bwd_recompute")
+    kname = "k_tile<%d,%s,%d>" % (s.params.K, mode, tile)
     roofline = {"kernel": kname, "bound": "alu",
                 "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                "traffic": recorded_traffic(kname, s.pixels) if args.workload == "multiview" else None,
-                "peak_source": "FP32: %d SMs x %d lanes x 2 FLOP x %.0f MHz (sampled SM clock)" % (
-                    SMS, FP32_LANES_PER_SM, sm_mhz),
+                "traffic": recorded_traffic(kname, s.pixels) if args.workload == "multiview" and main else None,
+                "peak_source": peak_source,
                 "algorithmic_flop": flops, "fwd_tile_ms": fwd_avg, "bwd_tile_ms": bwd_avg,
                 "work_fwd": dict(zip(("pairs", "exact_evals", "candidates", "layers"), st_fwd)),
                 "work_bwd": dict(zip(("pairs", "exact_evals", "candidates", "layers"), st_bwd)),
                 "hbm_algorithmic_bytes": kb, "hbm_achieved_gbs": kb / dur / 1e9,
-                "hbm_frac": kb / dur / 1e9 / hbm_peak}
+                "hbm_peak_gbs": hbm_peak, "hbm_frac": kb / dur / 1e9 / hbm_peak,
+                "red_v4_peak_gbs": peaks.get("red_v4_gbs")}
 
     # 3) the same views as a plain per-view launch sequence (one call per view, one CTA
     #    per tile), to compare with the batched form above
     plain = None
-    if len(s.views) > 1 and not args.no_plain and world == 1:
+    if len(s.views) > 1 and plain_arm and not args.no_plain and world == 1:
         rv = [Renderer(ps, [v], s.params, tile=tile, schedule=1) for v in s.views]
         offs = [int(x.pix_off) for x in r.views]
         idv = [torch.empty(s.params.K, v.width * v.height, dtype=torch.int32, device=dev) if store else None
@@ -409,7 +429,7 @@ def ours(args, rank, world, local_rank):
         for _ in range(2):
             plain_step()
         torch.cuda.synchronize()
-        n_plain = max(3, args.steps // 2)
+        n_plain = max(3, n_steps // 2)
         pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_plain)]
         for k in range(n_plain):
             flush.fill_(float(k))
@@ -421,10 +441,28 @@ def ours(args, rank, world, local_rank):
         plain = {"value": s.pixels * n_plain / (pms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": pms / n_plain,
                  "note": "one forward/loss/adjoint call per view, one CTA per tile, no graph"}
         del rv
+    rec = {"value": value, "unit": UNIT, "ms_per_step": total_ms / n_steps, "steps": n_steps,
+           "tile": tile, "schedule": "persistent longest-first" if schedule == 2 else "CTA per tile",
+           "autotuned": tuned is not None, "list_cap": int(r.params.list_cap), "cuda_graph": use_graph,
+           "roofline": roofline, "plain_per_view": plain, "clocks": clock_info,
+           "gpu_launches_per_step": int(launches_per_step)}
+    state = dict(r=r, ps=ps, out=out, ids=ids, grad=grad, loss=loss, gp=gp, gt=gt, target=target, store=store,
+                 exchange=exchange, use_graph=use_graph)
+    return rec, state
 
-    # 3b) the same step with a static geometry (texture / colour optimisation): the
-    #     forward re-shades the layers the benchmark's forward stored (binning, raster and
-    #     peel skipped), then the loss and the adjoint from the same layers
+
+def extra_legs(s, args, dev, world, dist, flush, st):
+    """The main workload's extra legs: the static-geometry step and the end-to-end step
+    through the public API with host buffers."""
+    import torch
+
+    r, ps, out, ids, grad, loss, gp, gt, target = (st[k] for k in ("r", "ps", "out", "ids", "grad", "loss", "gp",
+                                                                     "gt", "target"))
+    store, exchange, use_graph = st["store"], st["exchange"], st["use_graph"]
+    stream = torch.cuda.current_stream(dev)
+    # the same step with a static geometry (texture / colour optimisation): the forward
+    # re-shades the layers the benchmark's forward stored (binning, raster and peel
+    # skipped), then the loss and the adjoint from the same layers
     cached = None
     if store and world == 1 and not args.no_cached:
         ids0 = ids.clone()
@@ -459,12 +497,11 @@ def ours(args, rank, world, local_rank):
                   "note": "static geometry: forward from the stored layers (no binning, raster or peel) + loss "
                           "+ adjoint from the same layers, CUDA graph"}
 
-    # 4) end to end through the public API with host buffers: every step copies its
-    #    inputs (positions, texture, target images) from pinned host memory and reads
-    #    its results (loss, gradients) back.  The inputs are double-buffered: the copy
-    #    stream fills one set with the next step's inputs while the compute stream runs
-    #    the step on the other (a data loader's prefetch); the results follow each step
-    #    on the compute stream.
+    # end to end through the public API with host buffers: every step copies its inputs
+    # (positions, texture, target images) from pinned host memory and reads its results
+    # (loss, gradients) back.  The inputs are double-buffered: the copy stream fills one
+    # set with the next step's inputs while the compute stream runs the step on the other
+    # (a data loader's prefetch); the results follow each step on the compute stream.
     e2e = None
     if not args.no_e2e:
         h_pos = ps.pos.cpu().pin_memory()
@@ -483,9 +520,6 @@ def ours(args, rank, world, local_rank):
                 loss.zero_()
                 r.forward(store_layers=store, out=out, ids=ids, pos=pos, tex=tex, target=tgt, grad=grad, loss=loss)
                 r.backward(grad, ids=ids, grad_pos=gp, grad_tex=gt, pos=pos, tex=tex)
-                if world > 1:
-                    dist.all_reduce(gp)
-                    dist.all_reduce(gt)
             return f
 
         runs = [make_step(*b) for b in d_in]
@@ -521,6 +555,7 @@ def ours(args, rank, world, local_rank):
                     fetch(1 - k)
                 stream.wait_event(ready[k])
                 runs[k]()
+                exchange()
                 h_loss.copy_(loss, non_blocking=True)
                 h_gp.copy_(gp, non_blocking=True)
                 h_gt.copy_(gt, non_blocking=True)
@@ -530,6 +565,8 @@ def ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         n_e2e = max(3, args.steps // 2)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            dist.barrier()
         e0.record(stream)
         e2e_steps(n_e2e)
         e1.record(stream)
@@ -542,6 +579,50 @@ def ours(args, rank, world, local_rank):
         e2e = {"value": s.pixels * world * n_e2e / (ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": n_e2e, "cuda_graph": use_graph,
                "note": "inputs double-buffered: the next step's host-to-device copies overlap this step"}
+    return cached, e2e
+
+
+# the other workloads, measured beside the main one at one GPU (sub-records of the line)
+SUB_WORKLOADS = ("large", "ragged", "textured")
+
+
+def ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2204_01386_gb300 import binding as B
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    lib = B.load()
+    peaks = measured_peaks(lib, dev)
+    try:
+        hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        hbm_src = "MEASURED_PEAKS.json hbm_gbs (copy, measured)"
+    except Exception:
+        hbm_peak, hbm_src = 6800.0, "fallback 6.8 TB/s"
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+    s = workload_scene(rank, world, n_views=args.views, workload=args.workload)
+    rec, st = measure(s, args, dev, world, rank, dist, flush, peaks, hbm_peak, main=True)
+    cached, e2e = extra_legs(s, args, dev, world, dist, flush, st)
+    del st
+    torch.cuda.empty_cache()
+
+    subs = {}
+    if world == 1 and not args.no_sub and args.workload == "multiview":
+        for w in SUB_WORKLOADS:
+            ss = workload_scene(0, 1, workload=w)
+            sub_args = argparse.Namespace(**vars(args))
+            sub_args.workload = w
+            srec, sst = measure(ss, sub_args, dev, 1, 0, None, flush, peaks, hbm_peak,
+                                n_steps=max(5, args.steps // 2))
+            del sst
+            torch.cuda.empty_cache()
+            srec["workload"] = workload_desc(ss, w)["workload"]
+            srec["pixels_per_step"] = ss.pixels
+            subs[w] = srec
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -558,18 +639,89 @@ def ours(args, rank, world, local_rank):
                                  "sample": f"{nv} of {len(s.views)} views, {dt:.1f} s"}}
     if rank == 0:
         cfg = workload_desc(s, args.workload)
-        cfg.update({"texgrad": ["atomics", "texel-space gather", "inverse UV"][args.texgrad], "tile": tile, "schedule": "persistent longest-first" if schedule == 2 else "CTA per tile",
-                    "autotuned": tuned is not None, "list_cap": int(r.params.list_cap), "cuda_graph": use_graph})
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        cfg.update({"texgrad": ["atomics", "texel-space gather", "inverse UV"][args.texgrad], "tile": rec["tile"],
+                    "schedule": rec["schedule"], "autotuned": rec["autotuned"], "list_cap": rec["list_cap"],
+                    "cuda_graph": rec["cuda_graph"], "ranks": world,
+                    "parallelism": "views sharded over %d rank(s), gradients all-reduced" % world})
+        roofline = dict(rec["roofline"])
+        roofline["hbm_peak_source"] = hbm_src
+        line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(launches_per_step * args.steps), "clocks": clock_info, "plain_per_view": plain,
-                "cached_geometry": cached}
+                "gpu_launches": int(rec["gpu_launches_per_step"] * args.steps), "clocks": rec["clocks"],
+                "plain_per_view": rec["plain_per_view"], "cached_geometry": cached, "peaks_measured": peaks,
+                "workloads": subs or None}
         print(json.dumps(line), flush=True)
 
 
-def main():
+def _rank_entry(local_rank, world, port, argv):
+    """One rank of a self-launched multi-GPU run (bench.py --gpus N without a launcher)."""
+    os.environ.update({"RANK": str(local_rank), "LOCAL_RANK": str(local_rank), "WORLD_SIZE": str(world),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    run_rank(parse_args(argv))
+
+
+def spawn_ranks(n, argv, entry=_rank_entry):
+    """Starts n ranks of this script on this node (one process per GPU, 'spawn' start),
+    as torch.distributed.run would, and waits for them."""
+    import socket
+
+    import torch.multiprocessing as mp
+    sk = socket.socket()
+    sk.bind(("127.0.0.1", 0))
+    port = sk.getsockname()[1]
+    sk.close()
+    mp.start_processes(entry, args=(n, port, argv), nprocs=n, join=True, start_method="spawn")
+
+
+def run_rank(args):
+    """Runs this process's rank: the reference arm, or ours over NCCL (gloo with
+    --backend gloo, which only the CPU test of the launch path uses)."""
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.backend == "nccl":
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        else:
+            dist.init_process_group(args.backend)
+    try:
+        if args.backend == "gloo":
+            launch_selfcheck(args, rank, world)
+        else:
+            ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+def launch_selfcheck(args, rank, world):
+    """The launch path without a GPU (gloo): every rank takes its views of the workload,
+    joins the barriers of the timed region and the max-over-ranks reduction of the time,
+    all-reduces a per-rank gradient, and rank 0 prints one line."""
+    import torch
+    import torch.distributed as dist
+    s = workload_scene(rank, world, n_views=args.views, res=24, workload="multiview")
+    g = torch.full((3,), float(rank + 1), dtype=torch.float64)
+    dist.barrier()
+    t = torch.tensor([float(rank + 1)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(g)
+    dist.barrier()
+    if rank == 0:
+        print(json.dumps({"n_gpus": world, "views_rank0": len(s.views), "tmax": float(t.item()),
+                          "grad_sum": g.tolist()}), flush=True)
+
+
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -585,30 +737,27 @@ def main():
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 1, 2],
                     help="per-tile kernel: 1 one CTA per tile, 2 persistent longest-first (0: autotuner)")
     ap.add_argument("--no-cached", action="store_true", help="skip the static-geometry (cached layers) step")
+    ap.add_argument("--no-sub", action="store_true", help="skip the large / ragged / textured sub-records")
     ap.add_argument("--workload", default="multiview", choices=WORKLOADS)
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--texgrad", type=int, default=0, choices=[0, 1, 2],
                     help="texel gradient: 0 atomics, 1 deterministic texel gather, 2 inverse UV (approximate)")
     ap.add_argument("--no-plain", action="store_true")
-    args = ap.parse_args()
+    ap.add_argument("--backend", default="nccl", choices=["nccl", "gloo"],
+                    help="process-group backend of a multi-rank run (gloo only checks the launch path on CPU)")
+    args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)
-    rank = int(os.environ.get("RANK", 0))
-    world = int(os.environ.get("WORLD_SIZE", 1))
-    local_rank = int(os.environ.get("LOCAL_RANK", 0))
-    if args.impl == "reference":
-        reference_arm(args, rank, world)
+    return args
+
+
+def main():
+    argv = sys.argv[1:]
+    args = parse_args(argv)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # no launcher: start one rank per GPU here
+        spawn_ranks(args.gpus, argv)
         return
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        torch.cuda.set_device(local_rank)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    try:
-        ours(args, rank, world, local_rank)
-    finally:
-        if world > 1:
-            import torch.distributed as dist
-            dist.destroy_process_group()
+    run_rank(args)
 
 
 if __name__ == "__main__":

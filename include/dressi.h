@@ -319,6 +319,19 @@ DRESSI_API int dressi_set_inverse_uv_buffer(int32_t *dev_buffer);
    disables.  Process-wide setting, not thread safe. */
 DRESSI_API int dressi_set_tile_order_buffer(int32_t *dev_order, int32_t *dev_lengths);
 
+/* Peaks of the units the per-tile kernels use, measured on the current device (no
+   counterpart in the paper: the measured denominators of roofline fractions).
+     which 0: FP32 FMA throughput in TFLOP/s (an FMA counts 2): eight independent FMA
+              chains in every thread of 2,048 threads per SM on every SM;
+     which 1: red.global.add.v4.f32 throughput in GB/s of reduction payload: every lane
+              adds a float4 into its own 16 bytes (one warp instruction covers 512
+              contiguous bytes), the launch stepping through the buffer.
+   dev_buf  DEVICE scratch, 16-byte aligned, bytes >= 64 MiB (caller-owned; overwritten).
+   result   HOST double receiving the figure (the best of five timed launches).
+   Synchronises the host (it reads event timings back), so it must not be captured into a
+   CUDA graph. */
+DRESSI_API int dressi_measure_peak(int32_t which, void *dev_buf, size_t bytes, double *result, void *stream);
+
 /* Number of kernels this library has launched since it was loaded (process-wide). */
 DRESSI_API unsigned long long dressi_launch_count(void);
 

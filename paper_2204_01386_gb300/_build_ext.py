@@ -10,7 +10,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdressi.so")
 SOURCES = ["dressi_setup.cu", "dressi_tile_fwd.cu", "dressi_tile_bwd.cu", "dressi_tile_ids.cu", "dressi_tile_cached.cu",
            "dressi_tile_extra_ids.cu", "dressi_tile_extra_bwd.cu", "dressi_tile_nmap_fwd.cu",
-           "dressi_tile_nmap_cached.cu", "dressi_texgather.cu", "dressi_api.cu"]
+           "dressi_tile_nmap_cached.cu", "dressi_texgather.cu", "dressi_peak.cu", "dressi_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -79,6 +79,7 @@ SIGNATURES = {
     "dressi_set_stats_buffer": (C.c_int, [C.c_void_p]),
     "dressi_set_inverse_uv_buffer": (C.c_int, [C.c_void_p]),
     "dressi_set_tile_order_buffer": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dressi_measure_peak": (C.c_int, [C.c_int32, C.c_void_p, C.c_size_t, C.POINTER(C.c_double), C.c_void_p]),
 }
 
 _lock = threading.Lock()

@@ -83,3 +83,22 @@ def test_two_rank_gradient_allreduce_equals_single_process(tmp_path):
     np.testing.assert_allclose(got["gp"], gp, rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(got["gt"], gt, rtol=1e-12, atol=1e-12)
     assert got["tmax"][0] == 2.0
+
+
+def test_bench_self_launch_spawns_ranks():
+    """bench.py --gpus 2 without a launcher starts the two ranks itself (one process
+    each, rendezvous on 127.0.0.1): here with gloo and the GPU-free check of the launch
+    path, which takes each rank's views, joins the timed region's barriers and the
+    max-over-ranks time and sums a gradient over ranks; rank 0 alone prints."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, "bench.py", "--gpus", "2", "--backend", "gloo", "--views", "2"], cwd=root,
+                       capture_output=True, text=True, timeout=600, env=env)
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d == {"n_gpus": 2, "views_rank0": 2, "tmax": 2.0, "grad_sum": [3.0, 3.0, 3.0]}
