@@ -283,7 +283,9 @@ def test_persistent_schedule_equals_one_cta_per_tile():
         ga, gb = a.backward(grads, use_ids=use_ids)[0], b.backward(grads, use_ids=use_ids)[0]
         for x, y in zip(ga, gb):
             if x is not None:
-                assert rel_l2(x, y) < 1e-6
+                # 200 views of float atomics summed in another order differ by ~2e-6; one
+                # tile lost or taken twice moves the sum by orders of magnitude more
+                assert rel_l2(x, y) < 1e-5
     assert a.status() == 0 and b.status() == 0
 
 
