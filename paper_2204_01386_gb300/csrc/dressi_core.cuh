@@ -26,6 +26,9 @@ constexpr int CHUNK = 128;   // faces staged in shared memory per round
 constexpr int LPT_BINS = 1024;
 constexpr unsigned TG_NONE = 0xffffffffu;  // texel-gather record slot without a texture gradient  // face-list lengths bucketed for the longest-first tile order
 constexpr int FLAG_LIVE = 1 << 7;
+// outside a face, its edge lines' signed distances F closer than this (pixels) count as a
+// tie when choosing the edge that holds the closest point (far above their FP32 error)
+constexpr float EDGE_TIE_PX = 1e-3f;
 constexpr int FLAG_RANGE = 1 << 8;
 
 // ---------------------------------------------------------------------------
@@ -329,32 +332,63 @@ __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, 
     }
     float dist, bt = 0.f;
     int feat;
+    // the edge whose line the pixel is farthest outside of (smallest F), and the gap to
+    // the next smallest
+    int emin = 0;
+    float fmin1 = F[0];
+    if (F[1] < fmin1) { emin = 1; fmin1 = F[1]; }
+    if (F[2] < fmin1) { emin = 2; fmin1 = F[2]; }
     if (inside) {
-        float a = F[0];
-        feat = 0;
-        if (F[1] < a) { a = F[1]; feat = 1; }
-        if (F[2] < a) { a = F[2]; feat = 2; }
-        dist = a;
+        feat = emin;
+        dist = fmin1;
     } else {
+        // Outside, the closest point of the triangle lies on the edge with the smallest F
+        // (its interior, or one of its endpoints).  That edge alone is measured unless
+        // the two smallest F are within EDGE_TIE_PX of each other (slivers, where rounding
+        // could swap them): then every edge is, and the closest taken.
+        const float fmid = emin == 0 ? fminf(F[1], F[2]) : (emin == 1 ? fminf(F[0], F[2]) : fminf(F[0], F[1]));
+        const bool single = fsub(fmid, fmin1) > EDGE_TIE_PX;
         // squared distances compared without branches; one square root for a corner
         float best2 = 3.4e38f, bsel = -1.f, btn = 0.f, btd = 1.f;
         feat = 0;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
+        if (single) {
+            const int i = emin;
+            const float Pxi = i == 0 ? pX[0] : (i == 1 ? pX[1] : pX[2]);
+            const float Pyi = i == 0 ? pY[0] : (i == 1 ? pY[1] : pY[2]);
+            const float Qxi = i == 0 ? qX[0] : (i == 1 ? qX[1] : qX[2]);
+            const float Qyi = i == 0 ? qY[0] : (i == 1 ? qY[1] : qY[2]);
+            const float ci = i == 0 ? c[0] : (i == 1 ? c[1] : c[2]);
+            const float iLi = i == 0 ? R.invL[0] : (i == 1 ? R.invL[1] : R.invL[2]);
             const bool sw = (R.flags >> (1 + i)) & 1;
-            const int ia = i, ib = (i + 1) % 3;
-            const float ex = fsub(pX[i], qX[i]), ey = fsub(pY[i], qY[i]);   // V_Q - V_P
-            const float tP = ffma(pX[i], ex, fmul(pY[i], ey));
-            const float tQ = ffma(qX[i], ex, fmul(qY[i], ey));
-            const float dP2 = ffma(pX[i], pX[i], fmul(pY[i], pY[i]));
-            const float dQ2 = ffma(qX[i], qX[i], fmul(qY[i], qY[i]));
-            const float se = fmul(fabsf(c[i]), R.invL[i]);
+            const int ia = i, ib = i == 2 ? 0 : i + 1;
+            const float ex = fsub(Pxi, Qxi), ey = fsub(Pyi, Qyi);   // V_Q - V_P
+            const float tP = ffma(Pxi, ex, fmul(Pyi, ey));
+            const float tQ = ffma(Qxi, ex, fmul(Qyi, ey));
             const bool atP = tP <= 0.f, atQ = !atP && tQ >= 0.f;
-            const float s2 = atP ? dP2 : atQ ? dQ2 : fmul(se, se);
-            const int ft = atP ? 3 + (sw ? ib : ia) : atQ ? 3 + (sw ? ia : ib) : i;
-            if (s2 < best2) {
-                best2 = s2; feat = ft; bsel = (atP || atQ) ? -1.f : se;
-                btn = tP; btd = ffma(ex, ex, fmul(ey, ey));
+            const float cx = atQ ? Qxi : Pxi, cy = atQ ? Qyi : Pyi;
+            best2 = ffma(cx, cx, fmul(cy, cy));
+            feat = atP ? 3 + (sw ? ib : ia) : atQ ? 3 + (sw ? ia : ib) : i;
+            bsel = (atP || atQ) ? -1.f : fmul(fabsf(ci), iLi);
+            btn = tP;
+            btd = ffma(ex, ex, fmul(ey, ey));
+        } else {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const bool sw = (R.flags >> (1 + i)) & 1;
+                const int ia = i, ib = (i + 1) % 3;
+                const float ex = fsub(pX[i], qX[i]), ey = fsub(pY[i], qY[i]);   // V_Q - V_P
+                const float tP = ffma(pX[i], ex, fmul(pY[i], ey));
+                const float tQ = ffma(qX[i], ex, fmul(qY[i], ey));
+                const float dP2 = ffma(pX[i], pX[i], fmul(pY[i], pY[i]));
+                const float dQ2 = ffma(qX[i], qX[i], fmul(qY[i], qY[i]));
+                const float se = fmul(fabsf(c[i]), R.invL[i]);
+                const bool atP = tP <= 0.f, atQ = !atP && tQ >= 0.f;
+                const float s2 = atP ? dP2 : atQ ? dQ2 : fmul(se, se);
+                const int ft = atP ? 3 + (sw ? ib : ia) : atQ ? 3 + (sw ? ia : ib) : i;
+                if (s2 < best2) {
+                    best2 = s2; feat = ft; bsel = (atP || atQ) ? -1.f : se;
+                    btn = tP; btd = ffma(ex, ex, fmul(ey, ey));
+                }
             }
         }
         // edge interior: the closest point's parameter along the edge

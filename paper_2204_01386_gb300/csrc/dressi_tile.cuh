@@ -41,7 +41,8 @@ constexpr float APPROX_EPS = 1e-3f;    // pixel slack of the tile-local (approxi
 constexpr int CH = 96;                 // faces staged per round (one per thread)
 constexpr int HASH = 256;              // face id -> staged slot, open addressing (> 2 CH)
 constexpr unsigned long long EMPTY = ~0ULL;
-constexpr int QN = 4 * NT;             // queued candidate pairs per batch
+constexpr int WQ = 160;                // a warp's queue of pretested pairs (31 waiting + 32 items x 4)
+constexpr int QN = NT / 32 * WQ;       // the CTA's warp queues
 constexpr int NBLK = 1024;             // pair blocks of 32 with a table entry (32,768 items)
 
 // conservative tile-local data of a staged face: edge equations in pixels relative to
@@ -701,8 +702,8 @@ __device__ __forceinline__ void inv_uv_write(const Globals &g, const ViewK &V, c
 struct Smem {
     // every mode
     int view, totals[2], next;
-    int qn[2];           // queue fill of the current batch, by batch parity (the stored-ids
-                         // adjoint: its layer ring's items queued / taken)
+    int item_ctr;        // raster: the next (face, row segment) item of the chunk a warp takes
+    int qn[2];           // the stored-ids adjoint: its layer ring's items queued / taken
     unsigned long long m0[HS_MAX], m1[HS_MAX];   // per halo row: columns with S^H = 0 / 1
     unsigned char sh[HS_MAX * HS_MAX];
     // the raster (forward and re-rasterizing adjoint) only: the modes from stored layer
@@ -715,6 +716,8 @@ struct Smem {
     int hrect[CH];       // ring pairs: (x0 + 16) | (y0 + 16) << 8 | w << 16 | h << 24
     int start[CH];       // exclusive prefix of tile segments (4-pixel row pieces of the rects)
     int hstart[CH];      // exclusive prefix of ring pairs
+    unsigned rdiv[CH];   // rounded-up 2^32 / (segments per rect row), 0 for one (rect_xy)
+    unsigned hdiv[CH];   // the same for the ring rect's width
     int2 hash[HASH];     // (face id, slot) of the last staged chunk
     int wsum[2][NT / 32];
 };
@@ -777,10 +780,17 @@ __device__ __forceinline__ void fill_blocks(unsigned char *blk, int f, int start
     for (int b = (start + 31) >> 5; b <= be; ++b) blk[b] = (unsigned char)f;
 }
 
-// (x, y) of pair q in a rect of width w: q / w by a float reciprocal (exact for q < 2^16)
-__device__ __forceinline__ void rect_xy(int q, int w, int &x, int &y)
+// the multiplier of rect_xy for rects of width w >= 1: ceil(2^32 / w), 0 for w = 1
+__device__ __forceinline__ unsigned rect_div(int w)
 {
-    const int qy = __float2int_rz(((float)q + 0.5f) * __frcp_rn((float)w));
+    return w > 1 ? 0xffffffffu / (unsigned)w + 1u : 0u;
+}
+
+// (x, y) of pair q in a rect of width w, m = rect_div(w): q / w as the high word of q m,
+// exact for q < 2^32 / w (here q and w are below 2^12)
+__device__ __forceinline__ void rect_xy(int q, int w, unsigned m, int &x, int &y)
+{
+    const int qy = m ? (int)__umulhi((unsigned)q, m) : q;
     x = q - qy * w;
     y = qy;
 }
@@ -1366,6 +1376,124 @@ __device__ __forceinline__ unsigned adjoint_queued(const Globals &g, Smem &S, co
     return layers;
 }
 
+// The pretest and exact evaluation of one staged chunk's (face, 4-pixel row segment) items
+// (total of them).  Warps take 32 items at a time from the chunk's shared counter, so no
+// CTA barrier is needed until the chunk is done.  Each lane tests its item's (up to) four
+// pixel centres -- inside the face's grown bbox by construction of the rect -- with the
+// approximate edge equations stepped along x and a lower bound of the Shift key against
+// the pixel's current K-th key; the pairs that pass go to the warp's own queue (a ring of
+// WQ entries in shared memory), and whenever it holds 32 of them the warp evaluates them
+// exactly with all lanes and merges the candidates into the pixels' K-lists (other warps
+// merge into the same lists concurrently: the atomicMin cascade is order independent).
+// A queue entry is x | y << 5 | face << 10 with the top 14 bits of the key lower bound
+// above (truncated: still a lower bound).
+template <int K, int TT>
+__device__ __forceinline__ void raster_items(Smem &S, unsigned long long *kbuf, unsigned *wq,
+                                             const unsigned char *blk, const ViewK &V, int X0, int Y0, int nch,
+                                             int total, bool count, unsigned &n_pairs, unsigned &n_exact,
+                                             unsigned &n_cand)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int head = 0, qn = 0;   // the warp's queue: qn entries from wq[head] on (warp-uniform)
+    // exact evaluation of the n <= 32 entries at the queue's head, one per lane
+    auto evaluate = [&](int n) {
+        if (lane < n) {
+            int q = head + lane;
+            if (q >= WQ) q -= WQ;
+            const unsigned ent = wq[q];
+            const int x = ent & 31, y = (ent >> 5) & 31, f = (ent >> 10) & 0xff;
+            unsigned long long *slots = kbuf + (y * TT + x) * K;
+            const unsigned long long last = *reinterpret_cast<volatile unsigned long long *>(slots + K - 1);
+            if (!(__uint_as_float(ent & 0xfffc0000u) > __uint_as_float((unsigned int)(last >> 32)))) {
+                Frag fr;
+                ++n_exact;
+                if (eval_face<false>(S.F[f], (float)(X0 + x) + 0.5f, (float)(Y0 + y) + 0.5f, V.r_px, V.half_inv_S,
+                                     fr)) {
+                    ++n_cand;
+                    kbuf_insert<K>(slots, pack_frag(fr.key, S.F[f].id));
+                }
+            }
+        }
+        head += n;
+        if (head >= WQ) head -= WQ;
+        qn -= n;
+        __syncwarp();   // the entries read are free for the next pushes
+    };
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&S.item_ctr, 32);
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= total) break;
+        const int i = base + lane;
+        unsigned pm = 0u;   // pass bits of the segment's pixels
+        float kl[4] = {0.f, 0.f, 0.f, 0.f};
+        int f = 0, x = 0, y = 0;
+        if (i < total) {
+            f = pair_face(S.start, blk, nch, base, i);
+            const int rc = S.rect[f];
+            const int w = (rc >> 16) & 0xff;
+            int qx, qy;
+            rect_xy(i - S.start[f], (w + 3) >> 2, S.rdiv[f], qx, qy);
+            x = (rc & 0xff) + 4 * qx;
+            y = ((rc >> 8) & 0xff) + qy;
+            const int np = min(4, (rc & 0xff) + w - x);
+            if (count) n_pairs += np;
+            const Pre &P = S.P[f];
+            const float fx = (float)x + 0.5f, fy = (float)y + 0.5f;
+            float e0 = fmaf(P.nx[0], fx, fmaf(P.ny[0], fy, P.c[0]));
+            float e1 = fmaf(P.nx[1], fx, fmaf(P.ny[1], fy, P.c[1]));
+            float e2 = fmaf(P.nx[2], fx, fmaf(P.ny[2], fy, P.c[2]));
+            const float klb_in = 0.5f * P.zmin * (1.f - 1e-6f);
+            // the K-th slots change under other warps' merges; any value read is an upper
+            // bound of the final one, so a pair culled against it stays culled
+            const volatile unsigned long long *last = kbuf + (y * TT + x) * K + K - 1;
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                // F(p) ~ the smallest edge value: outside, the distance is at least -F;
+                // inside, the depth is at least the smallest corner depth
+                const float fmin = fminf(e0, fminf(e1, e2));
+                if (d < np && fmin >= -V.r_px - APPROX_EPS) {
+                    const float klb = fmin > APPROX_EPS    ? klb_in
+                                      : fmin < -APPROX_EPS ? fmaf(-fmin - APPROX_EPS, V.half_inv_S, 0.5f)
+                                                           : 0.f;
+                    if (!(klb > __uint_as_float((unsigned int)(last[d * K] >> 32)))) {
+                        pm |= 1u << d;
+                        kl[d] = klb;
+                    }
+                }
+                e0 += P.nx[0];
+                e1 += P.nx[1];
+                e2 += P.nx[2];
+            }
+        }
+        // warp-wide prefix of the pass counts: the lanes' places behind the queue's tail
+        const int c = __popc(pm);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int wtot = __shfl_sync(FULL, incl, 31);
+        if (wtot) {
+            int q = head + qn + incl - c;
+            if (q >= WQ) q -= WQ;
+            const unsigned ebase = ((unsigned)f << 10) | ((unsigned)y << 5) | (unsigned)x;
+#pragma unroll
+            for (int d = 0; d < 4; ++d)
+                if ((pm >> d) & 1u) {
+                    wq[q] = (__float_as_uint(kl[d]) & 0xfffc0000u) | (ebase + d);
+                    if (++q == WQ) q = 0;
+                }
+            qn += wtot;
+            __syncwarp();   // the pushed entries are visible to every lane
+            while (qn >= 32) evaluate(32);
+        }
+    }
+    if (qn > 0) evaluate(qn);
+}
+
 // everything one CTA does for global tile t.  MODE: 0 forward, 1 adjoint that
 // re-rasterizes, 2 adjoint from stored layer ids, 3 forward from stored layer ids
 // (re-shading a static geometry: no binning, raster or peel); 4, 5, 6, 7 = 2, 1, 0, 3
@@ -1413,7 +1541,6 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
     bool single_chunk = false;
     unsigned n_pairs = 0, n_exact = 0, n_cand = 0, n_layers = 0;
     float l2acc = 0.f;   // the fused L2 loss: this thread's sum of squares
-    int batch = 0;   // candidate-queue batches so far (selects the queue counter)
     if (!from_ids) {
         const long long lb = g.tile_off[t], le = g.tile_off[t + 1];
         const bool fallback = le > g.list_cap;
@@ -1451,6 +1578,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                     if (w > 0 && h > 0) {
                         cnt = ((w + 3) >> 2) * h;   // segments of up to 4 pixels per row
                         S.rect[tid] = x0 | (y0 << 8) | (w << 16) | (h << 24);
+                        S.rdiv[tid] = rect_div((w + 3) >> 2);
                     }
                     if (rho > 0) {
                         // hard bbox (without r) against the ring [-rho, TT + rho), clipped to the image
@@ -1465,6 +1593,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                         if (hw > 0 && hh > 0 && ring) {
                             hcnt = hw * hh;
                             S.hrect[tid] = (hx0 + 16) | ((hy0 + 16) << 8) | (hw << 16) | (hh << 24);
+                            S.hdiv[tid] = rect_div(hw);
                         }
                     }
                     // id -> slot for the shading phase
@@ -1508,104 +1637,18 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                     fill_blocks(blk, tid, oa + a - cnt, cnt);
                     fill_blocks(hblk, tid, ob + b - hcnt, hcnt);
                 }
-                if (tid == 0) { S.totals[0] = ta; S.totals[1] = tb; }
+                if (tid == 0) { S.totals[0] = ta; S.totals[1] = tb; S.item_ctr = 0; }
             }
             __syncthreads();
             const int total = S.totals[0], htotal = S.totals[1];
-            // (face, 4-pixel row segment) items of the tile's pairs, one per thread and
-            // batch: (1) every item takes the approximate test at its (up to) four pixel
-            // centres -- inside the face's grown bbox by construction of the rect -- with
-            // the edge equations stepped along x, and the pixels that pass are queued;
-            // (2) the queue takes the exact evaluation with full warps.  A queue entry is
-            // x | y << 5 | face << 10 with the top 14 bits of the key lower bound above
-            // (truncated: still a lower bound).
-            const int lane = tid & 31;
-            for (int b0 = 0; b0 < total; b0 += NT) {
-                int *qn = &S.qn[batch & 1];
-                const int i = b0 + tid;
-                unsigned pm = 0u;   // pass bits of the segment's pixels
-                float kl[4] = {0.f, 0.f, 0.f, 0.f};
-                int f = 0, x = 0, y = 0;
-                if (i < total) {
-                    f = pair_face(S.start, blk, nch, i - lane, i);
-                    const int rc = S.rect[f];
-                    const int w = (rc >> 16) & 0xff;
-                    int qx, qy;
-                    rect_xy(i - S.start[f], (w + 3) >> 2, qx, qy);
-                    x = (rc & 0xff) + 4 * qx;
-                    y = ((rc >> 8) & 0xff) + qy;
-                    const int np = min(4, (rc & 0xff) + w - x);
-                    if (g.stats) n_pairs += np;
-                    const Pre &P = S.P[f];
-                    const float fx = (float)x + 0.5f, fy = (float)y + 0.5f;
-                    float e0 = fmaf(P.nx[0], fx, fmaf(P.ny[0], fy, P.c[0]));
-                    float e1 = fmaf(P.nx[1], fx, fmaf(P.ny[1], fy, P.c[1]));
-                    float e2 = fmaf(P.nx[2], fx, fmaf(P.ny[2], fy, P.c[2]));
-                    const float klb_in = 0.5f * P.zmin * (1.f - 1e-6f);
-                    const unsigned long long *last = kbuf + (y * TT + x) * K + K - 1;
-#pragma unroll
-                    for (int d = 0; d < 4; ++d) {
-                        // F(p) ~ the smallest edge value: outside, the distance is at least
-                        // -F; inside, the depth is at least the smallest corner depth
-                        const float fmin = fminf(e0, fminf(e1, e2));
-                        if (d < np && fmin >= -V.r_px - APPROX_EPS) {
-                            const float klb = fmin > APPROX_EPS    ? klb_in
-                                              : fmin < -APPROX_EPS ? fmaf(-fmin - APPROX_EPS, V.half_inv_S, 0.5f)
-                                                                   : 0.f;
-                            if (!(klb > __uint_as_float((unsigned int)(last[d * K] >> 32)))) {
-                                pm |= 1u << d;
-                                kl[d] = klb;
-                            }
-                        }
-                        e0 += P.nx[0];
-                        e1 += P.nx[1];
-                        e2 += P.nx[2];
-                    }
-                }
-                // warp-wide prefix of the pass counts, one queue reservation per warp
-                const int c = __popc(pm);
-                int incl = c;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += v;
-                }
-                const int wtot = __shfl_sync(0xffffffffu, incl, 31);
-                if (wtot) {
-                    int qb = 0;
-                    if (lane == 0) qb = atomicAdd(qn, wtot);
-                    qb = __shfl_sync(0xffffffffu, qb, 0) + incl - c;
-                    const unsigned base = ((unsigned)f << 10) | ((unsigned)y << 5) | (unsigned)x;
-#pragma unroll
-                    for (int d = 0; d < 4; ++d)
-                        if ((pm >> d) & 1u) qbuf[qb++] = (__float_as_uint(kl[d]) & 0xfffc0000u) | (base + d);
-                }
-                __syncthreads();   // queue complete
-                const int nq = *qn;
-                if (tid == 0) S.qn[(batch & 1) ^ 1] = 0;   // the next batch's counter
-                for (int j = tid; j < nq; j += NT) {
-                    const unsigned ent = qbuf[j];
-                    const int x = ent & 31, y = (ent >> 5) & 31, f = (ent >> 10) & 0xff;
-                    unsigned long long *slots = kbuf + (y * TT + x) * K;
-                    const unsigned long long last = *reinterpret_cast<volatile unsigned long long *>(slots + K - 1);
-                    if (__uint_as_float(ent & 0xfffc0000u) > __uint_as_float((unsigned int)(last >> 32))) continue;
-                    Frag fr;
-                    ++n_exact;
-                    if (eval_face<false>(S.F[f], (float)(X0 + x) + 0.5f, (float)(Y0 + y) + 0.5f, V.r_px, V.half_inv_S,
-                                         fr)) {
-                        ++n_cand;
-                        kbuf_insert<K>(slots, pack_frag(fr.key, S.F[f].id));
-                    }
-                }
-                __syncthreads();   // queue consumed
-                ++batch;
-            }
+            raster_items<K, TT>(S, kbuf, qbuf + (tid >> 5) * WQ, blk, V, X0, Y0, nch, total, g.stats != nullptr,
+                                n_pairs, n_exact, n_cand);
             // (face, pixel) pairs of the ring: hard test only
             for (int i = tid; i < htotal; i += NT) {
                 const int f = pair_face(S.hstart, hblk, nch, i - (tid & 31), i);
                 const int rc = S.hrect[f];
                 int x, y;
-                rect_xy(i - S.hstart[f], (rc >> 16) & 0xff, x, y);
+                rect_xy(i - S.hstart[f], (rc >> 16) & 0xff, S.hdiv[f], x, y);
                 x += (rc & 0xff) - 16;
                 y += ((rc >> 8) & 0xff) - 16;
                 if (x >= 0 && x < TT && y >= 0 && y < TT) continue;   // interior: decided by the peel
