@@ -238,15 +238,16 @@ def recorded_traffic(kernel, pixels):
 
 
 def measured_peaks(lib, dev):
-    """FP32 FMA TFLOP/s and red.global.add.v4.f32 GB/s of this device, from the library's
-    microbenchmarks (dressi_measure_peak), and the SM count."""
+    """FP32 FMA TFLOP/s and red.global.add.v4.f32 GB/s (coalesced, and scattered one sector
+    per lane) of this device, from the library's microbenchmarks (dressi_measure_peak), and
+    the SM count."""
     import ctypes as C
 
     import torch
     buf = torch.zeros(64 << 18, dtype=torch.float32, device=dev)   # 64 MiB
     stream = C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
     res = {}
-    for which, name in ((0, "fp32_tflops"), (1, "red_v4_gbs")):
+    for which, name in ((0, "fp32_tflops"), (1, "red_v4_gbs"), (2, "red_v4_scattered_gbs")):
         v = C.c_double(0.0)
         code = lib.dressi_measure_peak(which, C.c_void_p(buf.data_ptr()), buf.numel() * 4, C.byref(v), stream)
         res[name] = float(v.value) if code == 0 else None
@@ -409,7 +410,7 @@ def measure(s, args, dev, world, rank, dist, flush, peaks, hbm_peak, main=False,
                 "work_bwd": dict(zip(("pairs", "exact_evals", "candidates", "layers"), st_bwd)),
                 "hbm_algorithmic_bytes": kb, "hbm_achieved_gbs": kb / dur / 1e9,
                 "hbm_peak_gbs": hbm_peak, "hbm_frac": kb / dur / 1e9 / hbm_peak,
-                "red_v4_peak_gbs": peaks.get("red_v4_gbs")}
+                "red_v4_peak_gbs": peaks.get("red_v4_gbs"), "red_v4_scattered_peak_gbs": peaks.get("red_v4_scattered_gbs")}
 
     # 3) the same views as a plain per-view launch sequence (one call per view, one CTA
     #    per tile), to compare with the batched form above

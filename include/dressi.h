@@ -325,7 +325,10 @@ DRESSI_API int dressi_set_tile_order_buffer(int32_t *dev_order, int32_t *dev_len
               chains in every thread of 2,048 threads per SM on every SM;
      which 1: red.global.add.v4.f32 throughput in GB/s of reduction payload: every lane
               adds a float4 into its own 16 bytes (one warp instruction covers 512
-              contiguous bytes), the launch stepping through the buffer.
+              contiguous bytes), the launch stepping through the buffer;
+     which 2: the same with every lane's float4 in a 32-byte sector of its own (lanes 4 KiB
+              apart), in GB/s of 32-byte sectors reduced at L2 (the scattered pattern of
+              gradient scatters).
    dev_buf  DEVICE scratch, 16-byte aligned, bytes >= 64 MiB (caller-owned; overwritten).
    result   HOST double receiving the figure (the best of five timed launches).
    Synchronises the host (it reads event timings back), so it must not be captured into a

@@ -30,6 +30,7 @@ constexpr int FLAG_LIVE = 1 << 7;
 // tie when choosing the edge that holds the closest point (far above their FP32 error)
 constexpr float EDGE_TIE_PX = 1e-3f;
 constexpr int FLAG_RANGE = 1 << 8;
+constexpr int FLAG_ODD = 1 << 9;    // the record's corner order is an odd permutation of the face's
 
 // ---------------------------------------------------------------------------
 // tables uploaded into the workspace
@@ -67,14 +68,20 @@ struct __align__(16) VRec {
 
 // per-face record used by every pixel evaluation.  28 words (112 bytes; word 19 holds
 // the flags): staged in shared memory, the records of 8 consecutive faces fall into
-// distinct banks for 16-byte loads.
+// distinct banks for 16-byte loads.  The corners are kept in lexicographic order of their
+// screen positions (xh, xl, yh, yl), so that the canonical (lexicographically smaller)
+// endpoint of edge i -> i+1 is corner i for edges 0 and 1 and corner 0 for edge 2 (the
+// swapped bits of the flags are always 0, 0, 1 for a live face): the evaluations pick no
+// endpoints at run time.  FLAG_ODD records whether that order is an odd permutation of the
+// face's own corner order (the normal map's tangent-frame handedness needs the latter).
 struct __align__(16) FaceRec {
     float xh[3], xl[3], yh[3], yl[3];
     float invL[3];   // 1 / length of edge i (canonical), correctly rounded
     float z[3];
     float invA;      // 1 / |twice the signed area|
     int flags;       // bit 0: orient > 0; bits 1-3: edge i swapped; bits 4-6: edge i owns;
-                     // FLAG_LIVE: not culled; FLAG_RANGE: a vertex index is out of range
+                     // FLAG_LIVE: not culled; FLAG_RANGE: a vertex index is out of range;
+                     // FLAG_ODD: corners permuted oddly
     int id;          // face index local to the mesh
     int vi[3];       // vertex indices local to the mesh
     float iw[3];     // 1 / w of the corners
@@ -188,6 +195,24 @@ __device__ __forceinline__ bool face_load(const Globals &g, const MeshK &m, cons
         R.z[i] = q.x; R.iw[i] = q.y;
         live = live && (__float_as_int(q.z) != 0);
     }
+    // corners in lexicographic order (a three-element sorting network), counting the swaps
+    bool odd = false;
+    auto order = [&](int a, int b) {
+        if (lex_less(R.xh[b], R.xl[b], R.yh[b], R.yl[b], R.xh[a], R.xl[a], R.yh[a], R.yl[a])) {
+            float t;
+            t = R.xh[a]; R.xh[a] = R.xh[b]; R.xh[b] = t;
+            t = R.xl[a]; R.xl[a] = R.xl[b]; R.xl[b] = t;
+            t = R.yh[a]; R.yh[a] = R.yh[b]; R.yh[b] = t;
+            t = R.yl[a]; R.yl[a] = R.yl[b]; R.yl[b] = t;
+            t = R.z[a]; R.z[a] = R.z[b]; R.z[b] = t;
+            t = R.iw[a]; R.iw[a] = R.iw[b]; R.iw[b] = t;
+            const int v = R.vi[a]; R.vi[a] = R.vi[b]; R.vi[b] = v;
+            odd = !odd;
+        }
+    };
+    order(0, 1);
+    order(1, 2);
+    order(0, 1);
     // twice the signed area from accurate corner differences
     const float ux = fadd(fsub(R.xh[1], R.xh[0]), fsub(R.xl[1], R.xl[0]));
     const float uy = fadd(fsub(R.yh[1], R.yh[0]), fsub(R.yl[1], R.yl[0]));
@@ -218,6 +243,7 @@ __device__ __forceinline__ bool face_load(const Globals &g, const MeshK &m, cons
     }
     R.invA = __fdiv_rn(1.f, fabsf(A2));
     if (live) flags |= FLAG_LIVE;
+    if (odd) flags |= FLAG_ODD;
     R.flags = flags;
     return live;
 }
@@ -312,7 +338,7 @@ __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, 
     bool early_out = false;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const bool sw = (R.flags >> (1 + i)) & 1;
+        const bool sw = i == 2;   // corners in lexicographic order
         const int ia = i, ib = (i + 1) % 3;
         pX[i] = sw ? dx[ib] : dx[ia]; pY[i] = sw ? dy[ib] : dy[ia];
         qX[i] = sw ? dx[ia] : dx[ib]; qY[i] = sw ? dy[ia] : dy[ib];
@@ -359,7 +385,7 @@ __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, 
             const float Qyi = i == 0 ? qY[0] : (i == 1 ? qY[1] : qY[2]);
             const float ci = i == 0 ? c[0] : (i == 1 ? c[1] : c[2]);
             const float iLi = i == 0 ? R.invL[0] : (i == 1 ? R.invL[1] : R.invL[2]);
-            const bool sw = (R.flags >> (1 + i)) & 1;
+            const bool sw = i == 2;   // corners in lexicographic order
             const int ia = i, ib = i == 2 ? 0 : i + 1;
             const float ex = fsub(Pxi, Qxi), ey = fsub(Pyi, Qyi);   // V_Q - V_P
             const float tP = ffma(Pxi, ex, fmul(Pyi, ey));
@@ -374,7 +400,7 @@ __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, 
         } else {
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                const bool sw = (R.flags >> (1 + i)) & 1;
+                const bool sw = i == 2;   // corners in lexicographic order
                 const int ia = i, ib = (i + 1) % 3;
                 const float ex = fsub(pX[i], qX[i]), ey = fsub(pY[i], qY[i]);   // V_Q - V_P
                 const float tP = ffma(pX[i], ex, fmul(pY[i], ey));
@@ -427,7 +453,7 @@ __device__ __forceinline__ void frag_lambda(const FaceRec &R, const Frag &fr, fl
         return;
     }
     const int i = fr.feat;
-    const bool sw = (R.flags >> (1 + i)) & 1;
+    const bool sw = i == 2;   // corners in lexicographic order
     const int P = sw ? (i + 1) % 3 : i, Q = sw ? i : (i + 1) % 3;
 #pragma unroll
     for (int j = 0; j < 3; ++j) lam[j] = (j == P) ? fsub(1.f, fr.t) : ((j == Q) ? fr.t : 0.f);
@@ -447,7 +473,7 @@ __device__ __forceinline__ bool hard_test(const FaceRec &R, float px, float py)
     bool inside = true;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const bool sw = (R.flags >> (1 + i)) & 1;
+        const bool sw = i == 2;   // corners in lexicographic order
         const int ia = i, ib = (i + 1) % 3;
         const float pX = sw ? dx[ib] : dx[ia], pY = sw ? dy[ib] : dy[ia];
         const float qX = sw ? dx[ia] : dx[ib], qY = sw ? dy[ia] : dy[ib];

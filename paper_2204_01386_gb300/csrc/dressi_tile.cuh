@@ -167,6 +167,7 @@ struct PeelState {
 struct Shade {
     int vi[3];
     float iw[3];
+    int odd;              // the record's corner order is an odd permutation of the face's
     float lam[3], b[3], Q;
     float C[3];
     float D;
@@ -256,7 +257,8 @@ __device__ __forceinline__ void nmap_eval(const Globals &g, const MeshK &M, cons
     N.dv2 = fsub(v[2], v[0]);
     const float det = fsub(fmul(du1, N.dv2), fmul(du2, N.dv1));
     N.idet = det != 0.f ? __fdiv_rn(1.f, det) : 0.f;
-    N.h = det < 0.f ? -1.f : 1.f;
+    // the handedness of the face's own corner order (the record's is that or its mirror)
+    N.h = ((det < 0.f) != (S.odd != 0)) ? -1.f : 1.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c)
         N.Tf[c] = fmul(fsub(fmul(fsub(P[1][c], P[0][c]), N.dv2), fmul(fsub(P[2][c], P[0][c]), N.dv1)), N.idet);
@@ -385,6 +387,7 @@ __device__ __forceinline__ bool layer_build(const Globals &g, const ViewK &V, co
     frag_lambda(L.R, L.fr, L.S.lam);
 #pragma unroll
     for (int i = 0; i < 3; ++i) { L.S.vi[i] = L.R.vi[i]; L.S.iw[i] = L.R.iw[i]; }
+    L.S.odd = (L.R.flags & FLAG_ODD) != 0;
     shade<X>(g, V, M, L.fr.dist, L.S);
     return true;
 }
@@ -630,7 +633,7 @@ __device__ __forceinline__ bool layer_adjoint(const Globals &g, const ViewK &V, 
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 if (L.fr.feat != i) continue;
-                const bool sw = (R.flags >> (1 + i)) & 1;
+                const bool sw = i == 2;   // corners in lexicographic order
                 const int ia = i, ib = (i + 1) % 3;
                 const float dPx = sw ? dx[ib] : dx[ia], dPy = sw ? dy[ib] : dy[ia];
                 const float dQx = sw ? dx[ia] : dx[ib], dQy = sw ? dy[ia] : dy[ib];
@@ -1026,6 +1029,7 @@ __device__ __forceinline__ unsigned finish_forward(const Globals &g, const Smem 
                 frag_lambda(R, fr, Sh.lam);
 #pragma unroll
                 for (int q = 0; q < 3; ++q) { Sh.vi[q] = R.vi[q]; Sh.iw[q] = R.iw[q]; }
+                Sh.odd = (R.flags & FLAG_ODD) != 0;
                 shade<EXTRA>(g, V, M, fr.dist, Sh);
                 C[0] = Sh.C[0]; C[1] = Sh.C[1]; C[2] = Sh.C[2];
                 D = Sh.D;
@@ -1587,12 +1591,21 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                         const int hx1 = min(min(TT + rho, V.W - X0) - 1, (int)floorf(B.bx1 - r - 0.5f + APPROX_EPS));
                         const int hy0 = max(max(-rho, -Y0), (int)ceilf(B.by0 + r - 0.5f - APPROX_EPS));
                         const int hy1 = min(min(TT + rho, V.H - Y0) - 1, (int)floorf(B.by1 - r - 0.5f + APPROX_EPS));
-                        const int hw = hx1 - hx0 + 1, hh = hy1 - hy0 + 1;
-                        // only faces reaching outside the tile interior have ring pixels
+                        // only faces reaching outside the tile interior have ring pixels; a box
+                        // that leaves the tile across one side only is cut to its part outside
                         const bool ring = hx0 < 0 || hy0 < 0 || hx1 >= TT || hy1 >= TT;
+                        int rx0 = hx0, rx1 = hx1, ry0 = hy0, ry1 = hy1;
+                        if (hx0 >= 0 && hx1 < TT) {
+                            if (hy1 < TT) ry1 = min(hy1, -1);
+                            else if (hy0 >= 0) ry0 = max(hy0, TT);
+                        } else if (hy0 >= 0 && hy1 < TT) {
+                            if (hx1 < TT) rx1 = min(hx1, -1);
+                            else if (hx0 >= 0) rx0 = max(hx0, TT);
+                        }
+                        const int hw = rx1 - rx0 + 1, hh = ry1 - ry0 + 1;
                         if (hw > 0 && hh > 0 && ring) {
                             hcnt = hw * hh;
-                            S.hrect[tid] = (hx0 + 16) | ((hy0 + 16) << 8) | (hw << 16) | (hh << 24);
+                            S.hrect[tid] = (rx0 + 16) | ((ry0 + 16) << 8) | (hw << 16) | (hh << 24);
                             S.hdiv[tid] = rect_div(hw);
                         }
                     }
