@@ -74,7 +74,9 @@ struct __align__(16) VRec {
 // swapped bits of the flags are always 0, 0, 1 for a live face): the evaluations pick no
 // endpoints at run time.  FLAG_ODD records whether that order is an odd permutation of the
 // face's own corner order (the normal map's tangent-frame handedness needs the latter).
-struct __align__(16) FaceRec {
+// the geometric part (the first 20 words): all that SignedDist, the hard test and Shift
+// read, and what the raster stages in shared memory
+struct __align__(16) FaceGeo {
     float xh[3], xl[3], yh[3], yl[3];
     float invL[3];   // 1 / length of edge i (canonical), correctly rounded
     float z[3];
@@ -82,6 +84,10 @@ struct __align__(16) FaceRec {
     int flags;       // bit 0: orient > 0; bits 1-3: edge i swapped; bits 4-6: edge i owns;
                      // FLAG_LIVE: not culled; FLAG_RANGE: a vertex index is out of range;
                      // FLAG_ODD: corners permuted oddly
+};
+static_assert(sizeof(FaceGeo) == 80, "FaceGeo is 20 words");
+
+struct __align__(16) FaceRec : FaceGeo {
     int id;          // face index local to the mesh
     int vi[3];       // vertex indices local to the mesh
     float iw[3];     // 1 / w of the corners
@@ -283,10 +289,10 @@ __device__ __forceinline__ void prefetch_l2(const void *a)
 }
 
 // face_get into shared memory: seven 16-byte copies
-__device__ __forceinline__ bool face_stage(const Globals &g, const ViewK &V, const MeshK &m, int f, FaceRec &dst)
+// the geometric part of face_get into shared memory: five 16-byte copies
+__device__ __forceinline__ bool face_stage(const Globals &g, const ViewK &V, const MeshK &m, int f, FaceGeo &dst)
 {
     if ((unsigned)f >= (unsigned)m.nF) {
-        dst.id = f;
         dst.flags = FLAG_RANGE;
         return false;
     }
@@ -294,12 +300,24 @@ __device__ __forceinline__ bool face_stage(const Globals &g, const ViewK &V, con
     float4 *d = reinterpret_cast<float4 *>(&dst);
     int flags = 0;
 #pragma unroll
-    for (int i = 0; i < 7; ++i) {
+    for (int i = 0; i < 5; ++i) {
         const float4 q = __ldg(src + i);
         d[i] = q;
         if (i == 4) flags = __float_as_int(q.w);   // word 19
     }
     return (flags & FLAG_LIVE) != 0;
+}
+
+// the record of face f with its geometric part taken from a staged copy: the rest (id,
+// vertex indices, 1/w) from the face table
+__device__ __forceinline__ void face_complete(const Globals &g, const ViewK &V, int f, const FaceGeo &geo, FaceRec &R)
+{
+    static_cast<FaceGeo &>(R) = geo;
+    const float4 *src = reinterpret_cast<const float4 *>(g.frec + V.frec_off + f);
+    const float4 a = __ldg(src + 5), b = __ldg(src + 6);
+    R.id = __float_as_int(a.x);
+    R.vi[0] = __float_as_int(a.y); R.vi[1] = __float_as_int(a.z); R.vi[2] = __float_as_int(a.w);
+    R.iw[0] = b.x; R.iw[1] = b.y; R.iw[2] = b.z;
 }
 
 // Result of evaluating one face at one pixel centre.
@@ -323,7 +341,7 @@ struct Frag {
 // With LAMBDA false the closest point's parameter o.t is left at 0: the peel needs the
 // key alone, shading and the adjoint re-evaluate the kept layers with LAMBDA.
 template <bool LAMBDA = true>
-__device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, float r_px, float half_inv_S,
+__device__ __forceinline__ bool eval_face(const FaceGeo &R, float px, float py, float r_px, float half_inv_S,
                                           Frag &o)
 {
     float dx[3], dy[3];
@@ -439,7 +457,7 @@ __device__ __forceinline__ bool eval_face(const FaceRec &R, float px, float py, 
 // Screen-space barycentrics of a fragment: area ratios inside the hard face; for a
 // soft fragment those of its closest point of the hard face (a corner, or the point
 // at parameter t along the canonical edge P -> Q).
-__device__ __forceinline__ void frag_lambda(const FaceRec &R, const Frag &fr, float lam[3])
+__device__ __forceinline__ void frag_lambda(const FaceGeo &R, const Frag &fr, float lam[3])
 {
     if (fr.hard) {
         lam[0] = fmul(fr.Fn[1], R.invA);
@@ -461,7 +479,7 @@ __device__ __forceinline__ void frag_lambda(const FaceRec &R, const Frag &fr, fl
 
 // Hard test only (for S^H of halo pixels): true if p lies in the closed face under
 // the fill rule.
-__device__ __forceinline__ bool hard_test(const FaceRec &R, float px, float py)
+__device__ __forceinline__ bool hard_test(const FaceGeo &R, float px, float py)
 {
     float dx[3], dy[3];
 #pragma unroll

@@ -38,8 +38,8 @@ constexpr int TT_MAX = 32;             // tile edges: 16 (one pixel per thread) 
 constexpr int RHO_MAX = 8;             // largest supported edge-mask radius
 constexpr int HS_MAX = TT_MAX + 2 * RHO_MAX;
 constexpr float APPROX_EPS = 1e-3f;    // pixel slack of the tile-local (approximate) edge equations
-constexpr int CH = 96;                 // faces staged per round (one per thread)
-constexpr int HASH = 256;              // face id -> staged slot, open addressing (> 2 CH)
+constexpr int CH = 128;                // faces staged per round (one per thread)
+constexpr int HASH = 256;              // face id -> staged slot, open addressing (2 CH: at most half full)
 constexpr unsigned long long EMPTY = ~0ULL;
 constexpr int WQ = 160;                // a warp's queue of pretested pairs (31 waiting + 32 items x 4)
 constexpr int QN = NT / 32 * WQ;       // the CTA's warp queues
@@ -60,7 +60,7 @@ struct Box {
     float bx0, bx1, by0, by1;
 };
 
-__device__ __forceinline__ void make_pre(const FaceRec &R, bool live, float tx0, float ty0, float r_px, Pre &P, Box &B)
+__device__ __forceinline__ void make_pre(const FaceGeo &R, bool live, float tx0, float ty0, float r_px, Pre &P, Box &B)
 {
     if (!live) {
         B.bx0 = 3.0e38f; B.bx1 = -3.0e38f; B.by0 = 3.0e38f; B.by1 = -3.0e38f;
@@ -713,7 +713,8 @@ struct Smem {
     // ids are launched with the shared memory up to F (the stored-ids adjoint adds its
     // layer queues there, adj_smem_bytes), leaving the rest of the SM's unified L1 / shared storage
     // to the L1 cache
-    FaceRec F[CH];
+    FaceGeo F[CH];       // the staged chunk's faces (geometric part)
+    int fid[CH];         // their face ids
     Pre P[CH];
     int rect[CH];        // tile pairs: x0 | y0 << 8 | w << 16 | h << 24 (tile-local, x0/y0 >= 0)
     int hrect[CH];       // ring pairs: (x0 + 16) | (y0 + 16) << 8 | w << 16 | h << 24
@@ -1018,7 +1019,7 @@ __device__ __forceinline__ unsigned finish_forward(const Globals &g, const Smem 
             FaceRec R;
             bool ok;
             if (slot >= 0) {
-                R = S.F[slot];
+                face_complete(g, V, id, S.F[slot], R);
                 ok = (R.flags & FLAG_LIVE) != 0;
             } else {
                 ok = face_get(g, V, M, id, R);
@@ -1415,7 +1416,7 @@ __device__ __forceinline__ void raster_items(Smem &S, unsigned long long *kbuf, 
                 if (eval_face<false>(S.F[f], (float)(X0 + x) + 0.5f, (float)(Y0 + y) + 0.5f, V.r_px, V.half_inv_S,
                                      fr)) {
                     ++n_cand;
-                    kbuf_insert<K>(slots, pack_frag(fr.key, S.F[f].id));
+                    kbuf_insert<K>(slots, pack_frag(fr.key, S.fid[f]));
                 }
             }
         }
@@ -1568,7 +1569,8 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
             int cnt = 0, hcnt = 0;
             if (tid < nch) {
                 const int f = fallback ? c0 + tid : g.lists[lb + c0 + tid];
-                FaceRec &R = S.F[tid];
+                FaceGeo &R = S.F[tid];
+                S.fid[tid] = f;
                 const bool live = face_stage(g, V, M, f, R);
                 Box B;
                 make_pre(R, live, (float)X0, (float)Y0, V.r_px, S.P[tid], B);
@@ -1611,10 +1613,10 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                     }
                     // id -> slot for the shading phase
                     if (use_hash) {
-                        unsigned hsh = ((unsigned)R.id * 2654435761u) & (HASH - 1);
+                        unsigned hsh = ((unsigned)f * 2654435761u) & (HASH - 1);
                         for (int probe = 0; probe < HASH; ++probe) {
-                            const int prev = atomicCAS(&S.hash[hsh].x, -1, R.id);
-                            if (prev == -1 || prev == R.id) { S.hash[hsh].y = tid; break; }
+                            const int prev = atomicCAS(&S.hash[hsh].x, -1, f);
+                            if (prev == -1 || prev == f) { S.hash[hsh].y = tid; break; }
                             hsh = (hsh + 1) & (HASH - 1);
                         }
                     }

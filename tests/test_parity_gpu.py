@@ -88,6 +88,29 @@ def test_fp16_texture_error_against_fp32_oracle():
     assert worst > 1e-6   # the storage rounding is visible: the comparison is not vacuous
 
 
+def test_fp16_texture_error_full_config5_crop(capsys):
+    """The full large workload (1.31M tris, 8 views of 2048^2) with its 4096^2 texture stored
+    in FP16 and FP32 arithmetic, against the FP64 oracle fed the FP32 texture, on the 64 x 64
+    crop of view 0: the measured max-abs image error (printed), within half an FP16 ulp of
+    texels in [0, 1), 2^-12 (plus the FP32 forward tolerance)."""
+    s16 = synth.config5()
+    s32 = synth.config5(tex_dtype=np.float32)
+    win = (992, 1000, 64, 64)
+    gpu = CudaPath(s16)
+    gpu.forward()
+    v = s32.views[0]
+    o = oracle.render(s32.meshes[0], v, s32.params, window=win)
+    _, sv = masks(o, s32.params, v)
+    x0, y0, w, h = win
+    err = np.abs(gpu.view_rgba(0)[y0:y0 + h, x0:x0 + w] - o["rgba"])[sv]
+    worst = float(err.max())
+    with capsys.disabled():
+        print(f"\nFP16 texture storage, large workload 64x64 crop: max-abs image error {worst:.3e} "
+              f"against the FP64 oracle on the FP32 texture ({int(sv.sum())} stable pixels; bound 2^-12 = 2.441e-04)")
+    assert worst <= 2.0 ** -12 + 1e-5
+    assert worst > 1e-6
+
+
 @pytest.mark.parametrize("schedule", [1, 2])
 @pytest.mark.parametrize("store_layers", [True, False])
 @pytest.mark.parametrize("tile", [16, 32])
