@@ -515,15 +515,18 @@ def extra_legs(s, args, dev, world, dist, flush, st):
         d2h = 4 + h_gp.numel() * 4 + h_gt.numel() * 4
         d_in = [(ps.pos, ps.tex, target),
                 (torch.empty_like(ps.pos), torch.empty_like(ps.tex), torch.empty_like(target))]
+        # the results are double-buffered too: step i's device-to-host copies run on their own
+        # stream while step i + 1 computes into the other set
+        d_out = [(loss, gp, gt), (torch.zeros_like(loss), torch.empty_like(gp), torch.empty_like(gt))]
 
-        def make_step(pos, tex, tgt):
+        def make_step(pos, tex, tgt, ls, gpk, gtk):
             def f():
-                loss.zero_()
-                r.forward(store_layers=store, out=out, ids=ids, pos=pos, tex=tex, target=tgt, grad=grad, loss=loss)
-                r.backward(grad, ids=ids, grad_pos=gp, grad_tex=gt, pos=pos, tex=tex)
+                ls.zero_()
+                r.forward(store_layers=store, out=out, ids=ids, pos=pos, tex=tex, target=tgt, grad=grad, loss=ls)
+                r.backward(grad, ids=ids, grad_pos=gpk, grad_tex=gtk, pos=pos, tex=tex)
             return f
 
-        runs = [make_step(*b) for b in d_in]
+        runs = [make_step(*d_in[k], *d_out[k]) for k in range(2)]
         if use_graph:
             graphs = []
             for f in runs:
@@ -535,11 +538,14 @@ def extra_legs(s, args, dev, world, dist, flush, st):
                 graphs.append(gr)
             runs = [gr.replay for gr in graphs]
         copy = torch.cuda.Stream(dev)
-        ready = [torch.cuda.Event() for _ in range(2)]
-        free = [torch.cuda.Event() for _ in range(2)]
+        drain = torch.cuda.Stream(dev)
+        ready = [torch.cuda.Event() for _ in range(2)]     # inputs of set k on the device
+        free = [torch.cuda.Event() for _ in range(2)]      # set k's inputs no longer read
+        done = [torch.cuda.Event() for _ in range(2)]      # set k's results computed
+        drained = [torch.cuda.Event() for _ in range(2)]   # set k's results copied to the host
 
         def e2e_steps(n):
-            for ev in free:
+            for ev in free + drained:
                 ev.record(stream)
 
             def fetch(k):
@@ -555,12 +561,20 @@ def extra_legs(s, args, dev, world, dist, flush, st):
                 if i + 1 < n:
                     fetch(1 - k)
                 stream.wait_event(ready[k])
+                stream.wait_event(drained[k])
                 runs[k]()
-                exchange()
-                h_loss.copy_(loss, non_blocking=True)
-                h_gp.copy_(gp, non_blocking=True)
-                h_gt.copy_(gt, non_blocking=True)
+                if world > 1:
+                    dist.all_reduce(d_out[k][1])
+                    dist.all_reduce(d_out[k][2])
+                done[k].record(stream)
                 free[k].record(stream)
+                with torch.cuda.stream(drain):
+                    drain.wait_event(done[k])
+                    for h, d in zip((h_loss, h_gp, h_gt), d_out[k]):
+                        h.copy_(d, non_blocking=True)
+                    drained[k].record(drain)
+            # the last step's results are on the host before the clock stops
+            stream.wait_event(drained[(n - 1) % 2])
 
         e2e_steps(2)
         torch.cuda.synchronize()
@@ -579,7 +593,8 @@ def extra_legs(s, args, dev, world, dist, flush, st):
             ms = float(t.item())
         e2e = {"value": s.pixels * world * n_e2e / (ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": n_e2e, "cuda_graph": use_graph,
-               "note": "inputs double-buffered: the next step's host-to-device copies overlap this step"}
+               "note": "inputs and results double-buffered: the next step's host-to-device copies and the "
+                       "previous step's device-to-host copies overlap this step"}
     return cached, e2e
 
 

@@ -1551,6 +1551,8 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
         const bool fallback = le > g.list_cap;
         const int n = fallback ? M.nF : (int)(le - lb);
         if (fallback && tid == 0) atomicOr(g.status, DRESSI_DEV_TILE_OVERFLOW);
+        // an adjoint over a tile no face reaches has nothing to propagate
+        if (BWD && n == 0) return;
         single_chunk = n <= CH;
         // the id -> slot hash serves the forward's shading of a tile staged in one chunk
         const bool use_hash = !BWD && single_chunk;
@@ -1693,11 +1695,17 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
     } else {
         // layers stored by the forward: S^H of the tile and of its ring is the hard flag
         // of every pixel's stored front layer (a non-negative id: hard; bit 31: soft)
+        bool any = false;   // some pixel of the tile itself holds a layer
         for (int i = tid; i < hs * hs; i += NT) {
             if (S.sh[i] == 2) continue;
-            const long long hp = V.pix_off + (long long)(Y0 - rho + i / hs) * V.W + (X0 - rho + i % hs);
-            S.sh[i] = __ldg(g.ids_in + hp) >= 0 ? 1 : 0;
+            const int hx = i % hs - rho, hy = i / hs - rho;
+            const long long hp = V.pix_off + (long long)(Y0 + hy) * V.W + (X0 + hx);
+            const int id0 = __ldg(g.ids_in + hp);
+            S.sh[i] = id0 >= 0 ? 1 : 0;
+            any |= id0 != -1 && hx >= 0 && hy >= 0 && hx < TT && hy < TT;
         }
+        // an adjoint over a tile whose pixels hold no layer has nothing to propagate
+        if (BWD && !__syncthreads_or(any)) return;
     }
     __syncthreads();
     if (g.edge_mode == 0) {
