@@ -1540,10 +1540,8 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
     const bool light_grad = EXTRA && g.glight != nullptr && g.shade_mode >= 2;
     float *glacc = light_grad ? gl_slots[tid] : nullptr;
     if (light_grad) glacc[0] = glacc[1] = glacc[2] = 0.f;
-    if (!from_ids)   // 16-byte stores (TT^2 K is even; kbuf is 16-byte aligned)
-        for (int i = tid; i < TT * TT * K / 2; i += NT)
-            reinterpret_cast<ulonglong2 *>(kbuf)[i] = make_ulonglong2(EMPTY, EMPTY);
     bool single_chunk = false;
+    bool empty = false;   // a forward over a tile that no face reaches
     unsigned n_pairs = 0, n_exact = 0, n_cand = 0, n_layers = 0;
     float l2acc = 0.f;   // the fused L2 loss: this thread's sum of squares
     if (!from_ids) {
@@ -1553,6 +1551,12 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
         if (fallback && tid == 0) atomicOr(g.status, DRESSI_DEV_TILE_OVERFLOW);
         // an adjoint over a tile no face reaches has nothing to propagate
         if (BWD && n == 0) return;
+        // a forward over such a tile has no layer and S^H = 0 in the tile and its ring (no
+        // face comes within the binning radius), so E = 0 or no layer to blend: background
+        empty = n == 0;
+        if (!empty)   // 16-byte stores (TT^2 K is even; kbuf is 16-byte aligned)
+            for (int i = tid; i < TT * TT * K / 2; i += NT)
+                reinterpret_cast<ulonglong2 *>(kbuf)[i] = make_ulonglong2(EMPTY, EMPTY);
         single_chunk = n <= CH;
         // the id -> slot hash serves the forward's shading of a tile staged in one chunk
         const bool use_hash = !BWD && single_chunk;
@@ -1687,7 +1691,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
         for (int j = 0; j < PPT; ++j) {
             const int p = tid + j * NT;
             const int lx = p % TT, ly = p / TT;
-            if (lx >= wlim || ly >= hlim) continue;
+            if (empty || lx >= wlim || ly >= hlim) continue;
             const unsigned long long v = kbuf[p * K];
             const bool sh = v != EMPTY && kept_hard(g, V, M, v, (float)(X0 + lx) + 0.5f, (float)(Y0 + ly) + 0.5f);
             S.sh[(ly + rho) * hs + (lx + rho)] = sh ? 1 : 0;
@@ -1708,7 +1712,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
         if (BWD && !__syncthreads_or(any)) return;
     }
     __syncthreads();
-    if (g.edge_mode == 0) {
+    if (g.edge_mode == 0 && !empty) {
         // per halo row, the columns holding S^H = 0 and S^H = 1 (hs <= 48 fits 64 bits)
         const int lane = tid & 31;
         for (int row = tid >> 5; row < hs; row += NT / 32) {
@@ -1727,6 +1731,25 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
 
     if constexpr (MODE == 2) {
         n_layers = adjoint_queued<K, TT>(g, S, V, M, X0, Y0, rho, wlim, hlim);
+    } else if (empty) {
+        // background: no layer, RGBA 0 (the loss's gradient 2 (0 - target))
+        for (int j = 0; j < PPT; ++j) {
+            const int p = tid + j * NT;
+            const int lx = p % TT, ly = p / TT;
+            if (lx >= wlim || ly >= hlim) continue;
+            const long long pix = V.pix_off + (long long)(Y0 + ly) * V.W + (X0 + lx);
+            if (g.ids)
+#pragma unroll
+                for (int k = 0; k < K; ++k) g.ids[(long long)k * g.n_pix + pix] = -1;
+            const float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+            reinterpret_cast<float4 *>(g.out)[pix] = o;
+            if (g.l2_target) {
+                const float4 tg = __ldg(reinterpret_cast<const float4 *>(g.l2_target) + pix);
+                const float dx = o.x - tg.x, dy = o.y - tg.y, dz = o.z - tg.z, dw = o.w - tg.w;
+                reinterpret_cast<float4 *>(g.l2_grad)[pix] = make_float4(2.f * dx, 2.f * dy, 2.f * dz, 2.f * dw);
+                l2acc += dx * dx + dy * dy + dz * dz + dw * dw;
+            }
+        }
     } else for (int j = 0; j < PPT; ++j) {
         const int p = tid + j * NT;
         const int lx = p % TT, ly = p / TT;
