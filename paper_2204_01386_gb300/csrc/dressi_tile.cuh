@@ -1821,15 +1821,16 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
     }
 }
 
-// one CTA per tile.  CTAs per SM (measured best): four for the forward (64 registers)
-// and for the layer-queued adjoint from stored ids (64, a few spills: more warps beat
-// the registers for its gathers); the adjoint that re-rasterizes holds both
-// the raster and the adjoint state: four with 16 px tiles, three with 32 px tiles (whose
-// K-lists limit the shared memory to three CTAs anyway).
+// one CTA per tile.  CTAs per SM (measured best): four for the forward (64 registers),
+// for the layer-queued adjoint from stored ids (64, a few spills: more warps beat the
+// registers for its gathers; five, at 48 registers, spill too much) and for the adjoint
+// that re-rasterizes, which holds both the raster and the adjoint state (64 registers and
+// spills, but four CTAs beat three at 80 registers by 4 % on the 2048^2 views); three for
+// the instantiations with the normal map, the light gradient and the inverse UV.
 template <int MODE, int TT>
 constexpr int tile_min_ctas()
 {
-    return MODE == 0 || MODE == 3 || MODE == 2 ? 4 : (MODE == 4 || MODE >= 6) ? 3 : (TT == 16 ? 4 : 3);
+    return (MODE == 4 || MODE >= 6) ? 3 : 4;
 }
 
 template <int K, int MODE, int TT>
