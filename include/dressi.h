@@ -122,7 +122,7 @@ typedef struct {
                            edges and UV differences, orthogonalised against the interpolated
                            normal n; bitangent h n x T', h the sign of the UV determinant),
                            n' = normalize(nt0 T' + nt1 B' + nt2 n) */
-    int32_t texgrad_mode; /* 0 warp-aggregated atomics, 1 texel-space gather (deterministic),
+    int32_t texgrad_mode; /* 0 vector red.global atomics, 1 texel-space gather (deterministic),
                              2 inverse UV (Sec. 3.3.2, Alg. 1; approximate: each texel takes the
                              dL/d(albedo) of the last shaded sample that lands on it) */
     int32_t tile;       /* tile edge in pixels: 16 or 32; 0 = 16 */
