@@ -142,9 +142,11 @@ typedef struct {
                             transform, face table, normals and, for layer_ids == NULL, the
                             tile lists -- and the backward takes it instead of rebuilding it
                             (with layer_ids == NULL it still re-rasterizes: layers and
-                            barycentrics are recomputed).  0 = rebuild.  The caller
-                            guarantees the precondition; a workspace written by another call
-                            since gives wrong gradients. */
+                            barycentrics are recomputed, each pixel's K-list starting from the
+                            K-th (key, face) that a forward without layer ids kept in the
+                            workspace, which culls the candidates that cannot reach the K
+                            layers).  0 = rebuild.  The caller guarantees the precondition; a
+                            workspace written by another call since gives wrong gradients. */
 } dressi_params;
 
 /* Size in bytes of the workspace that dressi_forward / dressi_backward need for

@@ -44,7 +44,7 @@ static void launch_tile_profiled(const Globals &g, int pass, cudaStream_t s)
 struct Layout {
     size_t views, meshes, vrec, frec, tile_view, tile_count, tile_off, tile_cursor, lists, nrm, adj_off, adj_cur, adj, scan_partial,
         sgrad, ngrad, queue,
-        tile_order, lpt_hist, tg_keys, tg_pay0, tg_pay1, tg_scratch, inv_uv, total;
+        tile_order, lpt_hist, kth, kth_flag, tg_keys, tg_pay0, tg_pay1, tg_scratch, inv_uv, total;
     long long tg_slots;   // texel-gather record slots (0 unless texgrad_mode 1 with a texture)
     long long n_vrec;
     int total_tiles;
@@ -187,6 +187,8 @@ static bool make_plan(const dressi_scene *sc, const dressi_view *views, int n_vi
     L.queue = o; o = align_up(o + sizeof(int) * 4);
     L.tile_order = o; o = align_up(o + sizeof(int) * (size_t)std::max(tiles, 1));
     L.lpt_hist = o; o = align_up(o + sizeof(int) * LPT_BINS);
+    L.kth = o; o = align_up(o + sizeof(unsigned long long) * (size_t)std::max<long long>(view_pixels, 1));
+    L.kth_flag = o; o = align_up(o + sizeof(int));
     L.tg_slots = (p->texgrad_mode != 0 && textured) ? view_pixels * p->K : 0;
     // the texel gather sorts 32-bit texel keys with 0xffffffff marking an empty slot: every
     // packed texel index must stay below it
@@ -282,6 +284,8 @@ static Globals make_globals(const dressi_scene *sc, const dressi_params *p, cons
     g.queue = reinterpret_cast<int *>(ws + L.queue);
     g.tile_order = nullptr;
     g.lpt_hist = reinterpret_cast<int *>(ws + L.lpt_hist);
+    g.kth = nullptr;
+    g.kth_flag = reinterpret_cast<int *>(ws + L.kth_flag);
     g.stats = g_stats;
     g.tg_keys = reinterpret_cast<unsigned *>(ws + L.tg_keys);
     g.tg_pay0 = reinterpret_cast<float4 *>(ws + L.tg_pay0);
@@ -313,6 +317,15 @@ static void run_setup(const Globals &g, const Plan &P, char *ws, bool need_bins,
         launch_normals(g, (int)P.meshes.size(), P.max_nf, P.max_nv, s);
     }
     if (need_bins) launch_bin(g, (int)P.views.size(), P.max_nf_view, s);
+}
+
+// a forward that stores no layer ids keeps every pixel's K-th (key, id) in the workspace
+// for a re-rasterizing adjoint; the flag says whether the last forward did
+static void keep_kth(Globals &g, const Plan &P, char *ws, cudaStream_t s)
+{
+    const bool keep = g.ids == nullptr;
+    g.kth = keep ? reinterpret_cast<unsigned long long *>(ws + P.lay.kth) : nullptr;
+    cudaMemsetAsync(ws + P.lay.kth_flag, keep ? 1 : 0, sizeof(int), s);
 }
 
 // the per-tile kernel, persistent (longest face list first when the lists exist) or
@@ -450,6 +463,7 @@ int dressi_forward(const dressi_scene *scene, const dressi_view *views, int32_t 
     Globals g = make_globals(scene, params, P, w, n_pix, dev_status);
     g.out = out_rgba;
     g.ids = layer_ids;
+    keep_kth(g, P, w, s);
     run_setup(g, P, w, true, s);
     run_tiles(g, P, w, true, 0, s);
     return cudaGetLastError() == cudaSuccess ? DRESSI_OK : DRESSI_ERR_LAUNCH;
@@ -476,6 +490,7 @@ int dressi_forward_l2(const dressi_scene *scene, const dressi_view *views, int32
     g.l2_target = target;
     g.l2_grad = grad_rgba;
     g.l2_loss = loss_accum;
+    keep_kth(g, P, w, s);
     run_setup(g, P, w, true, s);
     run_tiles(g, P, w, true, 0, s);
     return cudaGetLastError() == cudaSuccess ? DRESSI_OK : DRESSI_ERR_LAUNCH;
@@ -509,6 +524,7 @@ int dressi_forward_from_layers(const dressi_scene *scene, const dressi_view *vie
     Globals g = make_globals(scene, params, P, w, n_pix, dev_status);
     g.out = out_rgba;
     g.ids_in = layer_ids;
+    cudaMemsetAsync(w + P.lay.kth_flag, 0, sizeof(int), s);   // no K-th keys from this pass
     // vertex records, face table and normals (shading needs them), no binning
     run_setup(g, P, w, false, s);
     run_tiles(g, P, w, false, 2, s);
@@ -561,6 +577,8 @@ int dressi_backward_ex(const dressi_scene *scene, const dressi_view *views, int3
     if (!tex_records) g.texgrad_mode = 0;
     if (gather) cudaMemsetAsync(w + P.lay.tg_keys, 0xff, sizeof(unsigned) * (size_t)P.lay.tg_slots, s);
     if (inv_uv) cudaMemsetAsync(w + P.lay.inv_uv, 0xff, sizeof(int) * (size_t)P.n_texels, s);
+    // re-rasterizing after a forward on this workspace: its K-th keys, if it kept them
+    if (params->reuse_setup && !layer_ids) g.kth = reinterpret_cast<unsigned long long *>(w + P.lay.kth);
     if (!params->reuse_setup) run_setup(g, P, w, layer_ids == nullptr, s);
     run_tiles(g, P, w, layer_ids == nullptr, 1, s);
     if (gather)

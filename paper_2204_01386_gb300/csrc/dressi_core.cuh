@@ -130,6 +130,12 @@ struct Globals {
     int *queue;           // tile queue head (zeroed before each pass)
     const int *tile_order;  // tiles by descending face-list length, or nullptr
     int *lpt_hist;        // [LPT_BINS] scratch of the ordering sort
+    // the forward without stored layer ids keeps each pixel's K-th (key, id) here (per view
+    // pixel, at slot_base + pixel; *kth_flag nonzero once it did); the re-rasterizing adjoint
+    // that takes the forward's setup starts every K-list with it, so that pairs whose key
+    // bound lies above it are culled from the start
+    unsigned long long *kth;
+    int *kth_flag;
     // forward
     float *out;
     int *ids;             // [K][n_pix] or nullptr

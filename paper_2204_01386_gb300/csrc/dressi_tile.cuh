@@ -1557,6 +1557,17 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
         if (!empty)   // 16-byte stores (TT^2 K is even; kbuf is 16-byte aligned)
             for (int i = tid; i < TT * TT * K / 2; i += NT)
                 reinterpret_cast<ulonglong2 *>(kbuf)[i] = make_ulonglong2(EMPTY, EMPTY);
+        if (BWD && g.kth && *g.kth_flag) {
+            // the forward's K-th (key, id) of every pixel as a first entry of its K-list: it
+            // is the K-th smallest of the pixel's candidates, so it stays in the last slot and
+            // every pair whose key bound exceeds it is culled; its own pair finds it there
+            __syncthreads();   // after the clearing stores
+            for (int p = tid; p < TT * TT; p += NT) {
+                const int lx = p % TT, ly = p / TT;
+                if (lx < wlim && ly < hlim)
+                    kbuf[p * K + K - 1] = g.kth[V.slot_base + (long long)(Y0 + ly) * V.W + (X0 + lx)];
+            }
+        }
         single_chunk = n <= CH;
         // the id -> slot hash serves the forward's shading of a tile staged in one chunk
         const bool use_hash = !BWD && single_chunk;
@@ -1692,6 +1703,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
             const int p = tid + j * NT;
             const int lx = p % TT, ly = p / TT;
             if (empty || lx >= wlim || ly >= hlim) continue;
+            if (!BWD && g.kth) g.kth[V.slot_base + (long long)(Y0 + ly) * V.W + (X0 + lx)] = kbuf[p * K + K - 1];
             const unsigned long long v = kbuf[p * K];
             const bool sh = v != EMPTY && kept_hard(g, V, M, v, (float)(X0 + lx) + 0.5f, (float)(Y0 + ly) + 0.5f);
             S.sh[(ly + rho) * hs + (lx + rho)] = sh ? 1 : 0;

@@ -63,6 +63,12 @@ class CudaPath:
         # layer ids are always kept here so they can be compared; whether the
         # backward re-rasterizes is chosen in backward()
         out, ids = self.r.forward(store_layers=True)
+        if not store_layers:
+            # then the pass a checkpointed step runs: no layer ids, each pixel's K-th
+            # (key, id) kept in the workspace, where the re-rasterizing adjoint (which takes
+            # this setup) starts its K-lists from them
+            out2, _ = self.r.forward(store_layers=False)
+            assert torch.equal(out, out2)
         torch.cuda.synchronize()
         self.out, self.ids = out, ids
         return out, ids

@@ -5,6 +5,7 @@ import torch
 
 import oracle
 import synth
+from paper_2204_01386_gb300 import PackedScene, Renderer
 from parity import CudaPath, compare_scene, masks, rel_l2
 from scenes_small import grid_mesh, pixel_mesh, pixel_scene
 
@@ -204,6 +205,25 @@ def test_exact_fill_rule_on_gpu():
     assert si.mean() > 0.5
     assert (gpu.view_ids(0)[:, si] == o["ids"][:, si]).all()
     assert (gpu.view_rgba(0)[..., 3] == 1.0).all()
+
+
+@pytest.mark.parametrize("tile,schedule", [(32, 2), (16, 1)])
+def test_reraster_adjoint_from_forward_kth_keys_equals_cold(tile, schedule):
+    """The re-rasterizing adjoint that starts its K-lists from the K-th keys a forward
+    without layer ids left in the workspace gives the gradients of a cold re-raster (its own
+    setup, no keys) up to the order of the float atomics, on the large workload's mesh."""
+    s = synth.config5(subdiv=5, n_views=3, res=384, tex_side=512)
+    ps = PackedScene(s.meshes, "cuda")
+    r = Renderer(ps, s.views, s.params, tile=tile, schedule=schedule)
+    g = torch.randn(r.n_pix, 4, device="cuda")
+    r.forward(store_layers=False)
+    seeded = r.backward(g, ids=None)
+    cold = r.backward(g, ids=None, reuse_setup=False)
+    torch.cuda.synchronize()
+    for a, b in zip(seeded, cold):
+        if a is not None:
+            assert rel_l2(a.double().cpu().numpy(), b.double().cpu().numpy()) < 1e-6
+    assert r.device_status() == 0
 
 
 def test_store_and_recompute_backward_agree():
