@@ -514,11 +514,13 @@ __device__ __forceinline__ bool frag_less(float ka, int ia, float kb, int ib)
     return ka < kb || (ka == kb && ia < ib);
 }
 
+// 1 / (1 + exp(-x)) from e = exp(-|x|) <= 1 (no overflow): 1 / (1 + e) for x >= 0, e / (1 + e)
+// below; the exponential and the division are the fast hardware forms (a few ulp)
 __device__ __forceinline__ float sigmoidf_stable(float x)
 {
-    if (x >= 0.f) return __fdiv_rn(1.f, 1.f + expf(-x));
-    float e = expf(x);
-    return __fdiv_rn(e, 1.f + e);
+    const float e = __expf(-fabsf(x));
+    const float s = __fdividef(1.f, 1.f + e);
+    return x >= 0.f ? s : e * s;
 }
 
 }  // namespace dressi

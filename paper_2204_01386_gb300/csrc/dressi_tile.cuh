@@ -301,6 +301,9 @@ __device__ __forceinline__ void nmap_eval(const Globals &g, const MeshK &M, cons
 // b, C, D and the sampling state of one layer from S.vi, S.iw, S.lam and dist.  Every
 // operation is rounded as written (no contraction left to the compiler), so the kernels
 // that shade a layer -- forward, forward from stored layers, adjoint -- agree bit for bit.
+// The reciprocals of the barycentric sum and of the normal's length, and the sigmoid's
+// exponential and division, are the fast hardware approximations (a few ulp, far inside the
+// 1e-5 image tolerance): this function runs for every shaded layer in every pass.
 // X: the kernel has the normal map compiled in (the kernels without it stay lean)
 template <bool X>
 __device__ __forceinline__ void shade(const Globals &g, const ViewK &V, const MeshK &M, float dist, Shade &S)
@@ -309,7 +312,7 @@ __device__ __forceinline__ void shade(const Globals &g, const ViewK &V, const Me
 #pragma unroll
     for (int i = 0; i < 3; ++i) q[i] = fmul(S.lam[i], S.iw[i]);
     S.Q = fadd(fadd(q[0], q[1]), q[2]);
-    const float iQ = __fdiv_rn(1.f, S.Q);
+    const float iQ = __fdividef(1.f, S.Q);   // 2 ulp
 #pragma unroll
     for (int i = 0; i < 3; ++i) S.b[i] = fmul(q[i], iQ);
     S.D = sigmoidf_stable(fmul(dist, V.inv_sigma_px));
@@ -357,8 +360,9 @@ __device__ __forceinline__ void shade(const Globals &g, const ViewK &V, const Me
         m[1] = ffma(S.b[i], nv.y, m[1]);
         m[2] = ffma(S.b[i], nv.z, m[2]);
     }
-    S.mlen = __fsqrt_rn(ffma(m[0], m[0], ffma(m[1], m[1], fmul(m[2], m[2]))));
-    const float il = S.mlen > 0.f ? __fdiv_rn(1.f, S.mlen) : 0.f;
+    const float m2 = ffma(m[0], m[0], ffma(m[1], m[1], fmul(m[2], m[2])));
+    const float il = m2 > 0.f ? rsqrtf(m2) : 0.f;   // 2 ulp
+    S.mlen = fmul(m2, il);
     S.n[0] = fmul(m[0], il); S.n[1] = fmul(m[1], il); S.n[2] = fmul(m[2], il);
     S.np[0] = S.n[0]; S.np[1] = S.n[1]; S.np[2] = S.n[2];
     if (X && g.shade_mode == 3) {
