@@ -4,13 +4,16 @@
 //
 // One CTA owns one TT x TT pixel tile of one view (TT = 16 or 32; 256 threads).  Per CTA:
 //   1. the tile's face list is staged in shared memory, CH faces at a time, from the
-//      per-(view, face) record table, with tile-local edge equations for a cheap
-//      conservative pretest; the next round's records are prefetched into L2;
-//   2. every (face, pixel) pair of the faces' r-grown bounding boxes is enumerated
-//      (pair -> face through a per-32-pair table); pairs passing the pretest and the
-//      key lower bound are queued, and the queue gets the exact SignedDist, hard test
-//      and Shift key with full warps; each pixel keeps its K smallest (key, id) pairs
-//      in shared memory (depth peeling of Alg. 2 as a per-pixel K-selection);
+//      per-(view, face) record table (the 80-byte geometric part of each record), with
+//      tile-local edge equations for a cheap conservative pretest; the next round's
+//      records are prefetched into L2;
+//   2. every (face, 4-pixel row segment) item of the faces' r-grown bounding boxes is
+//      enumerated (item -> face through a per-32-item table); warps take 32 items at a
+//      time, the pixels passing the pretest and the key lower bound go to the warp's own
+//      queue, and the queue gets the exact SignedDist, hard test and Shift key with full
+//      warps; each pixel keeps its K smallest (key, id) pairs in shared memory (depth
+//      peeling of Alg. 2 as a per-pixel K-selection; the re-rasterizing adjoint starts
+//      from the forward's K-th pair when the forward kept it);
 //   3. the hard stencil S^H of a ring of rho pixels around the tile is built from the
 //      same staged faces (hard test only), so the edge mask E of every tile pixel is
 //      known without a second pass over the image;
