@@ -166,7 +166,7 @@ static bool make_plan(const dressi_scene *sc, const dressi_view *views, int n_vi
     // which must read as over capacity
     if (L.list_cap > 0x7ffffffeLL) L.list_cap = 0x7ffffffeLL;
     size_t o = 0;
-    L.views = o; o = align_up(o + sizeof(ViewK) * n_views);
+    L.views = o; o = align_up(o + sizeof(ViewK) * n_views);   // at 0, the mesh table right after it
     L.meshes = o; o = align_up(o + sizeof(MeshK) * sc->n_meshes);
     L.vrec = o; o = align_up(o + sizeof(VRec) * (size_t)std::max<long long>(vrec, 1));
     L.frec = o; o = align_up(o + sizeof(FaceRec) * (size_t)std::max<long long>(view_faces, 1));
@@ -298,18 +298,19 @@ static Globals make_globals(const dressi_scene *sc, const dressi_params *p, cons
 }
 
 // setup shared by both passes: tables, vertex transform, normals, binning
-static void run_setup(const Globals &g, const Plan &P, char *ws, bool need_bins, cudaStream_t s)
+static void run_setup(Globals &g, const Plan &P, char *ws, bool need_bins, cudaStream_t s)
 {
     const Layout &L = P.lay;
-    upload(P.views.data(), sizeof(ViewK) * P.views.size(), ws + L.views, s);
-    upload(P.meshes.data(), sizeof(MeshK) * P.meshes.size(), ws + L.meshes, s);
-    if (need_bins) {
-        cudaMemsetAsync(ws + L.tile_count, 0, sizeof(int) * (size_t)L.total_tiles, s);
-        cudaMemsetAsync(ws + L.tile_cursor, 0, sizeof(int) * (size_t)L.total_tiles, s);
-    }
+    // the view and mesh tables, adjacent in the workspace, in one upload
+    std::vector<unsigned char> tables(L.meshes + sizeof(MeshK) * P.meshes.size(), 0);
+    std::memcpy(tables.data() + L.views, P.views.data(), sizeof(ViewK) * P.views.size());
+    std::memcpy(tables.data() + L.meshes, P.meshes.data(), sizeof(MeshK) * P.meshes.size());
+    upload(tables.data(), tables.size(), ws + L.views, s);
+    // the vertex transform also writes the tile -> view table and, before the face table
+    // counts into them, clears the tile counters
+    g.zero_bins = need_bins ? 1 : 0;
     launch_vertex(g, (int)P.views.size(), P.max_nv_view, s);
     launch_face(g, (int)P.views.size(), P.max_nf_view, need_bins, s);
-    launch_tile_view(g, (int)P.views.size(), s);
     if (g.shade_mode >= 2) {
         const size_t nv = (size_t)std::max<long long>(g.n_verts_total, 1);
         cudaMemsetAsync(ws + L.adj_off, 0, sizeof(int) * (nv + 1), s);

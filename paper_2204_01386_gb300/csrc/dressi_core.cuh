@@ -136,6 +136,8 @@ struct Globals {
     // bound lies above it are culled from the start
     unsigned long long *kth;
     int *kth_flag;
+    int zero_bins;        // the vertex transform clears tile_count and tile_cursor
+    int pad2;
     // forward
     float *out;
     int *ids;             // [K][n_pix] or nullptr

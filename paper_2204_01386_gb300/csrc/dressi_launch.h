@@ -9,7 +9,6 @@ void count_launch(int n);
 void launch_vertex(const Globals &g, int n_views, int max_nv, cudaStream_t s);
 void launch_normals(const Globals &g, int n_meshes, int max_nf, int max_nv, cudaStream_t s);
 void launch_face(const Globals &g, int n_views, int max_nf, bool count, cudaStream_t s);
-void launch_tile_view(const Globals &g, int n_views, cudaStream_t s);
 void launch_bin(const Globals &g, int n_views, int max_nf, cudaStream_t s);
 void launch_tile(const Globals &g, bool backward, cudaStream_t s);
 void launch_tile_shade(const Globals &g, cudaStream_t s);

@@ -73,6 +73,16 @@ __global__ void k_vertex(Globals g)
     VRec *out = g.vrec + V.vrec_off;
     const long long nvt = g.n_verts_total;
     bool bad = false;
+    // this view's tiles: the tile -> view table, and cleared bin counters when the face table
+    // will count into them
+    const int nt = V.tiles_x * V.tiles_y;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += gridDim.x * blockDim.x) {
+        g.tile_view[V.tile_base + i] = blockIdx.y;
+        if (g.zero_bins) {
+            g.tile_count[V.tile_base + i] = 0;
+            g.tile_cursor[V.tile_base + i] = 0;
+        }
+    }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M.nV; i += gridDim.x * blockDim.x) {
         const long long gi = M.vert_off + i;
         const float p0 = __ldg(g.pos + gi), p1 = __ldg(g.pos + nvt + gi), p2 = __ldg(g.pos + 2 * nvt + gi);
@@ -171,16 +181,6 @@ __global__ void k_normal_csr(Globals g)
         const float s = l > 0.f ? 1.f / l : 0.f;
         g.nrm[gv] = make_float4(m0 * s, m1 * s, m2 * s, l);
     }
-}
-
-// ---------------------------------------------------------------------------
-// tile -> view table: one load per tile instead of a search over the views
-// ---------------------------------------------------------------------------
-__global__ void k_tile_view(Globals g)
-{
-    const ViewK &V = g.views[blockIdx.x];
-    const int n = V.tiles_x * V.tiles_y;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) g.tile_view[V.tile_base + i] = blockIdx.x;
 }
 
 // ---------------------------------------------------------------------------
@@ -501,12 +501,6 @@ void launch_normals(const Globals &g, int n_meshes, int max_nf, int max_nv, cuda
     k_adjacency<1><<<gf, 256, 0, s>>>(g);
     k_normal_csr<<<gv, 256, 0, s>>>(g);
     count_launch(3);
-}
-
-void launch_tile_view(const Globals &g, int n_views, cudaStream_t s)
-{
-    k_tile_view<<<n_views, 256, 0, s>>>(g);
-    count_launch(1);
 }
 
 void launch_face(const Globals &g, int n_views, int max_nf, bool count, cudaStream_t s)

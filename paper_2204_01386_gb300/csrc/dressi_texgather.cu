@@ -245,8 +245,40 @@ static int grid_of(long long n, int block, int cap)
     return (int)b;
 }
 
+// the whole scan in one block, SC_TILE items at a time with a running carry (short arrays:
+// one launch instead of three); the total goes where the three-kernel scan leaves it
+__global__ void __launch_bounds__(SC_THREADS) k_scan_single(int *a, int n, int *total_out)
+{
+    __shared__ int wt[32];
+    int carry = 0;
+    for (int c0 = 0; c0 < n; c0 += SC_TILE) {
+        const int base = c0 + threadIdx.x * SC_ITEMS;
+        int v[SC_ITEMS], s = 0;
+#pragma unroll
+        for (int j = 0; j < SC_ITEMS; ++j) {
+            v[j] = (base + j < n) ? a[base + j] : 0;
+            s = sat_add(s, v[j]);
+        }
+        int total;
+        int run = sat_add(block_excl_scan(s, wt, total), carry);
+#pragma unroll
+        for (int j = 0; j < SC_ITEMS; ++j) {
+            if (base + j < n) a[base + j] = run;
+            run = sat_add(run, v[j]);
+        }
+        carry = sat_add(carry, total);
+    }
+    if (threadIdx.x == 0) *total_out = carry;
+}
+
 void launch_scan_inplace(int *a, int n, int *partial, cudaStream_t s)
 {
+    if (n <= 2 * SC_TILE) {
+        // partial[number of SC_TILE parts] = total, as k_scan_partials leaves it
+        k_scan_single<<<1, SC_THREADS, 0, s>>>(a, n, partial + (n + SC_TILE - 1) / SC_TILE);
+        count_launch(1);
+        return;
+    }
     const int nparts = (n + SC_TILE - 1) / SC_TILE;
     k_scan_reduce<<<nparts, SC_THREADS, 0, s>>>(a, n, partial);
     k_scan_partials<<<1, SC_THREADS, 0, s>>>(partial, nparts);
