@@ -1727,8 +1727,11 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
             S.sh[i] = id0 >= 0 ? 1 : 0;
             any |= id0 != -1 && hx >= 0 && hy >= 0 && hx < TT && hy < TT;
         }
-        // an adjoint over a tile whose pixels hold no layer has nothing to propagate
-        if (BWD && !__syncthreads_or(any)) return;
+        // an adjoint over a tile whose pixels hold no layer has nothing to propagate; a
+        // forward over it writes the background
+        const bool some = __syncthreads_or(any);
+        if (BWD && !some) return;
+        empty = !some;
     }
     __syncthreads();
     if (g.edge_mode == 0 && !empty) {
