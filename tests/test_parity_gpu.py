@@ -207,14 +207,15 @@ def test_exact_fill_rule_on_gpu():
     assert (gpu.view_rgba(0)[..., 3] == 1.0).all()
 
 
-@pytest.mark.parametrize("tile,schedule", [(32, 2), (16, 1)])
-def test_reraster_adjoint_from_forward_kth_keys_equals_cold(tile, schedule):
+@pytest.mark.parametrize("tile,schedule,list_cap", [(32, 2, 0), (16, 1, 0), (32, 2, 4096)])
+def test_reraster_adjoint_from_forward_kth_keys_equals_cold(tile, schedule, list_cap):
     """The re-rasterizing adjoint that starts its K-lists from the K-th keys a forward
     without layer ids left in the workspace gives the gradients of a cold re-raster (its own
-    setup, no keys) up to the order of the float atomics, on the large workload's mesh."""
+    setup, no keys) up to the order of the float atomics, on the large workload's mesh; also
+    with tile lists over capacity (those tiles fall back to every face of the view)."""
     s = synth.config5(subdiv=5, n_views=3, res=384, tex_side=512)
     ps = PackedScene(s.meshes, "cuda")
-    r = Renderer(ps, s.views, s.params, tile=tile, schedule=schedule)
+    r = Renderer(ps, s.views, s.params, tile=tile, schedule=schedule, list_cap=list_cap)
     g = torch.randn(r.n_pix, 4, device="cuda")
     r.forward(store_layers=False)
     seeded = r.backward(g, ids=None)
@@ -223,7 +224,7 @@ def test_reraster_adjoint_from_forward_kth_keys_equals_cold(tile, schedule):
     for a, b in zip(seeded, cold):
         if a is not None:
             assert rel_l2(a.double().cpu().numpy(), b.double().cpu().numpy()) < 1e-6
-    assert r.device_status() == 0
+    assert r.device_status() == (1 if list_cap else 0)
 
 
 def test_store_and_recompute_backward_agree():
