@@ -42,7 +42,7 @@ static void launch_tile_profiled(const Globals &g, int pass, cudaStream_t s)
 }
 
 struct Layout {
-    size_t views, meshes, vrec, frec, tile_view, tile_count, tile_off, tile_cursor, lists, nrm, adj_off, adj_cur, adj, scan_partial,
+    size_t views, meshes, vrec, frec, brect, tile_view, tile_count, tile_off, tile_cursor, lists, nrm, adj_off, adj_cur, adj, scan_partial,
         sgrad, ngrad, queue,
         tile_order, lpt_hist, kth, kth_flag, tg_keys, tg_pay0, tg_pay1, tg_scratch, inv_uv, total;
     long long tg_slots;   // texel-gather record slots (0 unless texgrad_mode 1 with a texture)
@@ -170,6 +170,7 @@ static bool make_plan(const dressi_scene *sc, const dressi_view *views, int n_vi
     L.meshes = o; o = align_up(o + sizeof(MeshK) * sc->n_meshes);
     L.vrec = o; o = align_up(o + sizeof(VRec) * (size_t)std::max<long long>(vrec, 1));
     L.frec = o; o = align_up(o + sizeof(FaceRec) * (size_t)std::max<long long>(view_faces, 1));
+    L.brect = o; o = align_up(o + sizeof(unsigned) * (size_t)std::max<long long>(view_faces, 1));
     L.tile_view = o; o = align_up(o + sizeof(int) * (size_t)std::max(tiles, 1));
     L.tile_count = o; o = align_up(o + sizeof(int) * (size_t)tiles);
     L.tile_off = o; o = align_up(o + sizeof(int) * (size_t)(tiles + 1));
@@ -267,6 +268,7 @@ static Globals make_globals(const dressi_scene *sc, const dressi_params *p, cons
     g.ntex = sc->ntex;
     g.vrec = reinterpret_cast<VRec *>(ws + L.vrec);
     g.frec = reinterpret_cast<FaceRec *>(ws + L.frec);
+    g.brect = reinterpret_cast<unsigned *>(ws + L.brect);
     g.tile_view = reinterpret_cast<int *>(ws + L.tile_view);
     g.tile_count = reinterpret_cast<int *>(ws + L.tile_count);
     g.tile_off = reinterpret_cast<int *>(ws + L.tile_off);

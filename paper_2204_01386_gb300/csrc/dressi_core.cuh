@@ -116,6 +116,7 @@ struct Globals {
     const void *ntex;     // shade_mode 3: normal map, laid out like tex
     VRec *vrec;
     FaceRec *frec;        // per (view, face): the face's record, written by the setup
+    unsigned *brect;      // per (view, face): its binning tile rect, packed (pack_brect)
     int *tile_count, *tile_off, *tile_cursor, *lists;
     int *tile_view;       // [total_tiles] the view owning each tile
     float4 *nrm;          // [n_verts_total] normalized vertex normals, w = |sum|

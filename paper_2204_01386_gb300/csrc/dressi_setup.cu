@@ -207,6 +207,21 @@ __device__ __forceinline__ bool bin_rect(const Globals &g, const ViewK &V, const
     return tx0 <= tx1 && ty0 <= ty1;
 }
 
+// A face's tile rect [tx0, tx1] x [ty0, ty1], packed into one word for the list fill:
+// tx0 | ty0 << 11 | (tx1 - tx0) << 22 | (ty1 - ty0) << 27.  Tile coordinates are below
+// 2048 (views of at most 32,768 pixels at 16 px tiles); a rect more than 32 tiles wide or
+// high is BRECT_WIDE, and the list fill takes it from the face record.  Neither marker
+// is a valid packing (both would put tx0 + (tx1 - tx0) past 2047).
+constexpr unsigned BRECT_NONE = 0xffffffffu;   // no tile: culled, or off the view
+constexpr unsigned BRECT_WIDE = 0xfffffffeu;
+
+__device__ __forceinline__ unsigned pack_brect(bool any, int tx0, int tx1, int ty0, int ty1)
+{
+    if (!any) return BRECT_NONE;
+    if (tx1 - tx0 > 31 || ty1 - ty0 > 31) return BRECT_WIDE;
+    return (unsigned)tx0 | ((unsigned)ty0 << 11) | ((unsigned)(tx1 - tx0) << 22) | ((unsigned)(ty1 - ty0) << 27);
+}
+
 // the (face, tile) pairs of a warp's faces, one step per tile of each lane's box: the
 // lanes at the same tile in a step share one atomic (consecutive faces of a mesh are
 // mostly neighbours), and PASS 1 gives them consecutive list slots.  All 32 lanes call it.
@@ -246,11 +261,16 @@ __device__ __forceinline__ void bin_walk(const Globals &g, const ViewK &V, int f
 // binning (the lists' lengths).
 // ---------------------------------------------------------------------------
 template <bool COUNT>
-__global__ void k_face(Globals g)
+__global__ void __launch_bounds__(256) k_face(Globals g)
 {
+    // each warp's 32 records (7 float4 each) go through shared memory so that the warp
+    // writes its 3,584 contiguous bytes with full-line stores
+    __shared__ float4 stage[256 / 32][32 * 7];
     const ViewK &V = g.views[blockIdx.y];
     const MeshK &M = g.meshes[V.mesh];
     const VRec *vr = g.vrec + V.vrec_off;
+    const int lane = threadIdx.x & 31;
+    float4 *ws = stage[threadIdx.x >> 5];
     bool bad = false;
     // block-uniform trip count: every lane of a warp takes part in the binning steps
     for (int f0 = blockIdx.x * blockDim.x; f0 < M.nF; f0 += gridDim.x * blockDim.x) {
@@ -266,26 +286,36 @@ __global__ void k_face(Globals g)
                 for (int i = 0; i < 3; ++i) { R.vi[i] = 0; R.xh[i] = R.xl[i] = R.yh[i] = R.yl[i] = 0.f; }
             }
             live = (R.flags & FLAG_LIVE) != 0;
-            float4 *dst = reinterpret_cast<float4 *>(g.frec + V.frec_off + f);
-            dst[0] = make_float4(R.xh[0], R.xh[1], R.xh[2], R.xl[0]);
-            dst[1] = make_float4(R.xl[1], R.xl[2], R.yh[0], R.yh[1]);
-            dst[2] = make_float4(R.yh[2], R.yl[0], R.yl[1], R.yl[2]);
-            dst[3] = make_float4(R.invL[0], R.invL[1], R.invL[2], R.z[0]);
-            dst[4] = make_float4(R.z[1], R.z[2], R.invA, __int_as_float(R.flags));
-            dst[5] = make_float4(__int_as_float(R.id), __int_as_float(R.vi[0]), __int_as_float(R.vi[1]),
-                                 __int_as_float(R.vi[2]));
-            dst[6] = make_float4(R.iw[0], R.iw[1], R.iw[2], 0.f);
+            float4 *d = ws + lane * 7;   // 112-byte lane stride: no bank conflict within 8 lanes
+            d[0] = make_float4(R.xh[0], R.xh[1], R.xh[2], R.xl[0]);
+            d[1] = make_float4(R.xl[1], R.xl[2], R.yh[0], R.yh[1]);
+            d[2] = make_float4(R.yh[2], R.yl[0], R.yl[1], R.yl[2]);
+            d[3] = make_float4(R.invL[0], R.invL[1], R.invL[2], R.z[0]);
+            d[4] = make_float4(R.z[1], R.z[2], R.invA, __int_as_float(R.flags));
+            d[5] = make_float4(__int_as_float(R.id), __int_as_float(R.vi[0]), __int_as_float(R.vi[1]),
+                               __int_as_float(R.vi[2]));
+            d[6] = make_float4(R.iw[0], R.iw[1], R.iw[2], 0.f);
         }
+        __syncwarp();
+        {
+            const int wf0 = f0 + (threadIdx.x & ~31);   // the warp's first face
+            const int nrec = max(0, min(32, M.nF - wf0));
+            float4 *dst = reinterpret_cast<float4 *>(g.frec + V.frec_off + wf0);
+            for (int i = lane; i < nrec * 7; i += 32) dst[i] = ws[i];
+        }
+        __syncwarp();   // the staged records are read before the next iteration writes them
         if (COUNT) {
             int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
             const bool any = live && bin_rect(g, V, R.xh, R.yh, tx0, tx1, ty0, ty1);
+            if (f < M.nF) g.brect[V.frec_off + f] = pack_brect(any, tx0, tx1, ty0, ty1);
             bin_walk<0>(g, V, f, any, tx0, tx1, ty0, ty1);
         }
     }
     if (bad) atomicOr(g.status, DRESSI_DEV_FACE_RANGE);
 }
 
-// the list entries of every (face, tile) pair, into the slots the counts' prefix gives
+// the list entries of every (face, tile) pair, into the slots the counts' prefix gives;
+// each face's tile rect comes packed from the face table kernel
 __global__ void k_bin(Globals g)
 {
     const ViewK &V = g.views[blockIdx.y];
@@ -293,8 +323,18 @@ __global__ void k_bin(Globals g)
     for (int f0 = blockIdx.x * blockDim.x; f0 < M.nF; f0 += gridDim.x * blockDim.x) {
         const int f = f0 + threadIdx.x;
         int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
-        FaceRec R;
-        const bool any = f < M.nF && face_get(g, V, M, f, R) && bin_rect(g, V, R.xh, R.yh, tx0, tx1, ty0, ty1);
+        const unsigned b = f < M.nF ? __ldg(g.brect + V.frec_off + f) : BRECT_NONE;
+        bool any = false;
+        if (b == BRECT_WIDE) {
+            FaceRec R;
+            any = face_get(g, V, M, f, R) && bin_rect(g, V, R.xh, R.yh, tx0, tx1, ty0, ty1);
+        } else if (b != BRECT_NONE) {
+            tx0 = b & 2047;
+            ty0 = (b >> 11) & 2047;
+            tx1 = tx0 + ((b >> 22) & 31);
+            ty1 = ty0 + (b >> 27);
+            any = true;
+        }
         bin_walk<1>(g, V, f, any, tx0, tx1, ty0, ty1);
     }
 }
