@@ -1298,17 +1298,19 @@ __device__ __forceinline__ unsigned adjoint_queued(const Globals &g, Smem &S, co
         bool E = false, front = false;
         float4 gi4 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (in) {
+            // the layer ids and dL/dI together: one load latency instead of two in a row
+            int idk[K];
 #pragma unroll
-            for (int k = 0; k < K; ++k) nl += __ldg(g.ids_in + (long long)k * g.n_pix + pix) != -1 ? 1 : 0;
-            if (nl > 0) {
-                gi4 = __ldg(reinterpret_cast<const float4 *>(g.gin) + pix);
-                if (gi4.x != 0.f || gi4.y != 0.f || gi4.z != 0.f || gi4.w != 0.f) {
-                    E = edge_mask(g, S, lx, ly, rho);
-                    // outside the mask the pixel is its front layer's colour where S^H = 1
-                    front = !E && S.sh[(ly + rho) * hs + (lx + rho)] == 1 &&
-                            (gi4.x != 0.f || gi4.y != 0.f || gi4.z != 0.f);
-                    if (front) id0 = __ldg(g.ids_in + pix) & 0x7fffffff;
-                }
+            for (int k = 0; k < K; ++k) idk[k] = __ldg(g.ids_in + (long long)k * g.n_pix + pix);
+            gi4 = __ldg(reinterpret_cast<const float4 *>(g.gin) + pix);
+#pragma unroll
+            for (int k = 0; k < K; ++k) nl += idk[k] != -1 ? 1 : 0;
+            if (nl > 0 && (gi4.x != 0.f || gi4.y != 0.f || gi4.z != 0.f || gi4.w != 0.f)) {
+                E = edge_mask(g, S, lx, ly, rho);
+                // outside the mask the pixel is its front layer's colour where S^H = 1
+                front = !E && S.sh[(ly + rho) * hs + (lx + rho)] == 1 &&
+                        (gi4.x != 0.f || gi4.y != 0.f || gi4.z != 0.f);
+                id0 = idk[0] & 0x7fffffff;
             }
         }
         {
@@ -1719,13 +1721,27 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
         // layers stored by the forward: S^H of the tile and of its ring is the hard flag
         // of every pixel's stored front layer (a non-negative id: hard; bit 31: soft)
         bool any = false;   // some pixel of the tile itself holds a layer
-        for (int i = tid; i < hs * hs; i += NT) {
-            if (S.sh[i] == 2) continue;
+        // every load of the thread's share is issued before the first result is used
+        constexpr int HI = (HS_MAX * HS_MAX + NT - 1) / NT;
+        int fl[HI];
+        unsigned loaded = 0u;   // bit u: entry u is inside the halo and the image
+#pragma unroll
+        for (int u = 0; u < HI; ++u) {
+            const int i = tid + u * NT;
+            fl[u] = -1;
+            if (i < hs * hs && S.sh[i] != 2) {
+                const int hx = i % hs - rho, hy = i / hs - rho;
+                fl[u] = __ldg(g.ids_in + V.pix_off + (long long)(Y0 + hy) * V.W + (X0 + hx));
+                loaded |= 1u << u;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < HI; ++u) {
+            if (!((loaded >> u) & 1u)) continue;
+            const int i = tid + u * NT;
             const int hx = i % hs - rho, hy = i / hs - rho;
-            const long long hp = V.pix_off + (long long)(Y0 + hy) * V.W + (X0 + hx);
-            const int id0 = __ldg(g.ids_in + hp);
-            S.sh[i] = id0 >= 0 ? 1 : 0;
-            any |= id0 != -1 && hx >= 0 && hy >= 0 && hx < TT && hy < TT;
+            S.sh[i] = fl[u] >= 0 ? 1 : 0;
+            any |= fl[u] != -1 && hx >= 0 && hy >= 0 && hx < TT && hy < TT;
         }
         // an adjoint over a tile whose pixels hold no layer has nothing to propagate; a
         // forward over it writes the background
