@@ -297,7 +297,6 @@ __device__ __forceinline__ void prefetch_l2(const void *a)
     asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
 }
 
-// face_get into shared memory: seven 16-byte copies
 // the geometric part of face_get into shared memory: five 16-byte copies
 __device__ __forceinline__ bool face_stage(const Globals &g, const ViewK &V, const MeshK &m, int f, FaceGeo &dst)
 {
