@@ -739,6 +739,14 @@ __device__ __forceinline__ unsigned long long pack_frag(float key, int id)
     return ((unsigned long long)kb << 32) | (unsigned int)id;
 }
 
+// The K-list slots of tile pixel (x, y) start at kbuf + kslot(x, y) K.  The column is
+// XOR-swizzled by the row (bits 1-3), so that pixels in one column of neighbouring rows --
+// the exact evaluations of one face's row segments -- fall into different shared-memory
+// banks; within a row the map is a permutation.
+__device__ __forceinline__ int kswz(int y) { return (y & 7) << 1; }
+template <int TT>
+__device__ __forceinline__ int kslot(int x, int y) { return y * TT + (x ^ kswz(y)); }
+
 template <int K>
 __device__ __forceinline__ void kbuf_insert(unsigned long long *slots, unsigned long long v)
 {
@@ -1417,7 +1425,7 @@ __device__ __forceinline__ void raster_items(Smem &S, unsigned long long *kbuf, 
             if (q >= WQ) q -= WQ;
             const unsigned ent = wq[q];
             const int x = ent & 31, y = (ent >> 5) & 31, f = (ent >> 10) & 0xff;
-            unsigned long long *slots = kbuf + (y * TT + x) * K;
+            unsigned long long *slots = kbuf + kslot<TT>(x, y) * K;
             const unsigned long long last = *reinterpret_cast<volatile unsigned long long *>(slots + K - 1);
             if (!(__uint_as_float(ent & 0xfffc0000u) > __uint_as_float((unsigned int)(last >> 32)))) {
                 Frag fr;
@@ -1461,7 +1469,8 @@ __device__ __forceinline__ void raster_items(Smem &S, unsigned long long *kbuf, 
             const float klb_in = 0.5f * P.zmin * (1.f - 1e-6f);
             // the K-th slots change under other warps' merges; any value read is an upper
             // bound of the final one, so a pair culled against it stays culled
-            const volatile unsigned long long *last = kbuf + (y * TT + x) * K + K - 1;
+            const volatile unsigned long long *last = kbuf + K - 1;
+            const int row = y * TT, sw = kswz(y);
 #pragma unroll
             for (int d = 0; d < 4; ++d) {
                 // F(p) ~ the smallest edge value: outside, the distance is at least -F;
@@ -1471,7 +1480,7 @@ __device__ __forceinline__ void raster_items(Smem &S, unsigned long long *kbuf, 
                     const float klb = fmin > APPROX_EPS    ? klb_in
                                       : fmin < -APPROX_EPS ? fmaf(-fmin - APPROX_EPS, V.half_inv_S, 0.5f)
                                                            : 0.f;
-                    if (!(klb > __uint_as_float((unsigned int)(last[d * K] >> 32)))) {
+                    if (!(klb > __uint_as_float((unsigned int)(last[(row + ((x + d) ^ sw)) * K] >> 32)))) {
                         pm |= 1u << d;
                         kl[d] = klb;
                     }
@@ -1574,7 +1583,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
             for (int p = tid; p < TT * TT; p += NT) {
                 const int lx = p % TT, ly = p / TT;
                 if (lx < wlim && ly < hlim)
-                    kbuf[p * K + K - 1] = g.kth[V.slot_base + (long long)(Y0 + ly) * V.W + (X0 + lx)];
+                    kbuf[kslot<TT>(lx, ly) * K + K - 1] = g.kth[V.slot_base + (long long)(Y0 + ly) * V.W + (X0 + lx)];
             }
         }
         single_chunk = n <= CH;
@@ -1712,8 +1721,9 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
             const int p = tid + j * NT;
             const int lx = p % TT, ly = p / TT;
             if (empty || lx >= wlim || ly >= hlim) continue;
-            if (!BWD && g.kth) g.kth[V.slot_base + (long long)(Y0 + ly) * V.W + (X0 + lx)] = kbuf[p * K + K - 1];
-            const unsigned long long v = kbuf[p * K];
+            const int ks = kslot<TT>(lx, ly) * K;
+            if (!BWD && g.kth) g.kth[V.slot_base + (long long)(Y0 + ly) * V.W + (X0 + lx)] = kbuf[ks + K - 1];
+            const unsigned long long v = kbuf[ks];
             const bool sh = v != EMPTY && kept_hard(g, V, M, v, (float)(X0 + lx) + 0.5f, (float)(Y0 + ly) + 0.5f);
             S.sh[(ly + rho) * hs + (lx + rho)] = sh ? 1 : 0;
         }
@@ -1801,9 +1811,10 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
         for (int k = 0; k < K; ++k) ids[k] = 0x7fffffff;
         if (!in) {
         } else if (!from_ids) {
+            const int ks = kslot<TT>(lx, ly) * K;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                const unsigned long long v = kbuf[p * K + k];
+                const unsigned long long v = kbuf[ks + k];
                 ids[k] = (v == EMPTY) ? 0x7fffffff : (int)(unsigned int)(v & 0xffffffffu);
             }
             if (!BWD && g.ids) {
@@ -1811,7 +1822,7 @@ __device__ __forceinline__ void tile_body(const Globals &g, Smem &S, unsigned lo
                 hardbits = S.sh[(ly + rho) * hs + (lx + rho)] == 1 ? 1u : 0u;
 #pragma unroll
                 for (int k = 1; k < K; ++k) {
-                    const unsigned long long v = kbuf[p * K + k];
+                    const unsigned long long v = kbuf[ks + k];
                     if (v != EMPTY && kept_hard(g, V, M, v, (float)(X0 + lx) + 0.5f, (float)(Y0 + ly) + 0.5f))
                         hardbits |= 1u << k;
                 }
