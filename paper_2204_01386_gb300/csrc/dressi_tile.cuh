@@ -739,13 +739,14 @@ __device__ __forceinline__ unsigned long long pack_frag(float key, int id)
     return ((unsigned long long)kb << 32) | (unsigned int)id;
 }
 
-// The K-list slots of tile pixel (x, y) start at kbuf + kslot(x, y) K.  The column is
-// XOR-swizzled by the row (bits 1-3), so that pixels in one column of neighbouring rows --
-// the exact evaluations of one face's row segments -- fall into different shared-memory
-// banks; within a row the map is a permutation.
-__device__ __forceinline__ int kswz(int y) { return (y & 7) << 1; }
+// The K-list slots of tile pixel (x, y) start at kbuf + kslot(x, y) K.  Each row is rotated
+// by 12 y columns: with K = 3 (24-byte slot groups) the 8-byte bank pair of a pixel's group
+// is then 3 x + 4 y mod 16, distinct over every 4 x 4 block of pixels, so the exact
+// evaluations of one face's neighbouring row segments meet few bank conflicts; within a
+// row the map is a permutation.
+__device__ __forceinline__ int kswz(int y) { return 12 * y; }
 template <int TT>
-__device__ __forceinline__ int kslot(int x, int y) { return y * TT + (x ^ kswz(y)); }
+__device__ __forceinline__ int kslot(int x, int y) { return y * TT + ((x + kswz(y)) & (TT - 1)); }
 
 template <int K>
 __device__ __forceinline__ void kbuf_insert(unsigned long long *slots, unsigned long long v)
@@ -1480,7 +1481,7 @@ __device__ __forceinline__ void raster_items(Smem &S, unsigned long long *kbuf, 
                     const float klb = fmin > APPROX_EPS    ? klb_in
                                       : fmin < -APPROX_EPS ? fmaf(-fmin - APPROX_EPS, V.half_inv_S, 0.5f)
                                                            : 0.f;
-                    if (!(klb > __uint_as_float((unsigned int)(last[(row + ((x + d) ^ sw)) * K] >> 32)))) {
+                    if (!(klb > __uint_as_float((unsigned int)(last[(row + ((x + d + sw) & (TT - 1))) * K] >> 32)))) {
                         pm |= 1u << d;
                         kl[d] = klb;
                     }
