@@ -740,11 +740,12 @@ __device__ __forceinline__ unsigned long long pack_frag(float key, int id)
 }
 
 // The K-list slots of tile pixel (x, y) start at kbuf + kslot(x, y) K.  Each row is rotated
-// by 12 y columns: with K = 3 (24-byte slot groups) the 8-byte bank pair of a pixel's group
-// is then 3 x + 4 y mod 16, distinct over every 4 x 4 block of pixels, so the exact
-// evaluations of one face's neighbouring row segments meet few bank conflicts; within a
-// row the map is a permutation.
-__device__ __forceinline__ int kswz(int y) { return 12 * y; }
+// by 5 y columns: with K = 3 (24-byte slot groups) the 8-byte bank pair of a pixel's group
+// is then 3 x + 15 y mod 16, so both access patterns of the raster spread over the banks --
+// the pretest's lanes (one 4-pixel row segment each, the segments of a face's rows) at two
+// lanes per bank pair, the exact evaluations (8 x 4 pixel patches) at three at most; within
+// a row the map is a permutation.
+__device__ __forceinline__ int kswz(int y) { return 5 * y; }
 template <int TT>
 __device__ __forceinline__ int kslot(int x, int y) { return y * TT + ((x + kswz(y)) & (TT - 1)); }
 
