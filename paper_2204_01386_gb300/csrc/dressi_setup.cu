@@ -266,8 +266,8 @@ __global__ void __launch_bounds__(256) k_face(Globals g)
     // each warp's 32 records (7 float4 each) go through shared memory so that the warp
     // writes its 3,584 contiguous bytes with full-line stores
     __shared__ float4 stage[256 / 32][32 * 7];
-    const ViewK &V = g.views[blockIdx.y];
-    const MeshK &M = g.meshes[V.mesh];
+    const ViewK V = g.views[blockIdx.y];   // copies: the fields stay in registers across the stores
+    const MeshK M = g.meshes[V.mesh];
     const VRec *vr = g.vrec + V.vrec_off;
     const int lane = threadIdx.x & 31;
     float4 *ws = stage[threadIdx.x >> 5];
@@ -318,8 +318,8 @@ __global__ void __launch_bounds__(256) k_face(Globals g)
 // each face's tile rect comes packed from the face table kernel
 __global__ void k_bin(Globals g)
 {
-    const ViewK &V = g.views[blockIdx.y];
-    const MeshK &M = g.meshes[V.mesh];
+    const ViewK V = g.views[blockIdx.y];   // copies: the fields stay in registers across the stores
+    const MeshK M = g.meshes[V.mesh];
     for (int f0 = blockIdx.x * blockDim.x; f0 < M.nF; f0 += gridDim.x * blockDim.x) {
         const int f = f0 + threadIdx.x;
         int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
