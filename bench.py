@@ -578,7 +578,7 @@ def extra_legs(s, args, dev, world, dist, flush, st):
 
         e2e_steps(2)
         torch.cuda.synchronize()
-        n_e2e = max(3, args.steps // 2)
+        n_e2e = max(3, args.steps)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if world > 1:
             dist.barrier()
