@@ -15,9 +15,9 @@ from parity import FWD_TOL, masks
 pytestmark = pytest.mark.gpu
 
 
-def _renderer(scene):
+def _renderer(scene, tile=0, schedule=0):
     ps = PackedScene(scene.meshes, "cuda")
-    return Renderer(ps, scene.views, scene.params)
+    return Renderer(ps, scene.views, scene.params, tile=tile, schedule=schedule)
 
 
 def _restyled(scene, seed, sigma_scale=1.0, delta_scale=1.0, edge_mode=None):
@@ -39,10 +39,11 @@ def _restyled(scene, seed, sigma_scale=1.0, delta_scale=1.0, edge_mode=None):
     return dataclasses.replace(scene, meshes=meshes, views=views, params=p)
 
 
+@pytest.mark.parametrize("tile,schedule", [(0, 0), (32, 2), (16, 1)])
 @pytest.mark.parametrize("cfg", ["config1", "config2"])
-def test_from_layers_reproduces_forward(cfg):
+def test_from_layers_reproduces_forward(cfg, tile, schedule):
     s = getattr(synth, cfg)()
-    r = _renderer(s)
+    r = _renderer(s, tile, schedule)
     out, ids = r.forward(store_layers=True)
     again = r.forward_from_layers(ids)
     torch.cuda.synchronize()

@@ -16,9 +16,10 @@ def test_camera_gradient_vertex_colour(store_layers):
     assert "mvp0" in st["grad_err"]
 
 
+@pytest.mark.parametrize("tile,schedule", [(0, 0), (32, 2)])
 @pytest.mark.parametrize("store_layers", [True, False])
-def test_camera_and_light_gradient_lambert(store_layers):
-    st = compare_scene(synth.config2(), store_layers=store_layers, camera=True)
+def test_camera_and_light_gradient_lambert(store_layers, tile, schedule):
+    st = compare_scene(synth.config2(), store_layers=store_layers, camera=True, tile=tile, schedule=schedule)
     assert "mvp0" in st["grad_err"] and "light0" in st["grad_err"]
 
 

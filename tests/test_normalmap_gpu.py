@@ -12,9 +12,12 @@ from parity import compare_scene
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("tile,schedule", [(0, 0), (32, 2)])
 @pytest.mark.parametrize("store_layers", [True, False])
-def test_normal_map_parity(store_layers):
-    st = compare_scene(synth.config2n(), store_layers=store_layers, camera=True)
+def test_normal_map_parity(store_layers, tile, schedule):
+    # the library's default execution choice, and 32 px tiles with persistent CTAs in
+    # longest-first order (the kernels with the normal map compiled in)
+    st = compare_scene(synth.config2n(), store_layers=store_layers, camera=True, tile=tile, schedule=schedule)
     assert {"pos0", "tex0", "ntex0", "mvp0", "light0"} <= set(st["grad_err"]), st["grad_err"]
 
 

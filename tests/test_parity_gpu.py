@@ -1,4 +1,6 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI."""
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -66,6 +68,17 @@ def test_fp16_texture_storage():
     s = synth.config5(subdiv=4, n_views=2, res=128, tex_side=256)
     assert s.meshes[0].tex.dtype == np.float16
     st = compare_scene(s, store_layers=False)
+    assert st["ids_checked"] > 10000
+
+
+@pytest.mark.parametrize("store_layers", [True, False])
+def test_fp16_texture_with_texel_gather(store_layers):
+    """The deterministic texel gather (texgrad_mode 1) over an FP16 texture, with stored
+    layer ids and with the re-rasterizing adjoint (32 px tiles, persistent longest-first):
+    the FP32 texel gradient and the rest against the oracle on the FP16 texture."""
+    s = synth.config5(subdiv=4, n_views=2, res=128, tex_side=256)
+    s.params = dataclasses.replace(s.params, texgrad_mode=1)
+    st = compare_scene(s, store_layers=store_layers, tile=32, schedule=2)
     assert st["ids_checked"] > 10000
 
 
