@@ -25,10 +25,10 @@ def _with_mode(scene, jitter):
     return dataclasses.replace(scene, params=p)
 
 
-def _gpu_inverse_uv(scene, grads, store_layers=True):
+def _gpu_inverse_uv(scene, grads, store_layers=True, tile=0, schedule=0):
     """Runs forward + adjoint; returns (texel gradient [n_texels, 3], winners [n_texels])."""
     ps = PackedScene(scene.meshes, "cuda")
-    r = Renderer(ps, scene.views, scene.params)
+    r = Renderer(ps, scene.views, scene.params, tile=tile, schedule=schedule)
     _, ids = r.forward(store_layers=True)
     g = torch.zeros(r.n_pix, 4, device="cuda")
     for i, v in enumerate(r.views):
@@ -67,7 +67,7 @@ def test_inverse_uv_pixel_aligned_quad(jitter, axis, shift):
     np.testing.assert_array_equal(win, expect)
 
 
-def _compare(scene, jitter, store_layers=True, seed=0):
+def _compare(scene, jitter, store_layers=True, seed=0, tile=0, schedule=0):
     s = _with_mode(scene, jitter)
     rng = np.random.default_rng(seed)
     grads, recs, pix_stable = [], [], []
@@ -82,7 +82,7 @@ def _compare(scene, jitter, store_layers=True, seed=0):
         pix_stable.append(s_ids.reshape(-1))
         base += v.width * v.height
     pix_stable = np.concatenate(pix_stable)
-    gt, win = _gpu_inverse_uv(s, grads, store_layers)
+    gt, win = _gpu_inverse_uv(s, grads, store_layers, tile, schedule)
     m = s.meshes[0]
     o_grad, o_win, stable = oracle.inverse_uv_texels(recs, m.tex.shape[1], m.tex.shape[0])
     K = s.params.K
@@ -104,7 +104,8 @@ def test_inverse_uv_textured_sphere(store_layers, jitter):
     assert _compare(synth.config2(), jitter, store_layers) > 1000
 
 
-def test_inverse_uv_several_views():
+@pytest.mark.parametrize("tile,schedule", [(0, 0), (32, 2)])
+def test_inverse_uv_several_views(tile, schedule):
     """Three views of one sphere: a texel seen in several views keeps the last view's
-    sample."""
-    assert _compare(synth.config3(n_views=3, res=128), (-0.31, 0.12)) > 1000
+    sample, whichever order the tiles run in."""
+    assert _compare(synth.config3(n_views=3, res=128), (-0.31, 0.12), tile=tile, schedule=schedule) > 1000
