@@ -511,11 +511,6 @@ __device__ __forceinline__ bool hard_test(const FaceGeo &R, float px, float py)
     return inside;
 }
 
-__device__ __forceinline__ bool frag_less(float ka, int ia, float kb, int ib)
-{
-    return ka < kb || (ka == kb && ia < ib);
-}
-
 // 1 / (1 + exp(-x)) from e = exp(-|x|) <= 1 (no overflow): 1 / (1 + e) for x >= 0, e / (1 + e)
 // below; the exponential and the division are the fast hardware forms (a few ulp)
 __device__ __forceinline__ float sigmoidf_stable(float x)

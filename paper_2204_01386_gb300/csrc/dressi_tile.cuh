@@ -107,63 +107,6 @@ __device__ __forceinline__ float approx_fmin(const Pre &P, float lx, float ly)
     return fminf(f0, fminf(f1, f2));
 }
 
-// position of halo pixel h in the ring of width rho around a TT x TT tile (tile-local)
-template <int TT>
-__device__ __forceinline__ void halo_pos(int h, int rho, int &hx, int &hy)
-{
-    const int hs = TT + 2 * rho;
-    if (h < rho * hs) { hy = h / hs - rho; hx = h % hs - rho; return; }
-    h -= rho * hs;
-    if (h < rho * hs) { hy = TT + h / hs; hx = h % hs - rho; return; }
-    h -= rho * hs;
-    if (h < rho * TT) { hy = h / rho; hx = h % rho - rho; return; }
-    h -= rho * TT;
-    hy = h / rho;
-    hx = TT + h % rho;
-}
-
-// per-pixel K-selection of the peel; with CARRY the distance and barycentrics of
-// every kept fragment travel along, so shading does not re-evaluate the face
-template <int K, bool CARRY>
-struct PeelState {
-    float key[K];
-    int id[K];
-    bool hard[K];
-    float dist[CARRY ? K : 1], l0[CARRY ? K : 1], l1[CARRY ? K : 1], l2[CARRY ? K : 1];
-
-    __device__ __forceinline__ void init()
-    {
-#pragma unroll
-        for (int k = 0; k < K; ++k) { key[k] = 3.0e38f; id[k] = 0x7fffffff; hard[k] = false; }
-    }
-    __device__ __forceinline__ void put(int k, float ky, int i, bool h, float d, float a0, float a1, float a2)
-    {
-        key[k] = ky; id[k] = i; hard[k] = h;
-        if (CARRY) { dist[k] = d; l0[k] = a0; l1[k] = a1; l2[k] = a2; }
-    }
-    __device__ __forceinline__ void move(int to, int from)
-    {
-        key[to] = key[from]; id[to] = id[from]; hard[to] = hard[from];
-        if (CARRY) { dist[to] = dist[from]; l0[to] = l0[from]; l1[to] = l1[from]; l2[to] = l2[from]; }
-    }
-    // keeps the K smallest (key, id) pairs
-    __device__ __forceinline__ void insert(float ky, int i, bool h, float d, float a0, float a1, float a2)
-    {
-        if (!frag_less(ky, i, key[K - 1], id[K - 1])) return;
-        bool done = false;
-#pragma unroll
-        for (int t = K - 1; t > 0; --t) {
-            const bool lt = frag_less(ky, i, key[t - 1], id[t - 1]);
-            if (!done) {
-                if (lt) move(t, t - 1);
-                else put(t, ky, i, h, d, a0, a1, a2);
-            }
-            done = done || !lt;
-        }
-        if (!done) put(0, ky, i, h, d, a0, a1, a2);
-    }
-};
-
 // ---------------------------------------------------------------------------
 // per-layer shading (Sec. 3.3.2 texture sampling, Sec. 3.4.3 shading)
 // ---------------------------------------------------------------------------
