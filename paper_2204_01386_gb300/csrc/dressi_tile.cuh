@@ -12,8 +12,9 @@
 //      time, the pixels passing the pretest and the key lower bound go to the warp's own
 //      queue, and the queue gets the exact SignedDist, hard test and Shift key with full
 //      warps; each pixel keeps its K smallest (key, id) pairs in shared memory (depth
-//      peeling of Alg. 2 as a per-pixel K-selection; the re-rasterizing adjoint starts
-//      from the forward's K-th pair when the forward kept it);
+//      peeling of Alg. 2 as a per-pixel K-selection, the rows of K-lists rotated so that
+//      neighbouring pixels use different banks; the re-rasterizing adjoint starts from
+//      the forward's K-th pair when the forward kept it);
 //   3. the hard stencil S^H of a ring of rho pixels around the tile is built from the
 //      same staged faces (hard test only), so the edge mask E of every tile pixel is
 //      known without a second pass over the image;
