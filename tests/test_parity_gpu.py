@@ -271,6 +271,19 @@ def test_config3_full_size_sampled(tile, schedule, store_layers):
     assert st["ids_checked"] > 4000
 
 
+@pytest.mark.parametrize("store_layers", [True, False])
+@pytest.mark.parametrize("edge_mode", [1, 2])
+def test_config3_other_edge_modes_sampled(edge_mode, store_layers):
+    """The multi-view workload with E = 1 everywhere (every pixel blends all its layers:
+    the adjoints' blend lists at their longest) and with E = 0 (hard only), 32 px tiles,
+    persistent longest-first; the crops of the full-size test."""
+    s = synth.config3()
+    s.params = dataclasses.replace(s.params, edge_mode=edge_mode)
+    wins = [_C3_CROPS.get(i, (0, 0, 0, 0)) for i in range(len(s.views))]
+    st = compare_scene(s, windows=wins, tile=32, schedule=2, store_layers=store_layers)
+    assert st["ids_checked"] > 4000
+
+
 @pytest.mark.parametrize("tile,schedule", [(32, 2), (16, 1)])
 def test_config3_cut_tiles_at_the_image_edge(tile, schedule):
     """The multi-view workload at 500^2 (500 = 15 x 32 + 20 = 31 x 16 + 4): the last tile
