@@ -271,6 +271,17 @@ def test_config3_full_size_sampled(tile, schedule, store_layers):
     assert st["ids_checked"] > 4000
 
 
+@pytest.mark.parametrize("K", [1, 5])
+def test_config3_other_K_sampled(K):
+    """The multi-view workload with one layer and with five (40 KB of K-lists per 32 px
+    tile), re-rasterizing adjoint, 32 px persistent tiles; the crops of the full-size test."""
+    s = synth.config3()
+    s.params = dataclasses.replace(s.params, K=K)
+    wins = [_C3_CROPS.get(i, (0, 0, 0, 0)) for i in range(len(s.views))]
+    st = compare_scene(s, windows=wins, tile=32, schedule=2, store_layers=False)
+    assert st["ids_checked"] > 4000
+
+
 @pytest.mark.parametrize("store_layers", [True, False])
 @pytest.mark.parametrize("edge_mode", [1, 2])
 def test_config3_other_edge_modes_sampled(edge_mode, store_layers):
@@ -306,8 +317,8 @@ def test_config5_full_size_crop(tile, schedule):
     assert st["ids_checked"] > 5000
 
 
-@pytest.mark.parametrize("tile,schedule", [(32, 2), (16, 1)])
-def test_config4_sampled(tile, schedule):
+@pytest.mark.parametrize("tile,schedule,store_layers", [(32, 2, True), (16, 1, True), (32, 2, False)])
+def test_config4_sampled(tile, schedule, store_layers):
     """The full ragged batch (32 meshes of 1k..200k tris, 128^2..1024^2 views, 512^2..2048^2
     textures) in one call; checked against the oracle on the views of the four smallest
     meshes in full and on a 64 x 64 crop of every other view (seeded position within the
@@ -327,7 +338,7 @@ def test_config4_sampled(tile, schedule):
             x0 = int(g.integers(v.width // 4 - 32, 3 * v.width // 4 - 32 + 1))
             y0 = int(g.integers(v.height // 4 - 32, 3 * v.height // 4 - 32 + 1))
             wins.append((max(0, x0), max(0, y0), 64, 64))
-    st = compare_scene(s, windows=wins, tile=tile, schedule=schedule)
+    st = compare_scene(s, windows=wins, tile=tile, schedule=schedule, store_layers=store_layers)
     assert st["ids_checked"] > 500000
 
 
