@@ -317,14 +317,18 @@ def test_config5_full_size_crop(tile, schedule):
     assert st["ids_checked"] > 5000
 
 
-@pytest.mark.parametrize("tile,schedule,store_layers", [(32, 2, True), (16, 1, True), (32, 2, False)])
-def test_config4_sampled(tile, schedule, store_layers):
+@pytest.mark.parametrize("tile,schedule,store_layers,texgrad", [(32, 2, True, 0), (16, 1, True, 0), (32, 2, False, 0),
+                                                            (32, 2, True, 1)])
+def test_config4_sampled(tile, schedule, store_layers, texgrad):
     """The full ragged batch (32 meshes of 1k..200k tris, 128^2..1024^2 views, 512^2..2048^2
     textures) in one call; checked against the oracle on the views of the four smallest
     meshes in full and on a 64 x 64 crop of every other view (seeded position within the
     middle half of the view, so crops straddle silhouettes; the two largest meshes' crops
     are centred)."""
     s = synth.config4()
+    # texgrad 1: the deterministic texel gather over the 32 packed textures (tens of
+    # millions of (pixel, layer) records through the radix sort)
+    s.params = dataclasses.replace(s.params, texgrad_mode=texgrad)
     nf = [int(m.faces.shape[0]) for m in s.meshes]
     order = np.argsort(nf)
     g = np.random.default_rng(44)
