@@ -8,7 +8,9 @@
 // the key TG_NONE.  Then:
 //   1. a stable LSD radix sort (8-bit digits) orders the (key, slot) pairs by base
 //      texel; the first pass drops TG_NONE keys; equal keys keep slot order;
-//   2. one thread per texel sums, in a fixed order, the records of the four bases
+//   2. a table gives each base texel the first sorted position of its records (-1
+//      for none);
+//   3. one thread per texel sums, in a fixed order, the records of the four bases
 //      whose bilinear footprint holds the texel (itself, its left, upper and
 //      upper-left neighbours, with REPEAT wrap) with the matching weights.
 // No floating-point atomics: the result is bitwise reproducible.
@@ -130,9 +132,13 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const unsigned *keys, co
 {
     __shared__ int h[RS_BINS];
     const int n = rs_count(count, cap);
+    const long long base = (long long)blockIdx.x * RS_TILE;
+    if (base >= n) {   // past the records (the passes after the first see only the kept ones)
+        hist[threadIdx.x * nblocks + blockIdx.x] = 0;
+        return;
+    }
     h[threadIdx.x] = 0;
     __syncthreads();
-    const long long base = (long long)blockIdx.x * RS_TILE;
     for (int j = 0; j < RS_ITEMS; ++j) {
         const long long i = base + j * RS_THREADS + threadIdx.x;
         if (i < n) {
@@ -153,15 +159,19 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const unsigned *keys_
     __shared__ int wcnt[RS_THREADS / 32][RS_BINS];   // per-warp digit counts of a round
     const int n = rs_count(count, cap);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    run[tid] = offs[tid * nblocks + blockIdx.x];
     const long long base = (long long)blockIdx.x * RS_TILE;
+    if (base >= n) return;   // a block past the records has nothing to place
+    run[tid] = offs[tid * nblocks + blockIdx.x];
     for (int j = 0; j < RS_ITEMS; ++j) {
-        for (int w = 0; w < RS_THREADS / 32; ++w) wcnt[w][tid] = 0;
-        __syncthreads();
         const long long i = base + j * RS_THREADS + tid;
         unsigned k = TG_NONE;
         if (i < n) k = keys_in[i];
         const bool valid = k != TG_NONE;
+        // a round without a kept record (most of the first pass's slots are empty) places
+        // nothing; the test is a barrier, so the previous round's counts are read
+        if (!__syncthreads_or(valid)) continue;
+        for (int w = 0; w < RS_THREADS / 32; ++w) wcnt[w][tid] = 0;
+        __syncthreads();
         const int d = valid ? (int)((k >> shift) & 0xff) : RS_BINS;   // RS_BINS: dropped
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const int rank = __popc(peers & ((1u << lane) - 1u));
@@ -189,18 +199,17 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const unsigned *keys_
 }
 
 // --- gather ------------------------------------------------------------------------
-// first sorted position with key >= k
-__device__ __forceinline__ int lower_bound_u(const unsigned *keys, int n, unsigned k)
+// first[key] = the first sorted position holding key (the table starts at -1)
+__global__ void k_tg_first(const unsigned *keys, const int *count, int *first)
 {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (keys[mid] < k) lo = mid + 1; else hi = mid;
+    const int n = *count;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned k = keys[i];
+        if (i == 0 || keys[i - 1] != k) first[k] = i;
     }
-    return lo;
 }
 
-__global__ void k_tex_gather(Globals g, const unsigned *keys, const int *vals, const int *count)
+__global__ void k_tex_gather(Globals g, const unsigned *keys, const int *vals, const int *count, const int *first)
 {
     const MeshK &M = g.meshes[blockIdx.y];
     const long long n_tex = (long long)M.tex_w * M.tex_h;
@@ -220,8 +229,8 @@ __global__ void k_tex_gather(Globals g, const unsigned *keys, const int *vals, c
             // a texture of width or height 1 wraps a texel onto itself: the same base
             // then owns several corners of the footprint, all handled by its records
             const unsigned key = (unsigned)(M.tex_off + (long long)by * M.tex_w + bx);
-            int i = lower_bound_u(keys, n, key);
-            for (; i < n && keys[i] == key; ++i) {
+            int i = first[key];
+            for (; i >= 0 && i < n && keys[i] == key; ++i) {
                 const int slot = vals[i];
                 const float4 r = p0[slot];
                 const float fx = r.w, fy = p1[slot];
@@ -294,15 +303,13 @@ size_t texgather_scratch_bytes(long long slots, long long n_texels, size_t align
     const long long hist = (long long)RS_BINS * nblocks;
     const long long parts = (hist + SC_TILE - 1) / SC_TILE + 1;
     auto up = [align](size_t x) { return (x + align - 1) / align * align; };
-    (void)n_texels;
     return up(sizeof(unsigned) * slots) * 2 + up(sizeof(int) * slots) * 2 + up(sizeof(int) * hist) +
-           up(sizeof(int) * parts) + up(sizeof(int) * 4);
+           up(sizeof(int) * parts) + up(sizeof(int) * 4) + up(sizeof(int) * std::max<long long>(n_texels, 1));
 }
 
 void launch_tex_gather(const Globals &g, long long slots, long long n_texels, int n_meshes, int max_texels,
                        char *scratch, size_t align, cudaStream_t s)
 {
-    (void)n_texels;
     auto up = [align](size_t x) { return (x + align - 1) / align * align; };
     const long long nblocks = (slots + RS_TILE - 1) / RS_TILE;
     const long long hist_n = (long long)RS_BINS * nblocks;
@@ -313,7 +320,8 @@ void launch_tex_gather(const Globals &g, long long slots, long long n_texels, in
     int *vB = reinterpret_cast<int *>(p); p += up(sizeof(int) * slots);
     int *hist = reinterpret_cast<int *>(p); p += up(sizeof(int) * hist_n);
     int *partial = reinterpret_cast<int *>(p); p += up(sizeof(int) * ((hist_n + SC_TILE - 1) / SC_TILE + 1));
-    int *count = reinterpret_cast<int *>(p);
+    int *count = reinterpret_cast<int *>(p); p += up(sizeof(int) * 4);
+    int *first = reinterpret_cast<int *>(p);
     const int nparts = (int)((hist_n + SC_TILE - 1) / SC_TILE);
 
     // digits needed for the largest key
@@ -341,9 +349,11 @@ void launch_tex_gather(const Globals &g, long long slots, long long n_texels, in
         kout = (kout == kA) ? kB : kA;
         vout = (vout == vA) ? vB : vA;
     }
+    cudaMemsetAsync(first, 0xff, sizeof(int) * (size_t)std::max<long long>(n_texels, 1), s);
+    k_tg_first<<<grid_of(slots, 256, 152 * 16), 256, 0, s>>>(kin, count, first);
     dim3 grid(grid_of(max_texels, 256, 4096), n_meshes);
-    k_tex_gather<<<grid, 256, 0, s>>>(g, kin, vin, count);
-    count_launch(1);
+    k_tex_gather<<<grid, 256, 0, s>>>(g, kin, vin, count, first);
+    count_launch(2);
 }
 
 // ---------------------------------------------------------------------------
