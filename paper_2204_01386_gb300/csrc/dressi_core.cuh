@@ -23,8 +23,8 @@ namespace dressi {
 
 constexpr int MAXK = DRESSI_MAX_K;
 constexpr int CHUNK = 128;   // faces staged in shared memory per round
-constexpr int LPT_BINS = 1024;
-constexpr unsigned TG_NONE = 0xffffffffu;  // texel-gather record slot without a texture gradient  // face-list lengths bucketed for the longest-first tile order
+constexpr int LPT_BINS = 1024;             // face-list lengths bucketed for the longest-first tile order
+constexpr unsigned TG_NONE = 0xffffffffu;  // texel-gather record slot without a texture gradient
 constexpr int FLAG_LIVE = 1 << 7;
 // outside a face, its edge lines' signed distances F closer than this (pixels) count as a
 // tie when choosing the edge that holds the closest point (far above their FP32 error)
